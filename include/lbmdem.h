@@ -1,0 +1,205 @@
+/*
+ * lbmdem.h -- C ABI of the GB300 four-way coupled lattice Boltzmann / discrete
+ * element library (Rettinger & Ruede, "An efficient four-way coupled lattice
+ * Boltzmann - discrete element method for fully resolved simulations of
+ * particle-laden flows", arXiv 2003.01490).
+ *
+ * One context advances one simulation box of D3Q19 fluid with spherical
+ * particles on one CUDA device. lbm_step() runs Algorithm 1 of Sec. 4.2 per
+ * time step: moving no-slip boundary conditions (Eq. (14)) and the momentum
+ * exchange force/torque (Eqs. (15)-(17)) fused into the pull-stream + TRT+aB
+ * collision (Eqs. (1)-(2), (5), (12), Sec. 2.3.2), two-step force averaging
+ * (Sec. 4.2), n_sub DEM subcycles with lubrication (Eqs. (25)-(33)), linear
+ * spring-dashpot contact (Eqs. (39)-(52)) and Velocity Verlet (Eqs. (37)-(38)),
+ * then the particle mapping update and PDF refill (Sec. 2.2, Eq. (18)).
+ *
+ * Units are lattice units (dx = dt = rho0 = 1, c_s^2 = 1/3, Sec. 2.1). Cell
+ * (i, j, k) has its centre at (i + 1/2, j + 1/2, k + 1/2); walls lie on the
+ * domain faces. Host arrays are x-fastest: cell index = i + nx (j + ny k).
+ *
+ * Conventions for every call:
+ *   - All pointer arguments are HOST memory owned by the caller; a call reads
+ *     or fills them before it returns (getters synchronise the context stream).
+ *   - The context owns its device memory (lbm_create) or carves it from a
+ *     caller-owned device arena (lbm_create_in_arena); either way the caller
+ *     never frees pieces of it.
+ *   - Every call returns an lbm_status; none aborts the process. Errors raised
+ *     asynchronously on the device (capacity overflow, unstable density) are
+ *     sticky and are reported by the next lbm_sync() or getter.
+ *   - A context is used by one host thread at a time; distinct contexts are
+ *     independent.
+ */
+#ifndef LBMDEM_H
+#define LBMDEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = -1,   /* bad argument: size, parameter range, overlap, ... */
+    LBM_ERR_OOM = -2,       /* device allocation failed or arena too small       */
+    LBM_ERR_CUDA = -3,      /* a CUDA runtime call failed                        */
+    LBM_ERR_UNSTABLE = -4,  /* NaN or |rho - 1| > 0.5 detected on the device      */
+    LBM_ERR_CAPACITY = -5,  /* a fixed-capacity device list overflowed           */
+    LBM_ERR_STATE = -7      /* call not allowed in the current state             */
+} lbm_status;
+
+/* PDF storage format. Every format stores the shifted value f_q - w_q; the
+ * collision runs in float64 for LBM_STORE_F64 and in float32 otherwise. */
+typedef enum {
+    LBM_STORE_F64 = 0,
+    LBM_STORE_F32 = 1,
+    LBM_STORE_F16 = 2,
+    LBM_STORE_BF16 = 3
+} lbm_storage;
+
+/* Flag bits returned by lbm_get_fields(). */
+#define LBM_FLAG_SOLID 0x01u     /* cell centre inside a particle (Sec. 2.2)              */
+#define LBM_FLAG_SHELL 0x02u     /* fluid cell inside the TRT+aB shell (Sec. 2.3.2)       */
+#define LBM_FLAG_NEAR 0x04u      /* fluid cell that may have a particle link              */
+#define LBM_FLAG_MISS 0x08u      /* solid cell that may own a missing link (Sec. 2.2)     */
+#define LBM_FLAG_NEWFLUID 0x10u  /* solid before the last mapping update, fluid after     */
+
+/* Box: every axis is either periodic or closed by a no-slip wall on both of
+ * its faces (halfway bounce-back, Eq. (14) with delta = 1/2). */
+typedef struct {
+    int nx, ny, nz;
+    int periodic[3];                 /* 1 = periodic axis, 0 = walls on both faces */
+    double wall_vel_lo[3][3];        /* [axis][component] velocity of the low face  */
+    double wall_vel_hi[3][3];        /* [axis][component] velocity of the high face */
+} lbm_grid;
+
+/* Relaxation parameters of the TRT+aB collision (Secs. 2.1.1-2.1.3, 2.3.2). */
+typedef struct {
+    double tau;            /* 1/s_nu, > 0.5; viscosity nu = (tau - 1/2)/3, Eq. (7)   */
+    double magic;          /* Lambda of Eq. (11); paper value 3/16                    */
+    double lambda_b_shell; /* Lambda_b of Eq. (13) inside the shell; paper value 100  */
+    double lambda_b_bulk;  /* Lambda_b elsewhere; 1 gives TRT+aB, != 1 gives TRT+B    */
+    double shell_width;    /* delta_aB of Sec. 2.3.2; paper value 2                   */
+} lbm_relax;
+
+/* Particle parameters (Secs. 3.1, 4.1, 4.2). */
+typedef struct {
+    double e_dry;          /* dry coefficient of restitution, Eq. (42)                    */
+    double Tc;             /* collision time; <= 0 selects T_c = 2.31 D / c_s, Eq. (55)   */
+    double nu_p;           /* Poisson's ratio, Eq. (52)                                   */
+    double mu_p;           /* Coulomb friction coefficient, Eq. (47)                      */
+    int n_sub;             /* DEM subcycles per LBM step (Algorithm 1), >= 1              */
+    double lub_cut_n;      /* normal lubrication cut-off, Eq. (34): 2/3                   */
+    double lub_cut_tt;     /* tangential translation cut-off, Eq. (34): 1/2               */
+    double lub_cut_tr;     /* tangential rotation cut-off, Eq. (34): 1/2                  */
+    double lub_min_a;      /* delta_min = (a + b R) R, Eq. (56): a = 0.001                */
+    double lub_min_b;      /*                                   b = 0.00007               */
+    double gravity[3];     /* g; particles feel V (rho_p - rho_f) g (Sec. 4.1.1)          */
+    int lubrication;       /* 1 = apply Eqs. (25)-(33)                                    */
+    int tangential_lubrication; /* 1 = include Eqs. (30)-(33)                             */
+    int force_averaging;   /* 1 = average F^fp, T^fp over two steps (Sec. 4.2)            */
+    int fluid_counterforce;/* 1 = fluid body force -sum V (rho_p - 1) g / N_fluid         */
+    int fixed_particles;   /* 1 = particles keep position and velocity (no DEM)           */
+    int missing_links;     /* 1 = missing-link correction F_q = 2 w_q c_q (Sec. 2.2)       */
+} lbm_dem;
+
+/* Fill *relax and *dem with the paper's values (tau is set to 0.6). */
+lbm_status lbm_default_params(lbm_relax *relax, lbm_dem *dem);
+
+/* Device bytes that lbm_create_in_arena() needs for this box, storage format
+ * and particle capacity. */
+lbm_status lbm_required_bytes(const lbm_grid *grid, lbm_storage storage, int max_particles,
+                              size_t *bytes_out);
+
+/* Create a context on the current CUDA device. body_force is the fluid body
+ * force per unit volume (3 doubles, may be NULL for zero). cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream); all work of the context is
+ * queued on it. The fluid starts at rest with rho = 1 and no particles.
+ * Device memory is allocated by the library and released by lbm_destroy().
+ * Errors: LBM_ERR_INVALID (bad sizes, tau <= 1/2, non-positive max_particles),
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_grid *grid, const lbm_relax *relax, const double *body_force,
+                      const lbm_dem *dem, lbm_storage storage, int max_particles,
+                      void *cuda_stream, lbm_ctx **out);
+
+/* As lbm_create(), but every device buffer is carved from the caller-owned
+ * device allocation [arena, arena + arena_bytes), which must stay valid and
+ * untouched until lbm_destroy(). arena must be 256-byte aligned. */
+lbm_status lbm_create_in_arena(const lbm_grid *grid, const lbm_relax *relax,
+                               const double *body_force, const lbm_dem *dem,
+                               lbm_storage storage, int max_particles, void *cuda_stream,
+                               void *arena, size_t arena_bytes, lbm_ctx **out);
+
+/* Add n spheres (Sec. 2.2 mapping is applied at once). pos, vel, omega: n x 3
+ * doubles; radius, density: n doubles, density = rho_p / rho_f. Allowed only
+ * before the first lbm_step(). Errors: LBM_ERR_INVALID if a centre lies
+ * outside the box, a radius is < 1 cell, a density is <= 0, two spheres
+ * overlap (centre distance < R_i + R_j) or a sphere crosses a wall;
+ * LBM_ERR_CAPACITY if the total exceeds max_particles; LBM_ERR_STATE after the
+ * first step. *first_id_out (may be NULL) receives the index of the first new
+ * sphere; spheres are numbered in insertion order. */
+lbm_status lbm_add_spheres(lbm_ctx *ctx, int n, const double *pos, const double *vel,
+                           const double *omega, const double *radius, const double *density,
+                           int *first_id_out);
+
+/* Advance n_steps time steps of Algorithm 1 (asynchronous on the stream). */
+lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
+
+/* Copy particle state to host buffers of n_cap entries (x 3 doubles each where
+ * vector valued); any pointer may be NULL. force_hyd / torque_hyd receive the
+ * momentum-exchange force and torque F^fp, T^fp of Eqs. (16)-(17) of the last
+ * step, including the missing-link term, before averaging. *n_out (may be
+ * NULL) receives the particle count. Synchronises the stream. */
+lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *vel,
+                                  double *omega, double *force_hyd, double *torque_hyd,
+                                  int *n_out);
+
+/* Copy rho (cells doubles), u (3 x cells doubles, component-major: u_x block,
+ * then u_y, then u_z) and flags (cells bytes, LBM_FLAG_* bits) to host
+ * buffers; any pointer may be NULL. rho = sum_q f_q and u = (sum_q f_q c_q -
+ * a/2)/rho0 of the stored post-collision PDFs, with a the fluid body force of
+ * the last step; both are 0 in solid cells. Synchronises the stream. */
+lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho, double *u, unsigned char *flags);
+
+/* Copy the owning particle index of every cell (int32, -1 for a cell that has
+ * never been solid; for a fluid cell that was solid it holds the last owner). */
+lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);
+
+/* Copy / replace the post-collision PDFs f_q (unshifted values), 19 x cells
+ * doubles, direction-major (q = 0..18 in the order fixed by App. A). Values in
+ * solid cells are ignored by the method. Synchronises the stream. */
+lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *f);
+lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
+
+/* Wait for all queued work and report device-side errors (sticky). */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Device timing of lbm_step() by phase, with CUDA events recorded on the
+ * context stream between the launches of each step. Phases: 0 the fused
+ * stream/boundary/collision kernel (Eqs. (2), (14)-(17), (5)), 1 the force
+ * finalisation and averaging (Sec. 4.2), 2 the DEM subcycles (neighbour
+ * lists, lubrication, contact, Velocity Verlet), 3 the mapping update
+ * (Sec. 2.2), 4 the refill (Eq. (18)). lbm_profile(ctx, 1) clears the totals
+ * and starts recording; lbm_profile(ctx, 0) stops. lbm_profile_read()
+ * synchronises the stream and returns the summed milliseconds of the 5 phases
+ * and the number of timed steps. Recording costs a few event records per
+ * step; it is off by default. */
+lbm_status lbm_profile(lbm_ctx *ctx, int enable);
+lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
+
+/* Number of kernel launches this context has issued so far. */
+long long lbm_launch_count(const lbm_ctx *ctx);
+
+/* Human-readable text of the last error of ctx (never NULL; ctx may be NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Release the context and, for lbm_create(), its device memory. NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMDEM_H */

@@ -166,45 +166,44 @@ class Simulation:
         mu = RHO0 * viscosity(1.0 / p.tau)
         cut_max = max(p.lub_cut_n, p.lub_cut_tt, p.lub_cut_tr)
         seen = set()
-        for i in range(N):
-            for j in range(i + 1, N):
-                d = rel_vec(X[i], X[j], dom)
-                dist = math.sqrt(d @ d)
-                delta = dist - (R[i] + R[j])
-                key = (i, j)
-                if delta >= cut_max and delta >= 0.0:
-                    continue
-                n = d / dist
-                u_ij = U[i] - U[j]
-                if p.lubrication:
-                    dmin = lubrication_min_gap(0.5 * (R[i] + R[j]), p.lub_min_a, p.lub_min_b)
-                    Fi, Ti = lubrication_on_i(R[i], R[j], delta, n, u_ij, Om[i], Om[j], mu,
-                                              p.lub_cut_n, p.lub_cut_tt, p.lub_cut_tr, dmin,
-                                              p.tangential_lubrication)
-                    Fj, Tj = lubrication_on_i(R[j], R[i], delta, -n, -u_ij, Om[j], Om[i], mu,
-                                              p.lub_cut_n, p.lub_cut_tt, p.lub_cut_tr, dmin,
-                                              p.tangential_lubrication)
-                    F[i] += Fi
-                    T[i] += Ti
-                    F[j] += Fj
-                    T[j] += Tj
-                if delta < 0.0:
-                    ri = -0.5 * d
-                    rj = 0.5 * d
-                    u_cp = (U[i] + np.cross(Om[i], ri)) - (U[j] + np.cross(Om[j], rj))
-                    m_eff = m[i] * m[j] / (m[i] + m[j])
-                    Tc = collision_time(R[i] + R[j], p.Tc)
-                    kn, dn, kt, dt_ = contact_coefficients(m_eff, p.e_dry, Tc, p.nu_p)
-                    old = self.hist.get(key, np.zeros(3))
-                    Fn, Ft, new = contact_force(n, delta, u_cp, u_ij, kn, dn, kt, dt_, p.mu_p, old,
-                                                dt_p)
-                    F[i] += Fn + Ft
-                    F[j] -= Fn + Ft
-                    T[i] += np.cross(ri, Ft)
-                    T[j] += np.cross(rj, -Ft)
-                    if update_history:
-                        self.hist[key] = new
-                    seen.add(key)
+        for i, j in self._close_pairs(cut_max):
+            d = rel_vec(X[i], X[j], dom)
+            dist = math.sqrt(d @ d)
+            delta = dist - (R[i] + R[j])
+            key = (i, j)
+            if delta >= cut_max and delta >= 0.0:
+                continue
+            n = d / dist
+            u_ij = U[i] - U[j]
+            if p.lubrication:
+                dmin = lubrication_min_gap(0.5 * (R[i] + R[j]), p.lub_min_a, p.lub_min_b)
+                Fi, Ti = lubrication_on_i(R[i], R[j], delta, n, u_ij, Om[i], Om[j], mu,
+                                          p.lub_cut_n, p.lub_cut_tt, p.lub_cut_tr, dmin,
+                                          p.tangential_lubrication)
+                Fj, Tj = lubrication_on_i(R[j], R[i], delta, -n, -u_ij, Om[j], Om[i], mu,
+                                          p.lub_cut_n, p.lub_cut_tt, p.lub_cut_tr, dmin,
+                                          p.tangential_lubrication)
+                F[i] += Fi
+                T[i] += Ti
+                F[j] += Fj
+                T[j] += Tj
+            if delta < 0.0:
+                ri = -0.5 * d
+                rj = 0.5 * d
+                u_cp = (U[i] + np.cross(Om[i], ri)) - (U[j] + np.cross(Om[j], rj))
+                m_eff = m[i] * m[j] / (m[i] + m[j])
+                Tc = collision_time(R[i] + R[j], p.Tc)
+                kn, dn, kt, dt_ = contact_coefficients(m_eff, p.e_dry, Tc, p.nu_p)
+                old = self.hist.get(key, np.zeros(3))
+                Fn, Ft, new = contact_force(n, delta, u_cp, u_ij, kn, dn, kt, dt_, p.mu_p, old,
+                                            dt_p)
+                F[i] += Fn + Ft
+                F[j] -= Fn + Ft
+                T[i] += np.cross(ri, Ft)
+                T[j] += np.cross(rj, -Ft)
+                if update_history:
+                    self.hist[key] = new
+                seen.add(key)
         for a in range(3):
             if dom.periodic[a]:
                 continue
@@ -240,6 +239,24 @@ class Simulation:
         if update_history:
             self.hist = {k: v for k, v in self.hist.items() if k in seen}
         return F, T
+
+    def _close_pairs(self, cut_max):
+        """Pairs i < j whose surface gap may be below cut_max (a superset: the
+        exact test is repeated per pair), found with one vectorised distance
+        matrix so that far pairs, which add nothing, are not visited."""
+        X, R, dom = self.X, self.R, self.dom
+        N = len(R)
+        if N < 2:
+            return []
+        d = X[:, None, :] - X[None, :, :]
+        for a in range(3):
+            if dom.periodic[a]:
+                L = float(dom.shape[a])
+                d[..., a] = np.where(d[..., a] > 0.5 * L, d[..., a] - L, d[..., a])
+                d[..., a] = np.where(d[..., a] < -0.5 * L, d[..., a] + L, d[..., a])
+        gap = np.sqrt((d * d).sum(-1)) - (R[:, None] + R[None, :])
+        ii, jj = np.nonzero(np.triu(gap < cut_max + 1e-6, k=1))
+        return list(zip(ii.tolist(), jj.tolist()))
 
     def wrap_positions(self):
         for a in range(3):

@@ -1,0 +1,847 @@
+// api.cu -- C ABI of the library (declared in include/lbmdem.h): context
+// management, device memory layout, particle insertion and the per-step
+// launch sequence of Algorithm 1 (Sec. 4.2).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmdem.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace lbmdem;
+
+struct lbm_ctx {
+    Geom g{};
+    lbm_relax relax{};
+    lbm_dem dem{};
+    double a_user[3] = {0, 0, 0};
+    int storage = 1;
+    int max_particles = 0;
+    cudaStream_t stream = nullptr;
+    bool own_memory = false;
+    char* base = nullptr;
+    size_t bytes = 0;
+    size_t elem = 4;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t* flags = nullptr;
+    int* owner = nullptr;
+    int ntile[3] = {1, 1, 1};
+    long long ntiles = 1;
+    int* tile_count = nullptr;
+    int* tile_list = nullptr;
+    unsigned int* refill_list = nullptr;
+    int* refill_count = nullptr;
+    int refill_cap = 0;
+    unsigned long long* n_solid = nullptr;
+    int* status = nullptr;
+    double* accel = nullptr;
+    float* accel_f = nullptr;
+    unsigned int* near_list = nullptr;
+    int* near_count = nullptr;
+    int near_cap = 0;
+    double* scratch = nullptr;
+    long long scratch_cells = 0;
+    long long bin_cap = 1;
+    Particles P{};
+    int hcur = 0;
+    bool stepped = false;
+    long long launches = 0;
+    double ext_total[3] = {0, 0, 0};
+    double r_max = 0.0;
+    std::vector<double> hx, hR;    // host copies for insertion checks
+    std::string err;
+    // phase timing (lbm_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    long long prof_steps = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    g_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+size_t elem_size(lbm_storage s) {
+    switch (s) {
+        case LBM_STORE_F64: return 8;
+        case LBM_STORE_F32: return 4;
+        default: return 2;
+    }
+}
+
+// device memory layout: every piece 256-byte aligned, in a fixed order
+struct Layout {
+    size_t off[64];
+    size_t size[64];
+    int n = 0;
+    size_t total = 0;
+    int add(size_t bytes) {
+        off[n] = total;
+        size[n] = bytes;
+        total += align256(bytes ? bytes : 1);
+        return n++;
+    }
+};
+
+struct Sizes {
+    long long ncells;
+    int ntile[3];
+    long long ntiles;
+    int refill_cap;
+    long long scratch_cells;
+    long long bin_cap;
+};
+
+Sizes compute_sizes(const lbm_grid* g, int max_particles) {
+    Sizes s;
+    s.ncells = (long long)g->nx * g->ny * g->nz;
+    s.ntile[0] = (g->nx + TILE_X - 1) / TILE_X;
+    s.ntile[1] = (g->ny + TILE_Y - 1) / TILE_Y;
+    s.ntile[2] = (g->nz + TILE_Z - 1) / TILE_Z;
+    s.ntiles = (long long)s.ntile[0] * s.ntile[1] * s.ntile[2];
+    long long rc = 65536 + 1024LL * max_particles;
+    if (rc > s.ncells) rc = s.ncells;
+    s.refill_cap = (int)rc;
+    long long sc = s.ncells < (4LL << 20) ? s.ncells : (4LL << 20);
+    s.scratch_cells = sc;
+    long long bc = 4LL * max_particles + 64;
+    if (bc > s.ncells) bc = s.ncells;
+    s.bin_cap = bc;
+    return s;
+}
+
+void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Sizes& s) {
+    const size_t es = elem_size(st);
+    const size_t N = (size_t)s.ncells;
+    const size_t n = (size_t)np;
+    L.add(19 * N * es);                 // 0 f[0]
+    L.add(19 * N * es);                 // 1 f[1]
+    L.add(N);                           // 2 flags
+    L.add(4 * N);                       // 3 owner
+    L.add(4 * s.ntiles);                // 4 tile_count
+    L.add(4 * s.ntiles * TILE_CAP);     // 5 tile_list
+    L.add(4 * (size_t)s.refill_cap);    // 6 refill_list
+    L.add(4);                           // 7 refill_count
+    L.add(8);                           // 8 n_solid
+    L.add(4);                           // 9 status
+    L.add(8 * 3);                       // 10 accel
+    L.add(8 * 4 * (size_t)s.scratch_cells);  // 11 scratch
+    // particles
+    L.add(8 * 3 * n);  // 12 x
+    L.add(8 * 3 * n);  // 13 u
+    L.add(8 * 3 * n);  // 14 om
+    L.add(8 * n);      // 15 R
+    L.add(8 * n);      // 16 rho
+    L.add(8 * n);      // 17 m
+    L.add(8 * n);      // 18 I
+    L.add(8 * 3 * n);  // 19 F_prev
+    L.add(8 * 3 * n);  // 20 T_prev
+    L.add(8 * 3 * n);  // 21 F_new
+    L.add(8 * 3 * n);  // 22 T_new
+    L.add(8 * 6 * n);  // 23 acc_d
+    L.add(8 * 6 * n);  // 24 acc_i
+    L.add(8 * 6 * n);  // 25 fp
+    L.add(8 * 6 * n);  // 26 fp_old
+    L.add(8 * 6 * n);  // 27 fbar
+    L.add(sizeof(PartView) * n);                 // 28 view
+    L.add(4 * (size_t)s.bin_cap);                // 29 bin_count
+    L.add(4 * (size_t)s.bin_cap * BIN_CAP);      // 30 bin_list
+    L.add(4 * n);                                // 31 nbr_count
+    L.add(4 * n * NBR_CAP);                      // 32 nbr
+    for (int h = 0; h < 2; ++h) {
+        L.add(4 * n * HIST_CAP);                 // 33/38 hist_id
+        L.add(8 * 3 * n * HIST_CAP);             // 34/39 hist_d
+        L.add(4 * n);                            // 35/40 hist_n
+        L.add(8 * 3 * 6 * n);                    // 36/41 whist
+        L.add(6 * n);                            // 37/42 wact
+    }
+    L.add(4 * N);                                // 43 near_list
+    L.add(4);                                    // 44 near_count
+    L.add(4 * 3);                                // 45 accel_f
+    L.add(4 * 3 * n);                            // 46 xf
+    (void)g;
+}
+
+lbm_status validate(const lbm_grid* g, const lbm_relax* r, const lbm_dem* d, lbm_storage st,
+                    int max_particles) {
+    if (!g || !r || !d) return fail(nullptr, LBM_ERR_INVALID, "null parameter struct");
+    if (g->nx < 3 || g->ny < 3 || g->nz < 3) return fail(nullptr, LBM_ERR_INVALID, "box must be at least 3 cells per axis");
+    long long nc = (long long)g->nx * g->ny * g->nz;
+    if (nc >= (1LL << 31)) return fail(nullptr, LBM_ERR_INVALID, "box has 2^31 cells or more");
+    if (g->nz > 65535 || g->ny > 65535 * 2) return fail(nullptr, LBM_ERR_INVALID, "ny or nz too large");
+    if (!(r->tau > 0.5)) return fail(nullptr, LBM_ERR_INVALID, "tau must be > 1/2");
+    if (!(r->magic > 0.0) || !(r->lambda_b_shell > 0.0) || !(r->lambda_b_bulk > 0.0) || !(r->shell_width >= 0.0))
+        return fail(nullptr, LBM_ERR_INVALID, "magic, lambda_b must be > 0 and shell_width >= 0");
+    if (st < LBM_STORE_F64 || st > LBM_STORE_BF16) return fail(nullptr, LBM_ERR_INVALID, "unknown storage format");
+    if (max_particles < 0) return fail(nullptr, LBM_ERR_INVALID, "max_particles must be >= 0");
+    if (d->n_sub < 1) return fail(nullptr, LBM_ERR_INVALID, "n_sub must be >= 1");
+    if (!(d->e_dry > 0.0 && d->e_dry <= 1.0)) return fail(nullptr, LBM_ERR_INVALID, "e_dry must be in (0, 1]");
+    if (!(d->nu_p >= 0.0 && d->nu_p < 1.0)) return fail(nullptr, LBM_ERR_INVALID, "nu_p must be in [0, 1)");
+    if (!(d->mu_p >= 0.0)) return fail(nullptr, LBM_ERR_INVALID, "mu_p must be >= 0");
+    if (!(d->lub_cut_n > 0 && d->lub_cut_tt > 0 && d->lub_cut_tr > 0))
+        return fail(nullptr, LBM_ERR_INVALID, "lubrication cut-offs must be > 0");
+    return LBM_OK;
+}
+
+lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, const lbm_dem* d,
+                       lbm_storage st, int max_particles, void* stream, void* arena, size_t arena_bytes,
+                       lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    lbm_status v = validate(g, r, d, st, max_particles);
+    if (v != LBM_OK) return v;
+    lbm_ctx* ctx = new lbm_ctx();
+    ctx->relax = *r;
+    ctx->dem = *d;
+    ctx->storage = (int)st;
+    ctx->elem = elem_size(st);
+    ctx->max_particles = max_particles;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->g.n[0] = g->nx; ctx->g.n[1] = g->ny; ctx->g.n[2] = g->nz;
+    for (int a = 0; a < 3; ++a) {
+        ctx->g.per[a] = g->periodic[a] ? 1 : 0;
+        for (int c = 0; c < 3; ++c) {
+            ctx->g.wall_vel[0][a][c] = g->wall_vel_lo[a][c];
+            ctx->g.wall_vel[1][a][c] = g->wall_vel_hi[a][c];
+        }
+        ctx->a_user[a] = bf ? bf[a] : 0.0;
+    }
+    ctx->g.ncells = (long long)g->nx * g->ny * g->nz;
+    Sizes s = compute_sizes(g, max_particles);
+    Layout L;
+    build_layout(g, st, max_particles, L, s);
+    ctx->bytes = L.total;
+    if (arena) {
+        if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) {
+            delete ctx;
+            return fail(nullptr, LBM_ERR_INVALID, "arena must be 256-byte aligned");
+        }
+        if (arena_bytes < L.total) {
+            delete ctx;
+            return fail(nullptr, LBM_ERR_OOM, "arena smaller than lbm_required_bytes()");
+        }
+        ctx->base = static_cast<char*>(arena);
+        ctx->own_memory = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, LBM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        ctx->base = static_cast<char*>(p);
+        ctx->own_memory = true;
+    }
+    char* b = ctx->base;
+    auto at = [&](int k) { return (void*)(b + L.off[k]); };
+    ctx->f[0] = at(0);
+    ctx->f[1] = at(1);
+    ctx->flags = (uint8_t*)at(2);
+    ctx->owner = (int*)at(3);
+    for (int a = 0; a < 3; ++a) ctx->ntile[a] = s.ntile[a];
+    ctx->ntiles = s.ntiles;
+    ctx->tile_count = (int*)at(4);
+    ctx->tile_list = (int*)at(5);
+    ctx->refill_list = (unsigned int*)at(6);
+    ctx->refill_count = (int*)at(7);
+    ctx->refill_cap = s.refill_cap;
+    ctx->n_solid = (unsigned long long*)at(8);
+    ctx->status = (int*)at(9);
+    ctx->accel = (double*)at(10);
+    ctx->near_list = (unsigned int*)at(43);
+    ctx->near_count = (int*)at(44);
+    ctx->near_cap = (int)s.ncells;
+    ctx->accel_f = (float*)at(45);
+    ctx->P.xf = (float*)at(46);
+    ctx->scratch = (double*)at(11);
+    ctx->scratch_cells = s.scratch_cells;
+    ctx->bin_cap = s.bin_cap;
+    Particles& P = ctx->P;
+    P.n = 0;
+    P.x = (double*)at(12); P.u = (double*)at(13); P.om = (double*)at(14); P.R = (double*)at(15);
+    P.rho = (double*)at(16); P.m = (double*)at(17); P.I = (double*)at(18);
+    P.F_prev = (double*)at(19); P.T_prev = (double*)at(20); P.F_new = (double*)at(21); P.T_new = (double*)at(22);
+    P.acc_d = (double*)at(23); P.acc_i = (long long*)at(24);
+    P.fp = (double*)at(25); P.fp_old = (double*)at(26); P.fbar = (double*)at(27);
+    P.view = (PartView*)at(28);
+    P.bin_count = (int*)at(29); P.bin_list = (int*)at(30);
+    P.nbr_count = (int*)at(31); P.nbr = (int*)at(32);
+    for (int h = 0; h < 2; ++h) {
+        P.hist_id[h] = (int*)at(33 + 5 * h);
+        P.hist_d[h] = (double*)at(34 + 5 * h);
+        P.hist_n[h] = (int*)at(35 + 5 * h);
+        P.whist[h] = (double*)at(36 + 5 * h);
+        P.wact[h] = (unsigned char*)at(37 + 5 * h);
+    }
+    // initial state: fluid at rest with rho = 1 (shifted PDFs are zero), no particles
+    cudaStream_t sm = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemsetAsync(ctx->f[0], 0, L.size[0], sm);
+    e = e ? e : cudaMemsetAsync(ctx->f[1], 0, L.size[1], sm);
+    e = e ? e : cudaMemsetAsync(ctx->flags, 0, L.size[2], sm);
+    e = e ? e : cudaMemsetAsync(ctx->owner, 0xff, L.size[3], sm);
+    for (int k = 4; k < L.n && e == cudaSuccess; ++k)
+        if (k != 11) e = cudaMemsetAsync(b + L.off[k], 0, L.size[k] ? L.size[k] : 1, sm);
+    double acc0[3] = {ctx->a_user[0], ctx->a_user[1], ctx->a_user[2]};
+    float acc0f[3] = {(float)acc0[0], (float)acc0[1], (float)acc0[2]};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->accel, acc0, sizeof(acc0), cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->accel_f, acc0f, sizeof(acc0f), cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    if (e != cudaSuccess) {
+        if (ctx->own_memory) cudaFree(ctx->base);
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    }
+    // the wall-adjacent cells need the NEAR flag even without particles
+    MapParams mp{};
+    mp.g = ctx->g; mp.P = ctx->P; mp.flags = ctx->flags; mp.owner = ctx->owner;
+    for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
+    mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
+    mp.shell_width = ctx->relax.shell_width;
+    mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
+    mp.n_solid = ctx->n_solid; mp.status = ctx->status;
+    mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
+    launch_map(mp, sm);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    if (e != cudaSuccess) {
+        if (ctx->own_memory) cudaFree(ctx->base);
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, std::string("initial mapping: ") + cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+double s_minus_of(double s_nu, double magic) { return 1.0 / (0.5 + magic / (1.0 / s_nu - 0.5)); }
+double s_b_of(double s_nu, double lb) { return 1.0 / (0.5 + lb * (1.0 / s_nu - 0.5)); }
+
+MapParams map_params(lbm_ctx* ctx) {
+    MapParams mp{};
+    const int ts[3] = {TILE_X, TILE_Y, TILE_Z};
+    const double reach = ctx->r_max + std::fmax(ctx->relax.shell_width, 1.4142135623730951) + 0.02;
+    for (int a = 0; a < 3; ++a)
+        mp.small[a] = ctx->g.per[a] && ctx->g.n[a] <= 2.0 * reach + ts[a] + 2.0;
+    mp.g = ctx->g; mp.P = ctx->P; mp.flags = ctx->flags; mp.owner = ctx->owner;
+    for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
+    mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
+    mp.shell_width = ctx->relax.shell_width;
+    mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
+    mp.n_solid = ctx->n_solid; mp.status = ctx->status;
+    mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
+    return mp;
+}
+
+// remap all particles: clear tile lists and counters, scatter, map
+lbm_status remap(lbm_ctx* ctx) {
+    cudaStream_t sm = ctx->stream;
+    CK(cudaMemsetAsync(ctx->tile_count, 0, sizeof(int) * ctx->ntiles, sm));
+    CK(cudaMemsetAsync(ctx->refill_count, 0, sizeof(int), sm));
+    CK(cudaMemsetAsync(ctx->n_solid, 0, sizeof(unsigned long long), sm));
+    CK(cudaMemsetAsync(ctx->near_count, 0, sizeof(int), sm));
+    MapParams mp = map_params(ctx);
+    launch_tile_scatter(mp, sm);
+    launch_map(mp, sm);
+    ctx->launches += (ctx->P.n > 0 ? 1 : 0) + 1;
+    return LBM_OK;
+}
+
+DemParams dem_params(lbm_ctx* ctx) {
+    DemParams dp{};
+    dp.g = ctx->g;
+    dp.P = ctx->P;
+    const lbm_dem& d = ctx->dem;
+    dp.cut_max = std::fmax(d.lub_cut_n, std::fmax(d.lub_cut_tt, d.lub_cut_tr));
+    // bins no smaller than the largest interaction reach, at most bin_cap of them
+    const double bin_min = 2.0 * ctx->r_max + dp.cut_max + NBR_SKIN;
+    long long total = 1;
+    for (int a = 0; a < 3; ++a) {
+        int nb = (int)std::floor(ctx->g.n[a] / bin_min);
+        dp.nbins[a] = nb < 1 ? 1 : nb;
+        total *= dp.nbins[a];
+    }
+    while (total > ctx->bin_cap) {
+        int amax = 0;
+        for (int a = 1; a < 3; ++a)
+            if (dp.nbins[a] > dp.nbins[amax]) amax = a;
+        total /= dp.nbins[amax];
+        dp.nbins[amax] = dp.nbins[amax] / 2 > 0 ? dp.nbins[amax] / 2 : 1;
+        total *= dp.nbins[amax];
+    }
+    for (int a = 0; a < 3; ++a) dp.binsize[a] = (double)ctx->g.n[a] / dp.nbins[a];
+    dp.e_dry = d.e_dry; dp.Tc = d.Tc; dp.nu_p = d.nu_p; dp.mu_p = d.mu_p;
+    dp.cut_n = d.lub_cut_n; dp.cut_tt = d.lub_cut_tt; dp.cut_tr = d.lub_cut_tr;
+    dp.min_a = d.lub_min_a; dp.min_b = d.lub_min_b;
+    for (int a = 0; a < 3; ++a) dp.gravity[a] = d.gravity[a];
+    dp.mu_f = (ctx->relax.tau - 0.5) / 3.0;
+    dp.lubrication = d.lubrication;
+    dp.tangential = d.tangential_lubrication;
+    dp.dt = 1.0 / d.n_sub;
+    dp.status = ctx->status;
+    return dp;
+}
+
+// record the next profiling event on the context stream (no-op when off)
+cudaError_t prof_mark(lbm_ctx* ctx) {
+    if (!ctx->profiling) return cudaSuccess;
+    if (ctx->ev_used == ctx->events.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ctx->events.push_back(e);
+    }
+    return cudaEventRecord(ctx->events[ctx->ev_used++], ctx->stream);
+}
+
+lbm_status check_status(lbm_ctx* ctx) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st & ST_UNSTABLE) return fail(ctx, LBM_ERR_UNSTABLE, "density left (0.5, 1.5) or became NaN");
+    if (st & (ST_TILE_OVERFLOW | ST_NBR_OVERFLOW | ST_BIN_OVERFLOW | ST_REFILL_OVERFLOW | ST_HIST_OVERFLOW |
+              ST_FIXED_OVERFLOW)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "device list capacity exceeded (status bits 0x%x)", st);
+        return fail(ctx, LBM_ERR_CAPACITY, buf);
+    }
+    if (st & ST_FAST_PARTICLE) return fail(ctx, LBM_ERR_UNSTABLE, "particle speed above 0.5 cells per step");
+    return LBM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+lbm_status lbm_default_params(lbm_relax* relax, lbm_dem* dem) {
+    if (relax) {
+        relax->tau = 0.6;
+        relax->magic = 3.0 / 16.0;
+        relax->lambda_b_shell = 100.0;
+        relax->lambda_b_bulk = 1.0;
+        relax->shell_width = 2.0;
+    }
+    if (dem) {
+        dem->e_dry = 0.97;
+        dem->Tc = 0.0;
+        dem->nu_p = 0.23;
+        dem->mu_p = 0.15;
+        dem->n_sub = 10;
+        dem->lub_cut_n = 2.0 / 3.0;
+        dem->lub_cut_tt = 0.5;
+        dem->lub_cut_tr = 0.5;
+        dem->lub_min_a = 0.001;
+        dem->lub_min_b = 0.00007;
+        dem->gravity[0] = dem->gravity[1] = dem->gravity[2] = 0.0;
+        dem->lubrication = 1;
+        dem->tangential_lubrication = 1;
+        dem->force_averaging = 1;
+        dem->fluid_counterforce = 0;
+        dem->fixed_particles = 0;
+        dem->missing_links = 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_required_bytes(const lbm_grid* grid, lbm_storage storage, int max_particles, size_t* bytes_out) {
+    if (!grid || !bytes_out || max_particles < 0 || grid->nx < 3 || grid->ny < 3 || grid->nz < 3)
+        return fail(nullptr, LBM_ERR_INVALID, "invalid arguments");
+    Sizes s = compute_sizes(grid, max_particles);
+    Layout L;
+    build_layout(grid, storage, max_particles, L, s);
+    *bytes_out = L.total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_grid* grid, const lbm_relax* relax, const double* body_force, const lbm_dem* dem,
+                      lbm_storage storage, int max_particles, void* cuda_stream, lbm_ctx** out) {
+    return create_impl(grid, relax, body_force, dem, storage, max_particles, cuda_stream, nullptr, 0, out);
+}
+
+lbm_status lbm_create_in_arena(const lbm_grid* grid, const lbm_relax* relax, const double* body_force,
+                               const lbm_dem* dem, lbm_storage storage, int max_particles, void* cuda_stream,
+                               void* arena, size_t arena_bytes, lbm_ctx** out) {
+    if (!arena) return fail(nullptr, LBM_ERR_INVALID, "arena is NULL");
+    return create_impl(grid, relax, body_force, dem, storage, max_particles, cuda_stream, arena, arena_bytes, out);
+}
+
+lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double* vel, const double* omega,
+                           const double* radius, const double* density, int* first_id_out) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (ctx->stepped) return fail(ctx, LBM_ERR_STATE, "spheres can only be added before the first step");
+    if (n < 0 || (n > 0 && (!pos || !radius || !density))) return fail(ctx, LBM_ERR_INVALID, "invalid arrays");
+    if (ctx->P.n + n > ctx->max_particles) return fail(ctx, LBM_ERR_CAPACITY, "max_particles exceeded");
+    const int n0 = ctx->P.n;
+    std::vector<double> hx(ctx->hx), hR(ctx->hR);
+    for (int k = 0; k < n; ++k) {
+        const double R = radius[k], rho = density[k];
+        if (!(R >= 1.0)) return fail(ctx, LBM_ERR_INVALID, "radius must be >= 1 cell");
+        if (!(rho > 0.0)) return fail(ctx, LBM_ERR_INVALID, "density ratio must be > 0");
+        for (int a = 0; a < 3; ++a) {
+            const double x = pos[3 * k + a];
+            const double L = ctx->g.n[a];
+            if (!(x >= 0.0 && x < L)) return fail(ctx, LBM_ERR_INVALID, "sphere centre outside the box");
+            if (!ctx->g.per[a] && (x - R < 0.0 || x + R > L))
+                return fail(ctx, LBM_ERR_INVALID, "sphere crosses a wall");
+            if (ctx->g.per[a] && 2.0 * R >= L) return fail(ctx, LBM_ERR_INVALID, "sphere wider than a periodic box");
+        }
+        const int m = (int)hR.size();
+        for (int j = 0; j < m; ++j) {
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                double d = pos[3 * k + a] - hx[3 * j + a];
+                if (ctx->g.per[a]) {
+                    const double L = ctx->g.n[a];
+                    if (d > 0.5 * L) d -= L;
+                    if (d < -0.5 * L) d += L;
+                }
+                d2 += d * d;
+            }
+            const double rr = R + hR[j];
+            if (d2 < rr * rr) return fail(ctx, LBM_ERR_INVALID, "spheres overlap");
+        }
+        for (int a = 0; a < 3; ++a) hx.push_back(pos[3 * k + a]);
+        hR.push_back(R);
+    }
+    if (n == 0) {
+        if (first_id_out) *first_id_out = n0;
+        return LBM_OK;
+    }
+    const double pi = 3.14159265358979323846;
+    std::vector<double> x(3 * n), u(3 * n, 0.0), om(3 * n, 0.0), R(n), rho(n), m(n), I(n);
+    for (int k = 0; k < n; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            x[3 * k + a] = pos[3 * k + a];
+            if (vel) u[3 * k + a] = vel[3 * k + a];
+            if (omega) om[3 * k + a] = omega[3 * k + a];
+        }
+        R[k] = radius[k];
+        rho[k] = density[k];
+        const double D = 2.0 * R[k];
+        const double V = pi * D * D * D / 6.0;
+        m[k] = rho[k] * V;
+        I[k] = 0.4 * m[k] * R[k] * R[k];
+        for (int a = 0; a < 3; ++a) ctx->ext_total[a] += V * (rho[k] - 1.0) * ctx->dem.gravity[a];
+        if (R[k] > ctx->r_max) ctx->r_max = R[k];
+    }
+    cudaStream_t sm = ctx->stream;
+    Particles& P = ctx->P;
+    CK(cudaMemcpyAsync(P.x + 3 * n0, x.data(), 8 * 3 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.u + 3 * n0, u.data(), 8 * 3 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.om + 3 * n0, om.data(), 8 * 3 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.R + n0, R.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.rho + n0, rho.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.m + n0, m.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.I + n0, I.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    P.n = n0 + n;
+    ctx->hx.swap(hx);
+    ctx->hR.swap(hR);
+    launch_view_update(P, sm);
+    ctx->launches += 1;
+    lbm_status s = remap(ctx);
+    if (s != LBM_OK) return s;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(sm));
+    if (first_id_out) *first_id_out = n0;
+    return check_status(ctx);
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (n_steps < 0) return fail(ctx, LBM_ERR_INVALID, "n_steps must be >= 0");
+    cudaStream_t sm = ctx->stream;
+    const lbm_relax& r = ctx->relax;
+    const lbm_dem& d = ctx->dem;
+    const double s_nu = 1.0 / r.tau;
+    const bool move = ctx->P.n > 0 && !d.fixed_particles;
+    DemParams dp = dem_params(ctx);
+    for (int step = 0; step < n_steps; ++step) {
+        const bool first = !ctx->stepped;
+        if (first) {
+            ctx->stepped = true;
+            if (move) {
+                // F(t = 0) for the first Velocity-Verlet position update needs the
+                // neighbour lists of the initial positions
+                dp.hin = ctx->hcur;
+                dp.hout = 1 - ctx->hcur;
+                dp.P = ctx->P;
+                CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
+                launch_bins(dp, sm);
+                launch_neighbours(dp, sm);
+                launch_dem_force(dp, 1, sm);
+                ctx->launches += 3;
+            }
+        }
+        // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
+        CK(prof_mark(ctx));
+        LbmStepParams lp{};
+        lp.storage = ctx->storage;
+        lp.src = ctx->f[ctx->cur];
+        lp.dst = ctx->f[1 - ctx->cur];
+        lp.flags = ctx->flags;
+        lp.owner = ctx->owner;
+        lp.g = ctx->g;
+        lp.s_plus = s_nu;
+        lp.s_minus = s_minus_of(s_nu, r.magic);
+        lp.s_b_shell = s_b_of(s_nu, r.lambda_b_shell);
+        lp.s_b_bulk = s_b_of(s_nu, r.lambda_b_bulk);
+        lp.bulk_corr = r.lambda_b_bulk != 1.0;
+        for (int a = 0; a < 3; ++a) {
+            lp.a_user[a] = ctx->a_user[a];
+            lp.ext_total[a] = ctx->ext_total[a];
+        }
+        lp.n_solid = ctx->n_solid;
+        lp.counterforce = d.fluid_counterforce && ctx->P.n > 0;
+        lp.P = ctx->P;
+        lp.missing_links = d.missing_links && ctx->P.n > 0;
+        lp.status = ctx->status;
+        lp.near_list = ctx->near_list;
+        lp.near_count = ctx->near_count;
+        lp.near_cap = ctx->near_cap;
+        lp.near_blocks = ctx->P.n > 0 ? 152 * 8 : 1;
+        lp.accel_d = ctx->accel;
+        lp.accel_f = ctx->accel_f;
+        launch_lbm_step(lp, sm);
+        CK(prof_mark(ctx));
+        FinalizeParams fpp{};
+        fpp.P = ctx->P;
+        fpp.use_fixed = ctx->storage != LBM_STORE_F64;
+        fpp.first_step = first;
+        fpp.averaging = d.force_averaging;
+        launch_finalize(fpp, sm);
+        ctx->launches += 2 + (ctx->P.n > 0 ? 1 : 0);
+        CK(prof_mark(ctx));
+        if (move) {
+            // Algorithm 1, lines 4-10: DEM subcycles
+            dp.P = ctx->P;
+            CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
+            launch_bins(dp, sm);
+            launch_neighbours(dp, sm);
+            launch_dem_position(dp, sm);
+            ctx->launches += 3;
+            for (int s = 0; s < d.n_sub; ++s) {
+                dp.hin = ctx->hcur;
+                dp.hout = 1 - ctx->hcur;
+                launch_dem_force(dp, 0, sm);
+                ctx->hcur = 1 - ctx->hcur;
+                launch_dem_velocity(dp, s == d.n_sub - 1, sm);
+                ctx->launches += 2;
+            }
+            CK(prof_mark(ctx));
+            // Algorithm 1, line 11: mapping update and refill
+            lbm_status st = remap(ctx);
+            if (st != LBM_OK) return st;
+            CK(prof_mark(ctx));
+            RefillParams rp{};
+            rp.storage = ctx->storage;
+            rp.f = ctx->f[1 - ctx->cur];
+            rp.flags = ctx->flags;
+            rp.owner = ctx->owner;
+            rp.g = ctx->g;
+            rp.P = ctx->P;
+            rp.list = ctx->refill_list;
+            rp.count = ctx->refill_count;
+            rp.cap = ctx->refill_cap;
+            rp.s_nu = s_nu;
+            rp.accel = ctx->accel;
+            launch_refill(rp, sm);
+            ctx->launches += 1;
+            CK(prof_mark(ctx));
+        } else {
+            CK(prof_mark(ctx));
+            CK(prof_mark(ctx));
+            CK(prof_mark(ctx));
+        }
+        if (ctx->profiling) ctx->prof_steps += 1;
+        ctx->cur = 1 - ctx->cur;
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* ctx) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_status(ctx);
+}
+
+lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* vel, double* omega,
+                                  double* force_hyd, double* torque_hyd, int* n_out) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    const int n = ctx->P.n;
+    if (n_out) *n_out = n;
+    if (n_cap < n && (pos || vel || omega || force_hyd || torque_hyd))
+        return fail(ctx, LBM_ERR_INVALID, "n_cap smaller than the particle count");
+    cudaStream_t sm = ctx->stream;
+    if (n > 0) {
+        if (pos) CK(cudaMemcpyAsync(pos, ctx->P.x, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+        if (vel) CK(cudaMemcpyAsync(vel, ctx->P.u, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+        if (omega) CK(cudaMemcpyAsync(omega, ctx->P.om, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    }
+    std::vector<double> fp;
+    if (n > 0 && (force_hyd || torque_hyd)) {
+        fp.resize(6 * (size_t)n);
+        CK(cudaMemcpyAsync(fp.data(), ctx->P.fp, 48 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    }
+    CK(cudaStreamSynchronize(sm));
+    for (int i = 0; i < n && !fp.empty(); ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (force_hyd) force_hyd[3 * i + a] = fp[6 * i + a];
+            if (torque_hyd) torque_hyd[3 * i + a] = fp[6 * i + 3 + a];
+        }
+    return check_status(ctx);
+}
+
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, unsigned char* flags) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    cudaStream_t sm = ctx->stream;
+    const long long N = ctx->g.ncells;
+    if (flags) CK(cudaMemcpyAsync(flags, ctx->flags, (size_t)N, cudaMemcpyDeviceToHost, sm));
+    if (rho || u) {
+        std::vector<double> buf(4 * (size_t)ctx->scratch_cells);
+        for (long long first = 0; first < N; first += ctx->scratch_cells) {
+            const long long cnt = (N - first) < ctx->scratch_cells ? (N - first) : ctx->scratch_cells;
+            FieldsParams fp{};
+            fp.storage = ctx->storage;
+            fp.f = ctx->f[ctx->cur];
+            fp.flags = ctx->flags;
+            fp.g = ctx->g;
+            fp.first_cell = first;
+            fp.count = cnt;
+            fp.accel = ctx->accel;
+            fp.out = ctx->scratch;
+            launch_fields(fp, sm);
+            ctx->launches += 1;
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(buf.data(), ctx->scratch, 32 * (size_t)cnt, cudaMemcpyDeviceToHost, sm));
+            CK(cudaStreamSynchronize(sm));
+            if (rho) std::memcpy(rho + first, buf.data(), 8 * (size_t)cnt);
+            if (u)
+                for (int c = 0; c < 3; ++c)
+                    std::memcpy(u + (size_t)c * N + first, buf.data() + (size_t)(c + 1) * cnt, 8 * (size_t)cnt);
+        }
+    }
+    CK(cudaStreamSynchronize(sm));
+    return check_status(ctx);
+}
+
+lbm_status lbm_get_owner(lbm_ctx* ctx, int* owner) {
+    if (!ctx || !owner) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    CK(cudaMemcpyAsync(owner, ctx->owner, 4 * (size_t)ctx->g.ncells, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+static double w_of(int q) { return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f) {
+    if (!ctx || !f) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)ctx->g.ncells;
+    std::vector<char> raw(19 * N * ctx->elem);
+    CK(cudaMemcpyAsync(raw.data(), ctx->f[ctx->cur], raw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < 19; ++q) {
+        const double w = w_of(q);
+        for (size_t k = 0; k < N; ++k) {
+            const size_t j = q * N + k;
+            double v;
+            switch (ctx->storage) {
+                case LBM_STORE_F64: v = reinterpret_cast<const double*>(raw.data())[j]; break;
+                case LBM_STORE_F32: v = reinterpret_cast<const float*>(raw.data())[j]; break;
+                case LBM_STORE_F16: v = __half2float(reinterpret_cast<const __half*>(raw.data())[j]); break;
+                default: v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw.data())[j]); break;
+            }
+            f[j] = v + w;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f) {
+    if (!ctx || !f) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)ctx->g.ncells;
+    std::vector<char> raw(19 * N * ctx->elem);
+    for (int q = 0; q < 19; ++q) {
+        const double w = w_of(q);
+        for (size_t k = 0; k < N; ++k) {
+            const size_t j = q * N + k;
+            const double v = f[j] - w;
+            switch (ctx->storage) {
+                case LBM_STORE_F64: reinterpret_cast<double*>(raw.data())[j] = v; break;
+                case LBM_STORE_F32: reinterpret_cast<float*>(raw.data())[j] = (float)v; break;
+                case LBM_STORE_F16: reinterpret_cast<__half*>(raw.data())[j] = __float2half_rn((float)v); break;
+                default: reinterpret_cast<__nv_bfloat16*>(raw.data())[j] = __float2bfloat16_rn((float)v); break;
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->f[ctx->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_ctx* ctx, int enable) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (enable) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->ev_used = 0;
+        ctx->prof_steps = 0;
+    }
+    ctx->profiling = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* ctx, double* phase_ms, long long* steps) {
+    if (!ctx || !phase_ms) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 5; ++k) phase_ms[k] = 0.0;
+    for (size_t b = 0; b + 6 <= ctx->ev_used; b += 6)
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->events[b + k], ctx->events[b + k + 1]));
+            phase_ms[k] += ms;
+        }
+    if (steps) *steps = ctx->prof_steps;
+    return LBM_OK;
+}
+
+long long lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_err.c_str();
+}
+
+void lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    if (ctx->own_memory && ctx->base) cudaFree(ctx->base);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,452 @@
+// dem.cu -- particle side of Algorithm 1 in float64: force finalisation and
+// two-step averaging of the momentum-exchange force (Sec. 4.2), neighbour
+// search, lubrication correction (Eqs. (25)-(33)), linear spring-dashpot
+// contact with Coulomb-limited tangential spring (Eqs. (39)-(52)) and the
+// Velocity-Verlet subcycles (Eqs. (37)-(38)).
+//
+// One thread per particle gathers every interaction of its particle, so no
+// force atomics are needed; a pair is evaluated by both partners with exactly
+// mirrored operands (n_ji = -n_ij, u_ji = -u_ij, ...), which makes the pair
+// forces exactly opposite. Each particle keeps its own copy of the
+// tangential spring of every active contact (double buffered per subcycle).
+#include "common.cuh"
+#include "launch.h"
+
+namespace lbmdem {
+
+struct V3 {
+    double x, y, z;
+};
+__device__ __forceinline__ V3 mk(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 ld3(const double* p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
+__device__ __forceinline__ void st3(double* p, int i, V3 v) {
+    p[3 * i] = v.x;
+    p[3 * i + 1] = v.y;
+    p[3 * i + 2] = v.z;
+}
+__device__ __forceinline__ float mimgf(float d, int n, int per) {
+    if (per) {
+        const float half = 0.5f * (float)n;
+        if (d > half) d -= (float)n;
+        if (d < -half) d += (float)n;
+    }
+    return d;
+}
+__device__ __forceinline__ double mimg(double d, int n, int per) {
+    if (per) {
+        double half = 0.5 * (double)n;
+        if (d > half) d -= (double)n;
+        if (d < -half) d += (double)n;
+    }
+    return d;
+}
+
+// ------------------------------------------------------------ particle view
+
+__global__ void view_kernel(const Particles P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    PartView v;
+    for (int d = 0; d < 3; ++d) {
+        const double x = P.x[3 * i + d];
+        const double b = floor(x);
+        v.base[d] = (int)b;
+        v.frac[d] = (float)(x - b);
+        v.u[d] = (float)P.u[3 * i + d];
+        v.om[d] = (float)P.om[3 * i + d];
+        P.xf[3 * i + d] = (float)x;
+    }
+    v.R = (float)P.R[i];
+    v.pad = 0.f;
+    P.view[i] = v;
+}
+
+void launch_view_update(const Particles& P, cudaStream_t st) {
+    if (P.n == 0) return;
+    view_kernel<<<(P.n + 127) / 128, 128, 0, st>>>(P);
+}
+
+// ------------------------------------------------------------ finalisation
+
+__global__ void finalize_kernel(const FinalizeParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    for (int c = 0; c < 6; ++c) {
+        double v;
+        if (p.use_fixed) {
+            v = (double)p.P.acc_i[6 * i + c] * (1.0 / FIX_SCALE);
+            p.P.acc_i[6 * i + c] = 0;
+        } else {
+            v = p.P.acc_d[6 * i + c];
+            p.P.acc_d[6 * i + c] = 0.0;
+        }
+        const double old = p.first_step ? v : p.P.fp_old[6 * i + c];
+        p.P.fp[6 * i + c] = v;
+        p.P.fbar[6 * i + c] = p.averaging ? 0.5 * (v + old) : v;
+        p.P.fp_old[6 * i + c] = v;
+    }
+}
+
+void launch_finalize(const FinalizeParams& p, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    finalize_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+}
+
+// ------------------------------------------------------------ neighbour bins
+
+__device__ __forceinline__ int bin_coord(float x, float bs, int nb) {
+    int b = (int)(x / bs);
+    return b < 0 ? 0 : (b >= nb ? nb - 1 : b);
+}
+
+__global__ void bin_fill_kernel(const DemParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    int b[3];
+    for (int d = 0; d < 3; ++d) b[d] = bin_coord(p.P.xf[3 * i + d], (float)p.binsize[d], p.nbins[d]);
+    const long long bi = ((long long)b[2] * p.nbins[1] + b[1]) * p.nbins[0] + b[0];
+    const int slot = atomicAdd(p.P.bin_count + bi, 1);
+    if (slot < BIN_CAP) p.P.bin_list[bi * BIN_CAP + slot] = i;
+    else atomicOr(p.status, ST_BIN_OVERFLOW);
+}
+
+void launch_bins(const DemParams& p, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    bin_fill_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+}
+
+__global__ void neighbour_kernel(const DemParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    const float xi[3] = {p.P.xf[3 * i], p.P.xf[3 * i + 1], p.P.xf[3 * i + 2]};
+    const float Ri = (float)p.P.R[i];
+    const float extra = (float)(p.cut_max + NBR_SKIN) + 0.01f;
+    int b[3], lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        b[d] = bin_coord(xi[d], (float)p.binsize[d], p.nbins[d]);
+        if (p.nbins[d] < 3) { lo[d] = 0; hi[d] = p.nbins[d] - 1; }
+        else if (p.g.per[d]) { lo[d] = b[d] - 1; hi[d] = b[d] + 1; }
+        else { lo[d] = b[d] > 0 ? b[d] - 1 : 0; hi[d] = b[d] < p.nbins[d] - 1 ? b[d] + 1 : b[d]; }
+    }
+    int cnt = 0;
+    for (int bz = lo[2]; bz <= hi[2]; ++bz)
+        for (int by = lo[1]; by <= hi[1]; ++by)
+            for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                const int wx = (p.nbins[0] >= 3) ? wrap_idx(bx, p.nbins[0]) : bx;
+                const int wy = (p.nbins[1] >= 3) ? wrap_idx(by, p.nbins[1]) : by;
+                const int wz = (p.nbins[2] >= 3) ? wrap_idx(bz, p.nbins[2]) : bz;
+                const long long bi = ((long long)wz * p.nbins[1] + wy) * p.nbins[0] + wx;
+                const int nb = min(p.P.bin_count[bi], BIN_CAP);
+                for (int k = 0; k < nb; ++k) {
+                    const int j = p.P.bin_list[bi * BIN_CAP + k];
+                    if (j == i) continue;
+                    float d2 = 0.f;
+                    for (int d = 0; d < 3; ++d) {
+                        const float dd = mimgf(xi[d] - p.P.xf[3 * j + d], p.g.n[d], p.g.per[d]);
+                        d2 += dd * dd;
+                    }
+                    const float reach = Ri + (float)p.P.R[j] + extra;
+                    if (d2 < reach * reach) {
+                        if (cnt < NBR_CAP) p.P.nbr[i * NBR_CAP + cnt] = j;
+                        ++cnt;
+                    }
+                }
+            }
+    if (cnt > NBR_CAP) {
+        atomicOr(p.status, ST_NBR_OVERFLOW);
+        cnt = NBR_CAP;
+    }
+    p.P.nbr_count[i] = cnt;
+}
+
+void launch_neighbours(const DemParams& p, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    neighbour_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+}
+
+// ------------------------------------------------------------ Velocity Verlet
+
+__device__ __forceinline__ double wrap_pos(double x, int n, int per) {
+    if (per) {
+        const double L = (double)n;
+        if (x >= L) x -= L;
+        if (x < 0.0) x += L;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void position_update(const DemParams& p, int i) {
+    // Eq. (37): x += dt u + dt^2 / (2 m) F
+    const double m = p.P.m[i];
+    const double dt = p.dt;
+    const double c = dt * dt / (2.0 * m);
+    for (int d = 0; d < 3; ++d) {
+        const double x = wrap_pos(p.P.x[3 * i + d] + dt * p.P.u[3 * i + d] + c * p.P.F_prev[3 * i + d],
+                                  p.g.n[d], p.g.per[d]);
+        p.P.x[3 * i + d] = x;
+        p.P.xf[3 * i + d] = (float)x;
+    }
+}
+
+__global__ void position_kernel(const DemParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    position_update(p, i);
+}
+
+void launch_dem_position(const DemParams& p, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    position_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+}
+
+__global__ void velocity_kernel(const DemParams p, int last) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    // Eq. (38) for u and its rotational analogue for omega
+    const double m = p.P.m[i], I = p.P.I[i];
+    const double cu = p.dt / (2.0 * m), co = p.dt / (2.0 * I);
+    double usq = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double Fn = p.P.F_new[3 * i + d], Tn = p.P.T_new[3 * i + d];
+        const double u = p.P.u[3 * i + d] + cu * (p.P.F_prev[3 * i + d] + Fn);
+        p.P.u[3 * i + d] = u;
+        p.P.om[3 * i + d] = p.P.om[3 * i + d] + co * (p.P.T_prev[3 * i + d] + Tn);
+        p.P.F_prev[3 * i + d] = Fn;
+        p.P.T_prev[3 * i + d] = Tn;
+        usq += u * u;
+    }
+    if (!(usq < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
+    if (!last) {
+        position_update(p, i);
+    } else {
+        PartView v;
+        for (int d = 0; d < 3; ++d) {
+            const double x = p.P.x[3 * i + d];
+            const double b = floor(x);
+            v.base[d] = (int)b;
+            v.frac[d] = (float)(x - b);
+            v.u[d] = (float)p.P.u[3 * i + d];
+            v.om[d] = (float)p.P.om[3 * i + d];
+        }
+        v.R = (float)p.P.R[i];
+        v.pad = 0.f;
+        p.P.view[i] = v;
+    }
+}
+
+void launch_dem_velocity(const DemParams& p, int last, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    velocity_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p, last);
+}
+
+// ------------------------------------------------------------ interaction laws
+
+// lubrication force and torque on i due to j (Rj <= 0: plane wall), Eqs. (27)-(33)
+__device__ void lubrication_on_i(const DemParams& p, double Ri, double Rj, double delta, V3 n, V3 uij,
+                                 V3 omi, V3 omj, double dmin, V3& F, V3& T) {
+    const double pi = 3.14159265358979323846;
+    const double mu = p.mu_f;
+    const double dl = delta > dmin ? delta : dmin;
+    const V3 un = dot(uij, n) * n;
+    const V3 ut = uij - un;
+    double c_n, c_ftt, c_ttt, c_ftr, c_ttr;
+    V3 om_ftr, om_ttr;
+    if (Rj <= 0.0) {
+        c_n = 1.0; c_ftt = 8.0 / 15.0; c_ttt = 1.0 / 10.0; c_ftr = 2.0 / 15.0; c_ttr = 2.0 / 5.0;
+        om_ftr = omi;
+        om_ttr = omi;
+    } else {
+        const double k = Rj / Ri;
+        const double k1 = 1.0 + k;
+        c_n = k * k / (k1 * k1);
+        c_ftt = 4.0 * k * (2.0 + k + 2.0 * k * k) / (15.0 * k1 * k1 * k1);
+        c_ttt = k * (4.0 + k) / (10.0 * k1 * k1);
+        c_ftr = 2.0 * k * k / (15.0 * k1 * k1);
+        c_ttr = 2.0 * k / (5.0 * k1);
+        const V3 oms = omi + omj;
+        om_ftr = oms + (4.0 / k) * omi + (4.0 * k) * omj;
+        om_ttr = omi + (k / 4.0) * omj;
+    }
+    if (delta > 0.0 && delta < p.cut_n)
+        F = F + (-6.0 * pi * mu * Ri * Ri * c_n * (1.0 / dl - 1.0 / p.cut_n)) * un;
+    if (p.tangential && delta > 0.0 && delta < p.cut_tt) {
+        const double lg = log(dl / p.cut_tt);
+        F = F + (6.0 * pi * mu * Ri * c_ftt * lg) * ut;
+        T = T + (8.0 * pi * mu * Ri * Ri * c_ttt * lg) * cross(uij, n);
+    }
+    if (p.tangential && delta > 0.0 && delta < p.cut_tr) {
+        const double lg = log(dl / p.cut_tr);
+        F = F + (-6.0 * pi * mu * Ri * Ri * c_ftr * lg) * cross(om_ftr, n);
+        T = T + (8.0 * pi * mu * Ri * Ri * Ri * c_ttr * lg) * (om_ttr - dot(om_ttr, n) * n);
+    }
+}
+
+// normal + Coulomb-limited tangential contact force on i, Eqs. (41)-(50)
+__device__ void contact_force(const DemParams& p, V3 n, double delta, V3 ucp, V3 uij, double m_eff,
+                              double Tc, V3 dt_old, V3& Fn, V3& Ft, V3& dt_new) {
+    const double pi = 3.14159265358979323846;
+    const double le = log(p.e_dry);
+    const double kn = m_eff * (pi * pi + le * le) / (Tc * Tc);
+    const double dn = -2.0 * m_eff * le / Tc;
+    const double kappa = 2.0 * (1.0 - p.nu_p) / (2.0 - p.nu_p);
+    const double kt = kappa * kn, dtg = sqrt(kappa) * dn;
+    const V3 un = dot(uij, n) * n;
+    const V3 ut = ucp - un;
+    Fn = (-kn * delta) * n - dn * un;
+    const V3 proj = dt_old - dot(dt_old, n) * n;
+    const double lp = sqrt(dot(proj, proj));
+    const V3 rot = lp > 0.0 ? (sqrt(dot(dt_old, dt_old)) / lp) * proj : mk(0, 0, 0);
+    const V3 Fsd = (-kt) * rot - dtg * ut;
+    const double fc = p.mu_p * sqrt(dot(Fn, Fn));
+    const double lsd = sqrt(dot(Fsd, Fsd));
+    if (lsd < fc) {
+        Ft = Fsd;
+        dt_new = rot + p.dt * ut;
+    } else {
+        const V3 t = lsd > 0.0 ? (1.0 / lsd) * Fsd : mk(0, 0, 0);
+        Ft = fc * t;
+        dt_new = (-1.0 / kt) * (fc * t + dtg * ut);
+    }
+}
+
+__device__ __forceinline__ double collision_time(double diameter, double Tc) {
+    return Tc > 0.0 ? Tc : 2.31 * diameter * 1.7320508075688772;
+}
+
+__global__ void force_kernel(const DemParams p, int init) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P.n) return;
+    const Particles& P = p.P;
+    const V3 xi = ld3(P.x, i), ui = ld3(P.u, i), omi = ld3(P.om, i);
+    const double Ri = P.R[i], mi = P.m[i];
+    const double vol = P.m[i] / P.rho[i];
+    V3 F = mk(P.fbar[6 * i], P.fbar[6 * i + 1], P.fbar[6 * i + 2]) +
+           (vol * (P.rho[i] - 1.0)) * mk(p.gravity[0], p.gravity[1], p.gravity[2]);
+    V3 T = mk(P.fbar[6 * i + 3], P.fbar[6 * i + 4], P.fbar[6 * i + 5]);
+    const int hin = p.hin, hout = p.hout;
+    const int nin = P.hist_n[hin][i];
+    int nout = 0;
+    const int nn = P.nbr_count[i];
+    const float xif[3] = {P.xf[3 * i], P.xf[3 * i + 1], P.xf[3 * i + 2]};
+    const float reach_pad = (float)p.cut_max + 1e-3f;
+    for (int k = 0; k < nn; ++k) {
+        const int j = P.nbr[i * NBR_CAP + k];
+        {
+            // float32 prefilter: float positions are within 1e-4 of the float64
+            // ones, so a gap above cut_max + 1e-3 here is above cut_max exactly
+            float d2 = 0.f;
+            for (int d = 0; d < 3; ++d) {
+                const float dd = mimgf(xif[d] - P.xf[3 * j + d], p.g.n[d], p.g.per[d]);
+                d2 += dd * dd;
+            }
+            const float reach = (float)Ri + (float)P.R[j] + reach_pad;
+            if (d2 >= reach * reach) continue;
+        }
+        const V3 xj = ld3(P.x, j);
+        const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
+                        mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
+        const double dist = sqrt(dot(d, d));
+        const double Rj = P.R[j];
+        const double delta = dist - (Ri + Rj);
+        if (delta >= p.cut_max && delta >= 0.0) continue;
+        const V3 n = (1.0 / dist) * d;
+        const V3 uj = ld3(P.u, j), omj = ld3(P.om, j);
+        const V3 uij = ui - uj;
+        if (p.lubrication) {
+            const double Rm = 0.5 * (Ri + Rj);
+            const double dmin = (p.min_a + p.min_b * Rm) * Rm;
+            lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
+        }
+        if (delta < 0.0) {
+            const V3 ri = (-0.5) * d, rj = 0.5 * d;
+            const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
+            const double mj = P.m[j];
+            const double m_eff = mi * mj / (mi + mj);
+            const double Tc = collision_time(Ri + Rj, p.Tc);
+            V3 old = mk(0, 0, 0);
+            for (int h = 0; h < nin; ++h)
+                if (P.hist_id[hin][i * HIST_CAP + h] == j) {
+                    const double* s = P.hist_d[hin] + 3 * (i * HIST_CAP + h);
+                    old = mk(s[0], s[1], s[2]);
+                    break;
+                }
+            V3 Fn, Ft, dnew;
+            contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
+            F = F + (Fn + Ft);
+            T = T + cross(ri, Ft);
+            if (!init) {
+                if (nout < HIST_CAP) {
+                    P.hist_id[hout][i * HIST_CAP + nout] = j;
+                    double* s = P.hist_d[hout] + 3 * (i * HIST_CAP + nout);
+                    s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
+                    ++nout;
+                } else {
+                    atomicOr(p.status, ST_HIST_OVERFLOW);
+                }
+            }
+        }
+    }
+    // plane walls on the faces of non-periodic axes
+    const double xa[3] = {xi.x, xi.y, xi.z};
+    for (int a = 0; a < 3; ++a) {
+        if (p.g.per[a]) continue;
+        for (int side = 0; side < 2; ++side) {
+            const int face = 2 * a + side;
+            V3 nw = mk(0, 0, 0);
+            const double sgn = side == 0 ? 1.0 : -1.0;
+            if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
+            const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
+            const double delta = (xa[a] - xw) * sgn - Ri;
+            const double* uwp = p.g.wall_vel[side][a];
+            const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
+            const V3 uij = ui - uw;
+            if (p.lubrication) {
+                const double dmin = (p.min_a + p.min_b * Ri) * Ri;
+                lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
+            }
+            if (!init) P.wact[hout][6 * i + face] = 0;
+            if (delta < 0.0) {
+                const V3 ri = (-(Ri + 0.5 * delta)) * nw;
+                const V3 ucp = (ui + cross(omi, ri)) - uw;
+                const double Tc = collision_time(2.0 * Ri, p.Tc);
+                V3 old = mk(0, 0, 0);
+                if (P.wact[hin][6 * i + face]) {
+                    const double* s = P.whist[hin] + 3 * (6 * i + face);
+                    old = mk(s[0], s[1], s[2]);
+                }
+                V3 Fn, Ft, dnew;
+                contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
+                F = F + (Fn + Ft);
+                T = T + cross(ri, Ft);
+                if (!init) {
+                    double* s = P.whist[hout] + 3 * (6 * i + face);
+                    s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
+                    P.wact[hout][6 * i + face] = 1;
+                }
+            }
+        }
+    }
+    if (init) {
+        st3(P.F_prev, i, F);
+        st3(P.T_prev, i, T);
+    } else {
+        P.hist_n[hout][i] = nout;
+        st3(P.F_new, i, F);
+        st3(P.T_new, i, T);
+    }
+}
+
+void launch_dem_force(const DemParams& p, int init, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    force_kernel<<<(p.P.n + 63) / 64, 64, 0, st>>>(p, init);
+}
+
+}  // namespace lbmdem

@@ -1,0 +1,112 @@
+// launch.h -- host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace lbmdem {
+
+struct LbmStepParams {
+    int storage;                 // 0 f64, 1 f32, 2 f16, 3 bf16
+    const void* src;
+    void* dst;
+    const uint8_t* flags;
+    const int* owner;
+    Geom g;
+    double s_plus, s_minus, s_b_shell, s_b_bulk;
+    int bulk_corr;
+    double a_user[3];
+    double ext_total[3];
+    const unsigned long long* n_solid;
+    int counterforce;
+    Particles P;
+    int missing_links;
+    int* status;
+    const unsigned int* near_list;   // near-boundary cells from the mapping
+    const int* near_count;
+    int near_cap;
+    int near_blocks;                 // grid of the boundary kernel
+    double* accel_d;                 // out: fluid body force of the step [3]
+    float* accel_f;
+};
+void launch_lbm_step(const LbmStepParams& p, cudaStream_t st);
+
+struct MapParams {
+    Geom g;
+    Particles P;
+    uint8_t* flags;
+    int* owner;
+    int ntile[3];
+    int* tile_count;
+    int* tile_list;
+    double shell_width;
+    unsigned int* refill_list;
+    int* refill_count;
+    int refill_cap;
+    unsigned long long* n_solid;
+    unsigned int* near_list;
+    int* near_count;
+    int near_cap;
+    int small[3];           // periodic axis too short for one image per tile
+    int* status;
+};
+void launch_tile_scatter(const MapParams& p, cudaStream_t st);
+void launch_map(const MapParams& p, cudaStream_t st);
+
+struct RefillParams {
+    int storage;
+    void* f;
+    const uint8_t* flags;
+    const int* owner;
+    Geom g;
+    Particles P;
+    const unsigned int* list;
+    const int* count;
+    int cap;
+    double s_nu;
+    const double* accel;   // fluid body force of the step [3]
+};
+void launch_refill(const RefillParams& p, cudaStream_t st);
+
+struct FieldsParams {
+    int storage;
+    const void* f;
+    const uint8_t* flags;
+    Geom g;
+    long long first_cell;   // slab of cells [first_cell, first_cell + count)
+    long long count;
+    const double* accel;
+    double* out;            // [4 * count]: rho, ux, uy, uz blocks
+};
+void launch_fields(const FieldsParams& p, cudaStream_t st);
+
+struct FinalizeParams {
+    Particles P;
+    int use_fixed;          // accumulators in fixed point (float32 path)
+    int first_step;
+    int averaging;
+};
+void launch_finalize(const FinalizeParams& p, cudaStream_t st);
+
+struct DemParams {
+    Geom g;
+    Particles P;
+    int nbins[3];
+    double binsize[3];
+    double cut_max;         // largest lubrication cut-off
+    double e_dry, Tc, nu_p, mu_p;
+    double cut_n, cut_tt, cut_tr, min_a, min_b;
+    double gravity[3];
+    double mu_f;            // dynamic fluid viscosity rho0 nu
+    int lubrication, tangential;
+    double dt;              // subcycle time step 1/n_sub
+    int hin, hout;          // history buffers to read and write
+    int* status;
+};
+void launch_bins(const DemParams& p, cudaStream_t st);
+void launch_neighbours(const DemParams& p, cudaStream_t st);
+void launch_dem_position(const DemParams& p, cudaStream_t st);
+void launch_dem_force(const DemParams& p, int init, cudaStream_t st);
+void launch_dem_velocity(const DemParams& p, int last, cudaStream_t st);
+void launch_view_update(const Particles& P, cudaStream_t st);
+
+}  // namespace lbmdem

@@ -1,0 +1,582 @@
+// lbm_step.cu -- the two kernels of one lattice Boltzmann step with moving
+// particles (Algorithm 1, lines 1-3).
+//
+// boundary_kernel: one thread per cell of the near-boundary list built by the
+//   mapping. For a fluid cell x and a direction q whose upstream cell
+//   y = x - c_q is solid (particle i), the CLI moving no-slip condition of
+//   Eq. (14) along the link p = qbar (link fraction delta_p from the
+//   ray-sphere intersection; bounce-back, delta = 1/2 in the coefficients,
+//   when x + c_q is not fluid) gives f_q(x, t+1). That value is written into
+//   the slot f_q(y) of the solid cell, the one slot the pull of x reads, so the
+//   dense kernel needs no boundary logic. The link force of Eq. (15) and its
+//   torque are summed per particle (Eqs. (16)-(17)). Solid cells of the list
+//   add F_q = 2 w_q c_q for missing links from cells of other bodies (Sec. 2.2).
+// stream_collide_kernel: one thread per cell, pull streaming (Eq. (2)) with
+//   halfway bounce-back on the walls of the box (Eq. (14), delta = 1/2, wall
+//   velocity), then the two-relaxation-time collision (Eq. (10), magic
+//   parameter Eq. (11)) with Guo forcing; in TRT+aB shell cells (Sec. 2.3.2)
+//   and for Lambda_b,bulk != 1 the two bulk moments m4, m5 relax with s_b
+//   (Eq. (12)) through a rank-2 correction in moment space.
+//
+// PDFs are stored shifted (f_q - w_q) in SoA layout f[q][z][y][x], read from
+// one buffer and written to the other. The per-particle sums use a warp-level
+// reduction and one atomic per warp: float64 atomics for float64 storage,
+// exact 64-bit fixed point (scale 2^32) for the float32 compute path. The
+// float32 path runs no float64 instruction per cell.
+#include "common.cuh"
+#include "launch.h"
+
+namespace lbmdem {
+
+template <typename S>
+struct BcArgs {
+    S* src;                          // written only in solid-cell slots
+    const uint8_t* __restrict__ flags;
+    const int* __restrict__ owner;
+    Geom g;
+    const unsigned int* __restrict__ list;   // near-boundary cells (bit 31: solid cell)
+    const int* count;
+    int cap;
+    const double* __restrict__ px;
+    const double* __restrict__ pu;
+    const double* __restrict__ pom;
+    const double* __restrict__ pR;
+    const PartView* __restrict__ view;
+    double* acc_d;
+    long long* acc_i;
+    int missing_links;
+    int* status;
+    // fluid body force of the step: a_user - ext_total / N_fluid (counter force)
+    double a_user[3];
+    double ext_total[3];
+    int counterforce;
+    const unsigned long long* n_solid;
+    double* accel_d;
+    float* accel_f;
+};
+
+template <typename S, typename T>
+struct SCArgs {
+    const S* __restrict__ src;
+    S* __restrict__ dst;
+    const uint8_t* __restrict__ flags;
+    Geom g;
+    T s_plus, s_minus, s_b_shell, s_b_bulk;
+    T uw[2][3][3];                   // wall velocities [side][axis][component]
+    int bulk_corr;
+    const T* __restrict__ accel;     // [3]
+    int* status;
+};
+
+// ------------------------------------------------------------------ helpers
+
+// float -> fixed point with scale 2^32 using float32 and int32 operations only;
+// exact up to the final rounding at 2^-32. |v| must stay below 2^31.
+__device__ __forceinline__ long long to_fixed(float v, int* status) {
+    float hi = truncf(v);
+    float r1 = (v - hi) * 65536.0f;
+    float mid = truncf(r1);
+    float r2 = (r1 - mid) * 65536.0f;
+    if (!(fabsf(hi) < 2147483520.0f)) {
+        atomicOr(status, ST_FIXED_OVERFLOW);
+        return 0;
+    }
+    unsigned long long h = (unsigned long long)(long long)__float2int_rz(hi);
+    long long m = (long long)__float2int_rz(mid);
+    long long l = (long long)__float2int_rn(r2);
+    return (long long)(h << 32) + m * 65536LL + l;
+}
+
+__device__ __forceinline__ void add_particle(double* acc_d, long long*, int i, int c, double v, int*) {
+    atomicAdd(acc_d + 6 * i + c, v);
+}
+__device__ __forceinline__ void add_particle(double*, long long* acc_i, int i, int c, float v, int* st) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc_i + 6 * i + c),
+              (unsigned long long)to_fixed(v, st));
+}
+
+// warp-level commit of per-lane (particle key, F, T) partial sums
+template <typename T>
+__device__ __forceinline__ void commit_forces(int key, T (&acc)[6], double* acc_d, long long* acc_i,
+                                              int* status) {
+    const unsigned full = 0xffffffffu;
+    unsigned act = __ballot_sync(full, key >= 0);
+    if (act == 0) return;
+    int leader = __ffs(act) - 1;
+    int k0 = __shfl_sync(full, key, leader);
+    bool uni = __all_sync(full, key < 0 || key == k0);
+    if (uni) {
+        int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            T v = key >= 0 ? acc[c] : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+            if (lane == leader) add_particle(acc_d, acc_i, k0, c, v, status);
+        }
+    } else if (key >= 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) add_particle(acc_d, acc_i, key, c, acc[c], status);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void lane_accumulate(int i, const T (&F)[3], const T (&Tq)[3], int& key,
+                                                T (&acc)[6], double* acc_d, long long* acc_i,
+                                                int* status) {
+    if (key >= 0 && key != i) {  // a second particle in the same cell: flush the first
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            add_particle(acc_d, acc_i, key, c, acc[c], status);
+            acc[c] = T(0);
+        }
+    }
+    key = i;
+    acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
+    acc[3] += Tq[0]; acc[4] += Tq[1]; acc[5] += Tq[2];
+}
+
+__device__ __forceinline__ double min_image_d(double d, int n, int per) {
+    if (per) {
+        double half = 0.5 * (double)n;
+        if (d > half) d -= (double)n;
+        if (d < -half) d += (double)n;
+    }
+    return d;
+}
+__device__ __forceinline__ float min_image_f(float d, int n, int per) {
+    if (per) {
+        float half = 0.5f * (float)n;
+        if (d > half) d -= (float)n;
+        if (d < -half) d += (float)n;
+    }
+    return d;
+}
+
+// offset (cell centre - particle centre) with minimum image, and the rigid
+// body data of particle i, in the compute precision T
+template <typename T> struct PartOps;
+template <> struct PartOps<double> {
+    template <typename A>
+    __device__ static void load(const A& a, int i, int x, int y, int z, double (&r)[3], double& R,
+                                double (&u)[3], double (&om)[3]) {
+        const int c[3] = {x, y, z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = min_image_d(((double)c[d] + 0.5) - a.px[3 * i + d], a.g.n[d], a.g.per[d]);
+            u[d] = a.pu[3 * i + d];
+            om[d] = a.pom[3 * i + d];
+        }
+        R = a.pR[i];
+    }
+};
+template <> struct PartOps<float> {
+    template <typename A>
+    __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], float& R,
+                                float (&u)[3], float (&om)[3]) {
+        const PartView v = a.view[i];
+        const int c[3] = {x, y, z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = min_image_f((float)(c[d] - v.base[d]) + (0.5f - v.frac[d]), a.g.n[d], a.g.per[d]);
+            u[d] = v.u[d];
+            om[d] = v.om[d];
+        }
+        R = v.R;
+    }
+};
+
+// error-free transformations (Knuth's TwoSum, FMA product error)
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename T>
+__device__ __forceinline__ T two_sum(T a, T b, T& err) {
+    const T s = a + b;
+    const T bb = s - a;
+    err += (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// smallest t in [0, 1] with |r + t c| = R (link fraction delta of Eq. (14)).
+// |r|^2 - R^2 cancels strongly near the surface, so it is formed from exact
+// products and compensated sums; the root uses the cancellation-free form
+// t = 2 cc / (-b + sqrt(b^2 - 4 a cc)) of the smaller root.
+template <typename T>
+__device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T cc2, T R) {
+    const T b = T(2) * (r[0] * c0 + r[1] * c1 + r[2] * c2_);
+    T err = T(0);
+    const T p0 = r[0] * r[0], p1 = r[1] * r[1], p2 = r[2] * r[2], pR = R * R;
+    const T e = (fma_t<T>(r[0], r[0], -p0) + fma_t<T>(r[1], r[1], -p1)) +
+                (fma_t<T>(r[2], r[2], -p2) - fma_t<T>(R, R, -pR));
+    T sum = two_sum<T>(p0, p1, err);
+    sum = two_sum<T>(sum, p2, err);
+    sum = two_sum<T>(sum, -pR, err);
+    const T cc = sum + (err + e);
+    const T disc = b * b - T(4) * cc2 * cc;
+    if (disc < T(0)) return T(0.5);
+    const T sq = sqrt(disc);
+    const T t = b < T(0) ? (T(2) * cc) / (sq - b) : (-b - sq) / (T(2) * cc2);
+    return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+}
+
+// lattice directions as run-time tables (for link work distributed over lanes)
+__constant__ signed char k_c[Q][3] = {{0, 0, 0},   {0, 1, 0},   {0, -1, 0},  {-1, 0, 0},  {1, 0, 0},
+                                      {0, 0, 1},   {0, 0, -1},  {-1, 1, 0},  {1, 1, 0},   {-1, -1, 0},
+                                      {1, -1, 0},  {0, 1, 1},   {0, -1, 1},  {-1, 0, 1},  {1, 0, 1},
+                                      {0, 1, -1},  {0, -1, -1}, {-1, 0, -1}, {1, 0, -1}};
+__constant__ signed char k_opp[Q] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 16, 15, 18, 17, 12, 11, 14, 13};
+
+// ------------------------------------------------------------------ boundary kernel
+
+// CLI condition and momentum exchange of one particle link: fluid cell
+// (x, y, z), pull direction q, solid upstream cell x - c_q
+template <typename S, typename T>
+__device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, int z, int q, int& key,
+                                              T (&acc)[6]) {
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    const long long plane = (long long)nx * ny;
+    const long long N = a.g.ncells;
+    const int c[3] = {k_c[q][0], k_c[q][1], k_c[q][2]};
+    const int p = k_opp[q];
+    const int cpos[3] = {x, y, z};
+    int uv[3], dv[3];
+    bool cli = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        uv[d] = wrap_idx(cpos[d] - c[d], a.g.n[d]);
+        dv[d] = cpos[d] + c[d];
+        if (!a.g.per[d] && (dv[d] < 0 || dv[d] >= a.g.n[d])) cli = false;
+        dv[d] = wrap_idx(dv[d], a.g.n[d]);
+    }
+    const long long idx = (long long)z * plane + (long long)y * nx + x;
+    const long long up = (long long)uv[2] * plane + (long long)uv[1] * nx + uv[0];
+    const long long down = (long long)dv[2] * plane + (long long)dv[1] * nx + dv[0];
+    const int i = a.owner[up];
+    const T fout = Store<S>::load(a.src + (long long)p * N + idx);
+    const T fin = Store<S>::load(a.src + (long long)q * N + idx);
+    if (cli) cli = !(a.flags[down] & FL_SOLID);
+    const T fdown = cli ? Store<S>::load(a.src + (long long)p * N + down) : T(0);
+    T r[3], R, u[3], om[3];
+    PartOps<T>::load(a, i, x, y, z, r, R, u, om);
+    const T cp0 = (T)(-c[0]), cp1 = (T)(-c[1]), cp2 = (T)(-c[2]);
+    const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
+    const T delta = link_fraction<T>(r, cp0, cp1, cp2, (T)cc2, R);
+    const T dbc = cli ? delta : T(0.5);
+    const T kappa = (T(1) - T(2) * dbc) / (T(1) + T(2) * dbc);
+    const T rb[3] = {r[0] + delta * cp0, r[1] + delta * cp1, r[2] + delta * cp2};
+    const T ub[3] = {u[0] + (om[1] * rb[2] - om[2] * rb[1]), u[1] + (om[2] * rb[0] - om[0] * rb[2]),
+                     u[2] + (om[0] * rb[1] - om[1] * rb[0])};
+    const T ubc = ub[0] * cp0 + ub[1] * cp1 + ub[2] * cp2;
+    const T v = fout + kappa * (fdown - fin) - (T(12) * w / (T(1) + T(2) * dbc)) * ubc;
+    // the pull of x in direction q reads exactly this solid-cell slot
+    Store<S>::store(a.src + (long long)q * N + up, v);
+    // Eq. (15) on shifted PDFs: F = c_p (2 w + f~_p + f_q) - u_b (f~_p - f_q)
+    const T sum = T(2) * w + fout + v;
+    const T dif = fout - v;
+    const T F[3] = {cp0 * sum - ub[0] * dif, cp1 * sum - ub[1] * dif, cp2 * sum - ub[2] * dif};
+    const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
+    lane_accumulate<T>(i, F, Tq, key, acc, a.acc_d, a.acc_i, a.status);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
+    using T = typename Store<S>::T;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double acc3[3] = {a.a_user[0], a.a_user[1], a.a_user[2]};
+        if (a.counterforce) {
+            const double nf = (double)(a.g.ncells - (long long)(*a.n_solid));
+            for (int d = 0; d < 3; ++d) acc3[d] -= a.ext_total[d] / nf;
+        }
+        for (int d = 0; d < 3; ++d) {
+            a.accel_d[d] = acc3[d];
+            a.accel_f[d] = (float)acc3[d];
+        }
+    }
+    const int count = min(*a.count, a.cap);
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    const long long plane = (long long)nx * ny;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < count;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + threadIdx.x;
+        int key = -1;
+        T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        unsigned mask = 0;          // particle links of this lane's fluid cell
+        int x = 0, y = 0, z = 0;
+        if (k < count) {
+            const unsigned int e = a.list[k];
+            const bool solid_entry = (e & 0x80000000u) != 0;
+            const long long idx = (long long)(e & 0x7fffffffu);
+            x = (int)(idx % nx);
+            y = (int)((idx / nx) % ny);
+            z = (int)(idx / plane);
+            const int cpos[3] = {x, y, z};
+            if (solid_entry) {
+                // ------------------------------- missing links (Sec. 2.2)
+                const int i = a.owner[idx];
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    const int c[3] = {cx(q), cy(q), cz(q)};
+                    bool outside = false;
+                    int v[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        v[d] = cpos[d] - c[d];
+                        if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
+                        v[d] = wrap_idx(v[d], a.g.n[d]);
+                    }
+                    bool cand = outside;
+                    if (!outside) {
+                        const long long xo = (long long)v[2] * plane + (long long)v[1] * nx + v[0];
+                        cand = (a.flags[xo] & FL_SOLID) && a.owner[xo] != i;
+                    }
+                    if (!cand) continue;
+                    // exact float64 inside test of the far cell centre against
+                    // sphere i, in the operation order of the mapping
+                    double dd[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        dd[d] = min_image_d(((double)(cpos[d] - c[d]) + 0.5) - a.px[3 * i + d], a.g.n[d],
+                                            a.g.per[d]);
+                    const double Ri = a.pR[i];
+                    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
+                                                __dmul_rn(dd[2], dd[2]));
+                    if (!(d2 > __dmul_rn(Ri, Ri))) continue;
+                    T r[3], R, u[3], om[3];
+                    PartOps<T>::load(a, i, x - c[0], y - c[1], z - c[2], r, R, u, om);
+                    const T cf0 = (T)c[0], cf1 = (T)c[1], cf2 = (T)c[2];
+                    const T t = link_fraction<T>(r, cf0, cf1, cf2, (T)c2(q), R);
+                    const T rb[3] = {r[0] + t * cf0, r[1] + t * cf1, r[2] + t * cf2};
+                    const T w2 = T(2) * wq<T>(q);
+                    const T F[3] = {w2 * cf0, w2 * cf1, w2 * cf2};
+                    const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2],
+                                     rb[0] * F[1] - rb[1] * F[0]};
+                    lane_accumulate<T>(i, F, Tq, key, acc, a.acc_d, a.acc_i, a.status);
+                }
+            } else {
+                // link mask: directions whose upstream cell is solid
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    int v[3] = {x - cx(q), y - cy(q), z - cz(q)};
+                    bool outside = false;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
+                        v[d] = wrap_idx(v[d], a.g.n[d]);
+                    }
+                    if (!outside && (a.flags[(long long)v[2] * plane + (long long)v[1] * nx + v[0]] & FL_SOLID))
+                        mask |= 1u << q;
+                }
+            }
+        }
+        // spread the warp's links evenly over its lanes: inclusive prefix sum
+        // of the link counts, then lane l takes links l, l + 32, ...
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - cnt;
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int kk = r0 + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(FULL, incl, src + step - 1);
+                if (v <= kk) src += step;
+            }
+            src = src > 31 ? 31 : src;
+            const int sx = __shfl_sync(FULL, x, src);
+            const int sy = __shfl_sync(FULL, y, src);
+            const int sz = __shfl_sync(FULL, z, src);
+            const unsigned sm = __shfl_sync(FULL, mask, src);
+            const int sex = __shfl_sync(FULL, excl, src);
+            if (kk < total) {
+                const int q = (int)__fns(sm, 0, kk - sex + 1);
+                particle_link<S, T>(a, sx, sy, sz, q, key, acc);
+            }
+        }
+        commit_forces<T>(key, acc, a.acc_d, a.acc_i, a.status);
+    }
+}
+
+// ------------------------------------------------------------------ stream + collide
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) stream_collide_kernel(const SCArgs<S, T> a) {
+    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long plane = (long long)nx * ny;
+    const long long N = a.g.ncells;
+    const long long idx = (long long)z * plane + (long long)y * nx + x;
+    const uint8_t fl = a.flags[idx];
+    if (fl & FL_SOLID) return;
+
+    const int X3[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int Y3[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int Z3[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+#define NB(dx, dy, dz) ((long long)Z3[1 + (dz)] * plane + (long long)Y3[1 + (dy)] * nx + X3[1 + (dx)])
+    T f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = Store<S>::load(a.src + (long long)q * N + NB(-cx(q), -cy(q), -cz(q)));
+#undef NB
+    // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
+    const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
+    const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
+    const bool wz = !a.g.per[2] && (z == 0 || z == nz - 1);
+    if (wx || wy || wz) {
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const int u0 = x - cx(q), u1 = y - cy(q), u2 = z - cz(q);
+            int axis = -1, side = 0;
+            if (wz && (u2 < 0 || u2 >= nz)) { axis = 2; side = u2 < 0 ? 0 : 1; }
+            else if (wy && (u1 < 0 || u1 >= ny)) { axis = 1; side = u1 < 0 ? 0 : 1; }
+            else if (wx && (u0 < 0 || u0 >= nx)) { axis = 0; side = u0 < 0 ? 0 : 1; }
+            if (axis < 0) continue;
+            const int p = opp(q);
+            const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
+                          a.uw[side][axis][2] * (T)(-cz(q));
+            f[q] = Store<S>::load(a.src + (long long)p * N + idx) - T(6) * wq<T>(p) * ucp;
+        }
+    }
+
+    // ------------------------------------------- TRT+aB collision
+    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        drho += f[q];
+        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
+        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
+        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
+    }
+    const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
+    const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T ua = ux * ax + uy * ay + uz * az;
+    const T sp = a.s_plus, sm = a.s_minus;
+    const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
+    T fo[Q];
+    {
+        const T w0 = wq<T>(0);
+        const T feq0 = w0 * (drho - T(1.5) * usq);
+        fo[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua));
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int qb = opp(q);
+        if (qb < q) continue;
+        const T w = wq<T>(q);
+        const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
+        const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
+        const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
+        const T em = w * (T(3) * cu);
+        const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
+        const T Fm = w * (T(3) * ca);
+        const T fp = T(0.5) * (f[q] + f[qb]);
+        const T fm = T(0.5) * (f[q] - f[qb]);
+        const T dp = -sp * (fp - ep) + gp * Fp;
+        const T dm = -sm * (fm - em) + gm * Fm;
+        fo[q] = f[q] + dp + dm;
+        fo[qb] = f[qb] + dp - dm;
+    }
+    const bool shell = (fl & FL_SHELL) != 0;
+    if (shell || a.bulk_corr) {
+        // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) relax with s_b
+        const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
+        T saxis = T(0), sdiag = T(0);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
+        }
+        const T m4 = -f[0] + sdiag;
+        const T m5 = f[0] - T(2) * saxis + sdiag;
+        const T dm4 = ds * ((usq - m4) - ua);
+        const T dm5 = ds * (-m5);
+        // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
+        const T k4 = T(1.5) * dm4, k5 = T(0.5) * dm5;
+        fo[0] += wq<T>(0) * (-k4 + k5);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (c2(q) == 1) fo[q] += wq<T>(q) * (T(-2) * k5);
+            else fo[q] += wq<T>(q) * (k4 + k5);
+        }
+    }
+    if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, fo[q]);
+}
+
+template <typename S>
+void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
+    using T = typename Store<S>::T;
+    BcArgs<S> b;
+    b.src = static_cast<S*>(const_cast<void*>(p.src));
+    b.flags = p.flags;
+    b.owner = p.owner;
+    b.g = p.g;
+    b.list = p.near_list;
+    b.count = p.near_count;
+    b.cap = p.near_cap;
+    b.px = p.P.x;
+    b.pu = p.P.u;
+    b.pom = p.P.om;
+    b.pR = p.P.R;
+    b.view = p.P.view;
+    b.acc_d = p.P.acc_d;
+    b.acc_i = p.P.acc_i;
+    b.missing_links = p.missing_links;
+    b.status = p.status;
+    for (int d = 0; d < 3; ++d) {
+        b.a_user[d] = p.a_user[d];
+        b.ext_total[d] = p.ext_total[d];
+    }
+    b.counterforce = p.counterforce;
+    b.n_solid = p.n_solid;
+    b.accel_d = p.accel_d;
+    b.accel_f = p.accel_f;
+    const int bblocks = p.near_blocks > 0 ? p.near_blocks : 1;
+    boundary_kernel<S><<<bblocks, 256, 0, st>>>(b);
+
+    SCArgs<S, T> a;
+    a.src = static_cast<const S*>(p.src);
+    a.dst = static_cast<S*>(p.dst);
+    a.flags = p.flags;
+    a.g = p.g;
+    a.s_plus = (T)p.s_plus;
+    a.s_minus = (T)p.s_minus;
+    a.s_b_shell = (T)p.s_b_shell;
+    a.s_b_bulk = (T)p.s_b_bulk;
+    for (int s = 0; s < 2; ++s)
+        for (int ax = 0; ax < 3; ++ax)
+            for (int c = 0; c < 3; ++c) a.uw[s][ax][c] = (T)p.g.wall_vel[s][ax][c];
+    a.bulk_corr = p.bulk_corr;
+    a.accel = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)p.accel_d : (const void*)p.accel_f);
+    a.status = p.status;
+    const int nx = p.g.n[0];
+    int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
+    int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, p.g.n[2]);
+    stream_collide_kernel<S, T><<<grid, block, 0, st>>>(a);
+}
+
+void launch_lbm_step(const LbmStepParams& p, cudaStream_t st) {
+    switch (p.storage) {
+        case 0: launch_step_t<double>(p, st); break;
+        case 1: launch_step_t<float>(p, st); break;
+        case 2: launch_step_t<__half>(p, st); break;
+        default: launch_step_t<__nv_bfloat16>(p, st); break;
+    }
+}
+
+}  // namespace lbmdem

@@ -1,0 +1,304 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Tolerances:
+  * flags and owners (integer work): bit-exact;
+  * float64 storage: relative L2 <= 1e-11 on PDFs, velocity, density and
+    particle state for runs of up to 40 steps, <= 1e-10 for 300 steps (both
+    sides are float64; only the summation order of the per-particle sums and
+    the contraction into FMAs differ, each adding ~1e-16 per step, and the
+    coupled dynamics carry these differences along);
+  * float32 storage (and float32 collision): relative L2 <= 1e-6 on velocity
+    and density, <= 1e-5 on particle positions, the targets of the float32
+    path.
+"""
+import numpy as np
+import pytest
+
+from cases import build_gpu, build_oracle, spheres, rel_l2
+from oracle.lbm import equilibrium
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-11
+
+
+@pytest.fixture(scope='module')
+def L():
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_2003_01490_gb300 import lbmdem
+    lbmdem.load_library()
+    return lbmdem
+
+
+def random_state(shape, seed, amp_u=0.03):
+    nx, ny, nz = shape
+    r = np.random.default_rng(seed)
+    f = equilibrium(1 + 0.01 * r.standard_normal((nz, ny, nx)), amp_u * r.standard_normal((3, nz, ny, nx)))
+    return f * (1 + 0.02 * r.standard_normal(f.shape))
+
+
+def random_spheres(shape, periodic, n, rmin, rmax, seed, gap=0.3):
+    r = np.random.default_rng(seed)
+    pos, rad = [], []
+    L = np.array(shape, float)
+    while len(rad) < n:
+        R = r.uniform(rmin, rmax)
+        p = r.uniform(0, 1, 3) * L
+        ok = True
+        for a in range(3):
+            if not periodic[a] and (p[a] - R < 0.6 or p[a] + R > L[a] - 0.6):
+                ok = False
+        for q, Rq in zip(pos, rad):
+            d = p - q
+            for a in range(3):
+                if periodic[a]:
+                    d[a] -= L[a] * np.round(d[a] / L[a])
+            if np.linalg.norm(d) < R + Rq + gap:
+                ok = False
+        if ok:
+            pos.append(p)
+            rad.append(R)
+    return np.array(pos), np.array(rad)
+
+
+# ---------------------------------------------------------------- mapping
+
+@pytest.mark.parametrize('periodic', [(1, 1, 0), (1, 1, 1), (0, 1, 0)])
+def test_mapping_is_bit_exact(L, periodic):
+    shape = (70, 37, 41)            # not a multiple of the 32 x 4 x 4 tiles
+    pos, rad = random_spheres(shape, periodic, 14, 2.2, 7.5, seed=sum(periodic))
+    case = dict(shape=shape, periodic=periodic, tau=0.7, storage='f32',
+                spheres=spheres(pos, rad, density=np.full(len(rad), 1.5)),
+                dem=dict(fixed_particles=1))
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    _, _, flags = L.lbm_get_fields(ctx)
+    owner = L.lbm_get_owner(ctx)
+    solid = (flags & L.FLAG_SOLID) != 0
+    assert np.array_equal(solid, ora.owner >= 0)
+    assert np.array_equal(owner[solid], ora.owner[solid])
+    assert np.array_equal((flags & L.FLAG_SHELL) != 0, ora.shell)
+    # NEAR covers every fluid cell with a solid neighbour; MISS every solid
+    # cell next to another body or a wall
+    from oracle.d3q19 import C
+    nx, ny, nz = shape
+    fluid = ~solid
+    need_near = np.zeros_like(fluid)
+    need_miss = np.zeros_like(fluid)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing='ij')
+    for c in C[1:]:
+        xs = [x + c[0], y + c[1], z + c[2]]
+        out = np.zeros_like(fluid)
+        for a, n in enumerate(shape):
+            if periodic[a]:
+                xs[a] = xs[a] % n
+            else:
+                out |= (xs[a] < 0) | (xs[a] >= n)
+                xs[a] = np.clip(xs[a], 0, n - 1)
+        nb_solid = solid[xs[2], xs[1], xs[0]] & ~out
+        nb_owner = np.where(nb_solid, ora.owner[xs[2], xs[1], xs[0]], -1)
+        need_near |= fluid & nb_solid
+        need_miss |= solid & (out | (nb_solid & (nb_owner != ora.owner)))
+    assert not (need_near & ((flags & L.FLAG_NEAR) == 0)).any()
+    assert not (need_miss & ((flags & L.FLAG_MISS) == 0)).any()
+
+
+# ---------------------------------------------------------------- fluid only
+
+def test_fluid_with_moving_walls_f64(L):
+    shape = (37, 20, 23)
+    case = dict(shape=shape, periodic=(1, 0, 0), tau=0.62, storage='f64', body_force=(2e-5, 0, -1e-5),
+                wall_vel_hi=[[0, 0, 0], [0.01, 0, 0.005], [0.02, -0.01, 0]],
+                wall_vel_lo=[[0, 0, 0], [0, 0, 0], [-0.01, 0, 0]],
+                relax=dict(lambda_b_bulk=3.0), init_pdfs=random_state(shape, 1))
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    ora.step(15)
+    L.lbm_step(ctx, 15)
+    f = L.lbm_get_pdfs(ctx)
+    assert rel_l2(f - 1, ora.ft - 1) < F64_TOL
+    rho, u, _ = L.lbm_get_fields(ctx)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < F64_TOL and rel_l2(rho, r_o) < F64_TOL
+
+
+# ---------------------------------------------------------------- fixed particles
+
+def fixed_particle_case(storage, shape=(40, 36, 30)):
+    R = np.array([5.2, 4.6, 3.7])
+    pos = np.array([[10.3, 17.9, 15.2], [10.3 + 5.2 + 4.6 + 0.35, 18.4, 14.6], [30.0, 6.0, 3.1 + 0.9]])
+    vel = np.array([[0.01, -0.004, 0.002], [0.0, 0.006, -0.003], [-0.005, 0.0, 0.0]])
+    om = np.array([[0.0, 0.001, -0.002], [0.003, 0.0, 0.0], [0.0, 0.0, 0.004]])
+    return dict(shape=shape, periodic=(1, 1, 0), tau=0.58, storage=storage, body_force=(1e-5, 0, 0),
+                spheres=spheres(pos, R, vel=vel, omega=om), dem=dict(fixed_particles=1),
+                init_pdfs=random_state(shape, 2, amp_u=0.01))
+
+
+def test_fixed_moving_boundaries_f64(L):
+    case = fixed_particle_case('f64')
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    for _ in range(3):
+        ora.step(3)
+        L.lbm_step(ctx, 3)
+        st = L.lbm_get_particle_state(ctx)
+        assert rel_l2(st['force_hyd'], ora.Ffp) < F64_TOL
+        assert rel_l2(st['torque_hyd'], ora.Tfp) < F64_TOL
+    fluid = ora.owner < 0
+    f = L.lbm_get_pdfs(ctx)
+    assert rel_l2(f[:, fluid], ora.ft[:, fluid]) < F64_TOL
+
+
+def test_fixed_moving_boundaries_f32(L):
+    case = fixed_particle_case('f32')
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    ora.step(6)
+    L.lbm_step(ctx, 6)
+    st = L.lbm_get_particle_state(ctx)
+    assert rel_l2(st['force_hyd'], ora.Ffp) < 1e-5
+    assert rel_l2(st['torque_hyd'], ora.Tfp) < 1e-5
+    rho, u, _ = L.lbm_get_fields(ctx)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < 1e-6 and rel_l2(rho, r_o) < 1e-6
+
+
+# ---------------------------------------------------------------- moving particles
+
+def collision_case(storage):
+    shape = (34, 30, 36)
+    R = np.array([4.0, 3.5, 3.2])
+    # sphere 0 falls onto the wall z = 0; spheres 1 and 2 approach each other
+    pos = np.array([[9.0, 9.5, 4.0 + 0.3], [22.3, 15.0, 18.0], [22.0, 15.2, 18.0 + 3.5 + 3.2 + 0.3]])
+    vel = np.array([[0.01, 0.0, -0.06], [0.0, 0.0, 0.05], [0.0, 0.0, -0.05]])
+    om = np.array([[0.0, 0.002, 0.0], [0.0, 0.0, 0.0], [0.001, 0.0, 0.0]])
+    return dict(shape=shape, periodic=(1, 1, 0), tau=0.6, storage=storage,
+                spheres=spheres(pos, R, density=np.array([10.0, 8.0, 8.0]), vel=vel, omega=om),
+                dem=dict(gravity=(0.0, 0.0, -2e-4), Tc=8.0))
+
+
+def test_moving_particles_collisions_f64(L):
+    case = collision_case('f64')
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    contacts, refills = set(), 0
+    for _ in range(8):
+        for _ in range(5):
+            ora.step(1)
+            contacts |= {k[1] == 'wall' for k in ora.hist}
+            refills += len(ora.refilled)
+        L.lbm_step(ctx, 5)
+        st = L.lbm_get_particle_state(ctx)
+        assert rel_l2(st['pos'], ora.X) < F64_TOL
+        assert rel_l2(st['vel'], ora.U) < F64_TOL
+        assert rel_l2(st['omega'], ora.Om) < 1e-10
+    rho, u, flags = L.lbm_get_fields(ctx)
+    assert np.array_equal((flags & L.FLAG_SOLID) != 0, ora.owner >= 0)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < F64_TOL and rel_l2(rho, r_o) < F64_TOL
+    # the case exercised sphere-wall and sphere-sphere contacts and refills
+    assert contacts == {True, False} and refills > 0
+
+
+def test_moving_particles_collisions_f32(L):
+    case = collision_case('f32')
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    ora.step(40)
+    L.lbm_step(ctx, 40)
+    st = L.lbm_get_particle_state(ctx)
+    assert rel_l2(st['pos'], ora.X) < 1e-5
+    rho, u, flags = L.lbm_get_fields(ctx)
+    both = (ora.owner < 0) & ((flags & L.FLAG_SOLID) == 0)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o, both) < 1e-6 and rel_l2(rho, r_o, both) < 1e-6
+
+
+def test_sphere_wall_workload_first_300_steps_f64(L):
+    from paper_2003_01490_gb300 import workloads
+    w = workloads.sphere_wall()
+    case = dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage='f64',
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']),
+                dem=w['dem'])
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    ora.step(300)
+    L.lbm_step(ctx, 300)
+    st = L.lbm_get_particle_state(ctx)
+    assert rel_l2(st['pos'], ora.X) < 10 * F64_TOL
+    assert rel_l2(st['vel'], ora.U) < 10 * F64_TOL
+    rho, u, _ = L.lbm_get_fields(ctx)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < 10 * F64_TOL and rel_l2(rho, r_o) < 10 * F64_TOL
+
+
+# ---------------------------------------------------------------- suspension workload
+
+def suspension_case(storage):
+    from paper_2003_01490_gb300 import workloads
+    w = workloads.reduced_suspension(storage=storage)
+    return dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage=storage,
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']),
+                dem=w['dem'])
+
+
+@pytest.fixture(scope='module')
+def suspension_oracle():
+    """Float64 oracle of the 64 x 64 x 128 suspension (150 spheres), 6 steps."""
+    ora = build_oracle(suspension_case('f64'))
+    ora.step(6)
+    return ora
+
+
+@pytest.mark.parametrize('storage,tol_u,tol_x', [('f64', F64_TOL, F64_TOL), ('f32', 1e-6, 1e-5)])
+def test_reduced_suspension(L, suspension_oracle, storage, tol_u, tol_x):
+    ora = suspension_oracle
+    ctx = build_gpu(suspension_case(storage))
+    L.lbm_step(ctx, 6)
+    st = L.lbm_get_particle_state(ctx)
+    assert rel_l2(st['pos'], ora.X) < tol_x
+    rho, u, flags = L.lbm_get_fields(ctx)
+    both = (ora.owner < 0) & ((flags & L.FLAG_SOLID) == 0)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o, both) < tol_u and rel_l2(rho, r_o, both) < tol_u
+    if storage == 'f64':
+        assert np.array_equal((flags & L.FLAG_SOLID) != 0, ora.owner >= 0)
+        assert rel_l2(st['force_hyd'], ora.Ffp) < 1e-10
+
+
+def test_full_size_suspension_mapping_sampled(L):
+    """256 x 256 x 512 cells, 10,000 spheres: the flags and owners of sampled
+    cells equal a brute-force float64 evaluation over every nearby sphere."""
+    from scipy.spatial import cKDTree
+    from paper_2003_01490_gb300 import workloads
+    from oracle import Domain
+    from oracle.particles import map_cells
+    w = workloads.suspension()
+    case = dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage='f32',
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']),
+                dem=dict(w['dem'], fixed_particles=1))
+    ctx = build_gpu(case)
+    _, _, flags = L.lbm_get_fields(ctx)
+    owner = L.lbm_get_owner(ctx)
+    nx, ny, nz = w['shape']
+    r = np.random.default_rng(5)
+    cells = [r.integers(0, (nx, ny, nz), size=(40000, 3))]
+    for i in r.choice(len(w['radius']), 12, replace=False):
+        lo = np.floor(w['pos'][i] - 9).astype(int)
+        g = np.stack(np.meshgrid(*[np.arange(lo[a], lo[a] + 19) for a in range(3)], indexing='ij'), -1)
+        cells.append(g.reshape(-1, 3) % np.array([nx, ny, nz]))
+    cells = np.unique(np.concatenate(cells), axis=0)
+    tree = cKDTree(w['pos'], boxsize=np.array([nx, ny, nz], float))
+    dom = Domain(nx, ny, nz)
+    cand = tree.query_ball_point(cells + 0.5, r=w['radius'].max() + 2.0 + 0.1)
+    for (x, y, z), js in zip(cells, cand):
+        js = sorted(js)
+        o, sh = map_cells(np.array([[x + 0.5, y + 0.5, z + 0.5]]), w['pos'][js], w['radius'][js], dom, 2.0)
+        want_owner = js[o[0]] if o[0] >= 0 else -1
+        fl = flags[z, y, x]
+        assert bool(fl & L.FLAG_SOLID) == (want_owner >= 0), (x, y, z)
+        if want_owner >= 0:
+            assert owner[z, y, x] == want_owner, (x, y, z)
+        assert bool(fl & L.FLAG_SHELL) == bool(sh[0]), (x, y, z)
