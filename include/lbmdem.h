@@ -177,15 +177,16 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Device timing of lbm_step() by phase, with CUDA events recorded on the
- * context stream between the launches of each step. Phases: 0 the fused
- * stream/boundary/collision kernel (Eqs. (2), (14)-(17), (5)), 1 the force
- * finalisation and averaging (Sec. 4.2), 2 the DEM subcycles (neighbour
- * lists, lubrication, contact, Velocity Verlet), 3 the mapping update
- * (Sec. 2.2), 4 the refill (Eq. (18)). lbm_profile(ctx, 1) clears the totals
+ * context stream between the launches of each step. Phases: 0 the boundary
+ * kernel (particle links, Eqs. (14)-(17), and missing links), 1 the dense
+ * stream + collide kernel (Eqs. (2), (5) with wall bounce-back), 2 the force
+ * finalisation and averaging (Sec. 4.2), 3 the DEM subcycles (neighbour
+ * lists, lubrication, contact, Velocity Verlet), 4 the mapping update
+ * (Sec. 2.2), 5 the refill (Eq. (18)). lbm_profile(ctx, 1) clears the totals
  * and starts recording; lbm_profile(ctx, 0) stops. lbm_profile_read()
- * synchronises the stream and returns the summed milliseconds of the 5 phases
- * and the number of timed steps. Recording costs a few event records per
- * step; it is off by default. */
+ * synchronises the stream and returns the summed milliseconds of the 6 phases
+ * (phase_ms must hold 6 doubles) and the number of timed steps. Recording
+ * costs a few event records per step; it is off by default. */
 lbm_status lbm_profile(lbm_ctx *ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
 

@@ -13,6 +13,10 @@
 
 using namespace lbmdem;
 
+// phases of lbm_profile(): boundary, stream+collide, force finalisation, DEM,
+// mapping, refill
+constexpr int LBM_PHASES = 6;
+
 struct lbm_ctx {
     Geom g{};
     lbm_relax relax{};
@@ -43,6 +47,9 @@ struct lbm_ctx {
     unsigned int* near_list = nullptr;
     int* near_count = nullptr;
     int near_cap = 0;
+    unsigned int* miss_list = nullptr;
+    int* miss_count = nullptr;
+    int miss_cap = 0;
     double* scratch = nullptr;
     long long scratch_cells = 0;
     long long bin_cap = 1;
@@ -171,8 +178,8 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(4 * n);                                // 31 nbr_count
     L.add(4 * n * NBR_CAP);                      // 32 nbr
     for (int h = 0; h < 2; ++h) {
-        L.add(4 * n * HIST_CAP);                 // 33/38 hist_id
-        L.add(8 * 3 * n * HIST_CAP);             // 34/39 hist_d
+        L.add(4 * n * NBR_CAP);                  // 33/38 hist_id
+        L.add(8 * 3 * n * NBR_CAP);              // 34/39 hist_d
         L.add(4 * n);                            // 35/40 hist_n
         L.add(8 * 3 * 6 * n);                    // 36/41 whist
         L.add(6 * n);                            // 37/42 wact
@@ -181,6 +188,13 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(4);                                    // 44 near_count
     L.add(4 * 3);                                // 45 accel_f
     L.add(4 * 3 * n);                            // 46 xf
+    L.add(4 * N);                                // 47 miss_list
+    L.add(4);                                    // 48 miss_count
+    L.add(8 * 6 * n);                            // 49 acc_k
+    L.add(8 * 3 * n);                            // 50 x (second subcycle buffer)
+    L.add(8 * 3 * n);                            // 51 u
+    L.add(8 * 3 * n);                            // 52 om
+    L.add(4 * 3 * n);                            // 53 xf
     (void)g;
 }
 
@@ -275,12 +289,21 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->near_cap = (int)s.ncells;
     ctx->accel_f = (float*)at(45);
     ctx->P.xf = (float*)at(46);
+    ctx->miss_list = (unsigned int*)at(47);
+    ctx->miss_count = (int*)at(48);
+    ctx->miss_cap = (int)s.ncells;
+    ctx->P.acc_k = (long long*)at(49);
+    ctx->P.xs[1] = (double*)at(50);
+    ctx->P.us[1] = (double*)at(51);
+    ctx->P.oms[1] = (double*)at(52);
+    ctx->P.xfs[1] = (float*)at(53);
     ctx->scratch = (double*)at(11);
     ctx->scratch_cells = s.scratch_cells;
     ctx->bin_cap = s.bin_cap;
     Particles& P = ctx->P;
     P.n = 0;
     P.x = (double*)at(12); P.u = (double*)at(13); P.om = (double*)at(14); P.R = (double*)at(15);
+    P.xs[0] = P.x; P.us[0] = P.u; P.oms[0] = P.om; P.xfs[0] = P.xf;
     P.rho = (double*)at(16); P.m = (double*)at(17); P.I = (double*)at(18);
     P.F_prev = (double*)at(19); P.T_prev = (double*)at(20); P.F_new = (double*)at(21); P.T_new = (double*)at(22);
     P.acc_d = (double*)at(23); P.acc_i = (long long*)at(24);
@@ -323,6 +346,7 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
     mp.n_solid = ctx->n_solid; mp.status = ctx->status;
     mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
+    mp.miss_list = ctx->miss_list; mp.miss_count = ctx->miss_count; mp.miss_cap = ctx->miss_cap;
     launch_map(mp, sm);
     ctx->launches += 1;
     e = cudaGetLastError();
@@ -352,6 +376,7 @@ MapParams map_params(lbm_ctx* ctx) {
     mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
     mp.n_solid = ctx->n_solid; mp.status = ctx->status;
     mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
+    mp.miss_list = ctx->miss_list; mp.miss_count = ctx->miss_count; mp.miss_cap = ctx->miss_cap;
     return mp;
 }
 
@@ -362,6 +387,7 @@ lbm_status remap(lbm_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->refill_count, 0, sizeof(int), sm));
     CK(cudaMemsetAsync(ctx->n_solid, 0, sizeof(unsigned long long), sm));
     CK(cudaMemsetAsync(ctx->near_count, 0, sizeof(int), sm));
+    CK(cudaMemsetAsync(ctx->miss_count, 0, sizeof(int), sm));
     MapParams mp = map_params(ctx);
     launch_tile_scatter(mp, sm);
     launch_map(mp, sm);
@@ -432,6 +458,8 @@ lbm_status check_status(lbm_ctx* ctx) {
 }
 
 }  // namespace
+
+void lbmdem::set_global_error(const std::string& msg) { g_err = msg; }
 
 // ====================================================================== ABI
 
@@ -592,7 +620,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
                 CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
                 launch_bins(dp, sm);
                 launch_neighbours(dp, sm);
-                launch_dem_force(dp, 1, sm);
+                launch_dem_subcycle(dp, 0, 1, 0, sm);
                 ctx->launches += 3;
             }
         }
@@ -622,10 +650,15 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
         lp.near_list = ctx->near_list;
         lp.near_count = ctx->near_count;
         lp.near_cap = ctx->near_cap;
+        lp.miss_list = ctx->miss_list;
+        lp.miss_count = ctx->miss_count;
+        lp.miss_cap = ctx->miss_cap;
         lp.near_blocks = ctx->P.n > 0 ? 152 * 8 : 1;
         lp.accel_d = ctx->accel;
         lp.accel_f = ctx->accel_f;
-        launch_lbm_step(lp, sm);
+        launch_boundary(lp, sm);
+        CK(prof_mark(ctx));
+        launch_stream_collide(lp, sm);
         CK(prof_mark(ctx));
         FinalizeParams fpp{};
         fpp.P = ctx->P;
@@ -643,13 +676,18 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
             launch_neighbours(dp, sm);
             launch_dem_position(dp, sm);
             ctx->launches += 3;
+            int cur = 0;
             for (int s = 0; s < d.n_sub; ++s) {
                 dp.hin = ctx->hcur;
                 dp.hout = 1 - ctx->hcur;
-                launch_dem_force(dp, 0, sm);
+                launch_dem_subcycle(dp, cur, 0, s == d.n_sub - 1, sm);
                 ctx->hcur = 1 - ctx->hcur;
-                launch_dem_velocity(dp, s == d.n_sub - 1, sm);
-                ctx->launches += 2;
+                cur = 1 - cur;
+                ctx->launches += 1;
+            }
+            if (cur == 1) {
+                launch_state_copy(ctx->P, sm);
+                ctx->launches += 1;
             }
             CK(prof_mark(ctx));
             // Algorithm 1, line 11: mapping update and refill
@@ -817,9 +855,9 @@ lbm_status lbm_profile(lbm_ctx* ctx, int enable) {
 lbm_status lbm_profile_read(lbm_ctx* ctx, double* phase_ms, long long* steps) {
     if (!ctx || !phase_ms) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int k = 0; k < 5; ++k) phase_ms[k] = 0.0;
-    for (size_t b = 0; b + 6 <= ctx->ev_used; b += 6)
-        for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < LBM_PHASES; ++k) phase_ms[k] = 0.0;
+    for (size_t b = 0; b + LBM_PHASES + 1 <= ctx->ev_used; b += LBM_PHASES + 1)
+        for (int k = 0; k < LBM_PHASES; ++k) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ctx->events[b + k], ctx->events[b + k + 1]));
             phase_ms[k] += ms;

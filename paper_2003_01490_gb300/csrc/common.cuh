@@ -56,7 +56,6 @@ constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;   // mapping tile (512 cells)
 constexpr int TILE_CAP = 64;                          // candidate particles per tile
 constexpr int BIN_CAP = 32;                           // particles per DEM bin
 constexpr int NBR_CAP = 32;                           // neighbour candidates per particle
-constexpr int HIST_CAP = 16;                          // active sphere contacts per particle
 constexpr double NBR_SKIN = 1.0;                      // Verlet skin of the per-step list
 
 // --------------------------------------------------------------------------
@@ -121,19 +120,25 @@ struct Particles {
     double* T_new;         // [3n]
     double* acc_d;         // [6n] float64 link-force accumulators (F, T)
     long long* acc_i;      // [6n] fixed-point link-force accumulators (float32 kernels)
+    long long* acc_k;      // [6n] exact 36 x (constant link force, its torque about the base cell)
     double* fp;            // [6n] F^fp, T^fp of the last step
     double* fp_old;        // [6n] F^fp, T^fp of the step before
     double* fbar;          // [6n] averaged F^fp, T^fp used by the DEM
     PartView* view;        // [n]
     float* xf;             // [3n] float32 copy of x for neighbour prefilters
+    // double-buffered subcycle state: index 0 is x/u/om/xf above, 1 the copy
+    double* xs[2];
+    double* us[2];
+    double* oms[2];
+    float* xfs[2];
     // DEM neighbour structure and contact history
     int* bin_count;        // [nbins]
     int* bin_list;         // [nbins * BIN_CAP]
     int* nbr_count;        // [n]
     int* nbr;              // [n * NBR_CAP]
-    int* hist_id[2];       // [n * HIST_CAP] partner ids, double buffered
-    double* hist_d[2];     // [n * HIST_CAP * 3] tangential springs
-    int* hist_n[2];        // [n]
+    int* hist_id[2];       // [n * NBR_CAP] partner of each neighbour slot in contact (-1: none)
+    double* hist_d[2];     // [n * NBR_CAP * 3] tangential springs
+    int* hist_n[2];        // [n] number of valid slots
     double* whist[2];      // [n * 6 * 3] wall tangential springs per face
     unsigned char* wact[2];// [n * 6] wall contact active flags
 };

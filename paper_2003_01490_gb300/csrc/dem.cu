@@ -79,10 +79,31 @@ void launch_view_update(const Particles& P, cudaStream_t st) {
 __global__ void finalize_kernel(const FinalizeParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
+    double exact[6] = {0, 0, 0, 0, 0, 0};
+    if (p.use_fixed) {
+        // constant link parts summed exactly by the float32 boundary kernel:
+        // K = 36 sum 2 w c and 36 sum 2 w (n x c); torque adds g x (K / 36)
+        // with g = 1/2 - (x - floor(x)) the common fractional cell offset
+        double k[6], g[3];
+        for (int c = 0; c < 6; ++c) {
+            k[c] = (double)p.P.acc_k[6 * i + c] / 36.0;
+            p.P.acc_k[6 * i + c] = 0;
+        }
+        for (int d = 0; d < 3; ++d) {
+            const double x = p.P.x[3 * i + d];
+            g[d] = 0.5 - (x - floor(x));
+        }
+        exact[0] = k[0];
+        exact[1] = k[1];
+        exact[2] = k[2];
+        exact[3] = k[3] + (g[1] * k[2] - g[2] * k[1]);
+        exact[4] = k[4] + (g[2] * k[0] - g[0] * k[2]);
+        exact[5] = k[5] + (g[0] * k[1] - g[1] * k[0]);
+    }
     for (int c = 0; c < 6; ++c) {
         double v;
         if (p.use_fixed) {
-            v = (double)p.P.acc_i[6 * i + c] * (1.0 / FIX_SCALE);
+            v = (double)p.P.acc_i[6 * i + c] * (1.0 / FIX_SCALE) + exact[c];
             p.P.acc_i[6 * i + c] = 0;
         } else {
             v = p.P.acc_d[6 * i + c];
@@ -207,46 +228,6 @@ void launch_dem_position(const DemParams& p, cudaStream_t st) {
     position_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
 }
 
-__global__ void velocity_kernel(const DemParams p, int last) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.P.n) return;
-    // Eq. (38) for u and its rotational analogue for omega
-    const double m = p.P.m[i], I = p.P.I[i];
-    const double cu = p.dt / (2.0 * m), co = p.dt / (2.0 * I);
-    double usq = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        const double Fn = p.P.F_new[3 * i + d], Tn = p.P.T_new[3 * i + d];
-        const double u = p.P.u[3 * i + d] + cu * (p.P.F_prev[3 * i + d] + Fn);
-        p.P.u[3 * i + d] = u;
-        p.P.om[3 * i + d] = p.P.om[3 * i + d] + co * (p.P.T_prev[3 * i + d] + Tn);
-        p.P.F_prev[3 * i + d] = Fn;
-        p.P.T_prev[3 * i + d] = Tn;
-        usq += u * u;
-    }
-    if (!(usq < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
-    if (!last) {
-        position_update(p, i);
-    } else {
-        PartView v;
-        for (int d = 0; d < 3; ++d) {
-            const double x = p.P.x[3 * i + d];
-            const double b = floor(x);
-            v.base[d] = (int)b;
-            v.frac[d] = (float)(x - b);
-            v.u[d] = (float)p.P.u[3 * i + d];
-            v.om[d] = (float)p.P.om[3 * i + d];
-        }
-        v.R = (float)p.P.R[i];
-        v.pad = 0.f;
-        p.P.view[i] = v;
-    }
-}
-
-void launch_dem_velocity(const DemParams& p, int last, cudaStream_t st) {
-    if (p.P.n == 0) return;
-    velocity_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p, last);
-}
-
 // ------------------------------------------------------------ interaction laws
 
 // lubrication force and torque on i due to j (Rj <= 0: plane wall), Eqs. (27)-(33)
@@ -321,132 +302,214 @@ __device__ __forceinline__ double collision_time(double diameter, double Tc) {
     return Tc > 0.0 ? Tc : 2.31 * diameter * 1.7320508075688772;
 }
 
-__global__ void force_kernel(const DemParams p, int init) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.P.n) return;
+// One Velocity-Verlet subcycle (Algorithm 1, inner loop), 4 lanes per particle.
+// Reads the state of buffer `cur` (x, u, omega at the subcycle's positions),
+// evaluates lubrication (Eqs. (25)-(33)), contact (Eqs. (39)-(50)), the
+// averaged fluid force and V (rho_p - rho_f) g, then (lane 0 of the group)
+// updates the velocities (Eq. (38)) and, unless it is the last subcycle, the
+// positions of the next subcycle (Eq. (37)) into buffer 1 - cur.
+// init = 1 evaluates the initial force F(t = 0) only (no state or history
+// update). Pair terms are evaluated by both partners with mirrored operands.
+constexpr int GROUP = 4;
+
+__global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gid / GROUP;
+    const int sub = gid % GROUP;
+    const bool act = i < p.P.n;
     const Particles& P = p.P;
-    const V3 xi = ld3(P.x, i), ui = ld3(P.u, i), omi = ld3(P.om, i);
-    const double Ri = P.R[i], mi = P.m[i];
-    const double vol = P.m[i] / P.rho[i];
-    V3 F = mk(P.fbar[6 * i], P.fbar[6 * i + 1], P.fbar[6 * i + 2]) +
-           (vol * (P.rho[i] - 1.0)) * mk(p.gravity[0], p.gravity[1], p.gravity[2]);
-    V3 T = mk(P.fbar[6 * i + 3], P.fbar[6 * i + 4], P.fbar[6 * i + 5]);
+    const double* X = P.xs[cur];
+    const double* Uv = P.us[cur];
+    const double* Om = P.oms[cur];
+    const float* Xf = P.xfs[cur];
+    V3 F = mk(0, 0, 0), T = mk(0, 0, 0);
     const int hin = p.hin, hout = p.hout;
-    const int nin = P.hist_n[hin][i];
-    int nout = 0;
-    const int nn = P.nbr_count[i];
-    const float xif[3] = {P.xf[3 * i], P.xf[3 * i + 1], P.xf[3 * i + 2]};
-    const float reach_pad = (float)p.cut_max + 1e-3f;
-    for (int k = 0; k < nn; ++k) {
-        const int j = P.nbr[i * NBR_CAP + k];
-        {
+    if (act) {
+        const V3 xi = ld3(X, i), ui = ld3(Uv, i), omi = ld3(Om, i);
+        const double Ri = P.R[i], mi = P.m[i];
+        const float xif[3] = {Xf[3 * i], Xf[3 * i + 1], Xf[3 * i + 2]};
+        const float reach_pad = (float)p.cut_max + 1e-3f;
+        const int nn = P.nbr_count[i];
+        const int nin = P.hist_n[hin][i];
+        for (int k = sub; k < nn; k += GROUP) {
+            const int j = P.nbr[i * NBR_CAP + k];
+            bool contact = false;
+            V3 dnew = mk(0, 0, 0);
             // float32 prefilter: float positions are within 1e-4 of the float64
             // ones, so a gap above cut_max + 1e-3 here is above cut_max exactly
-            float d2 = 0.f;
+            float d2f = 0.f;
             for (int d = 0; d < 3; ++d) {
-                const float dd = mimgf(xif[d] - P.xf[3 * j + d], p.g.n[d], p.g.per[d]);
-                d2 += dd * dd;
+                const float dd = mimgf(xif[d] - Xf[3 * j + d], p.g.n[d], p.g.per[d]);
+                d2f += dd * dd;
             }
             const float reach = (float)Ri + (float)P.R[j] + reach_pad;
-            if (d2 >= reach * reach) continue;
-        }
-        const V3 xj = ld3(P.x, j);
-        const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
-                        mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
-        const double dist = sqrt(dot(d, d));
-        const double Rj = P.R[j];
-        const double delta = dist - (Ri + Rj);
-        if (delta >= p.cut_max && delta >= 0.0) continue;
-        const V3 n = (1.0 / dist) * d;
-        const V3 uj = ld3(P.u, j), omj = ld3(P.om, j);
-        const V3 uij = ui - uj;
-        if (p.lubrication) {
-            const double Rm = 0.5 * (Ri + Rj);
-            const double dmin = (p.min_a + p.min_b * Rm) * Rm;
-            lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
-        }
-        if (delta < 0.0) {
-            const V3 ri = (-0.5) * d, rj = 0.5 * d;
-            const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
-            const double mj = P.m[j];
-            const double m_eff = mi * mj / (mi + mj);
-            const double Tc = collision_time(Ri + Rj, p.Tc);
-            V3 old = mk(0, 0, 0);
-            for (int h = 0; h < nin; ++h)
-                if (P.hist_id[hin][i * HIST_CAP + h] == j) {
-                    const double* s = P.hist_d[hin] + 3 * (i * HIST_CAP + h);
-                    old = mk(s[0], s[1], s[2]);
-                    break;
+            if (d2f < reach * reach) {
+                const V3 xj = ld3(X, j);
+                const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
+                                mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
+                const double dist = sqrt(dot(d, d));
+                const double Rj = P.R[j];
+                const double delta = dist - (Ri + Rj);
+                if (!(delta >= p.cut_max && delta >= 0.0)) {
+                    const V3 n = (1.0 / dist) * d;
+                    const V3 uj = ld3(Uv, j), omj = ld3(Om, j);
+                    const V3 uij = ui - uj;
+                    if (p.lubrication) {
+                        const double Rm = 0.5 * (Ri + Rj);
+                        const double dmin = (p.min_a + p.min_b * Rm) * Rm;
+                        lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
+                    }
+                    if (delta < 0.0) {
+                        const V3 ri = (-0.5) * d, rj = 0.5 * d;
+                        const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
+                        const double mj = P.m[j];
+                        const double m_eff = mi * mj / (mi + mj);
+                        const double Tc = collision_time(Ri + Rj, p.Tc);
+                        V3 old = mk(0, 0, 0);
+                        for (int h = 0; h < nin; ++h)
+                            if (P.hist_id[hin][i * NBR_CAP + h] == j) {
+                                const double* s = P.hist_d[hin] + 3 * (i * NBR_CAP + h);
+                                old = mk(s[0], s[1], s[2]);
+                                break;
+                            }
+                        V3 Fn, Ft;
+                        contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
+                        F = F + (Fn + Ft);
+                        T = T + cross(ri, Ft);
+                        contact = true;
+                    }
                 }
-            V3 Fn, Ft, dnew;
-            contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
-            F = F + (Fn + Ft);
-            T = T + cross(ri, Ft);
+            }
             if (!init) {
-                if (nout < HIST_CAP) {
-                    P.hist_id[hout][i * HIST_CAP + nout] = j;
-                    double* s = P.hist_d[hout] + 3 * (i * HIST_CAP + nout);
+                // tangential spring of this neighbour slot for the next subcycle
+                P.hist_id[hout][i * NBR_CAP + k] = contact ? j : -1;
+                if (contact) {
+                    double* s = P.hist_d[hout] + 3 * (i * NBR_CAP + k);
                     s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
-                    ++nout;
-                } else {
-                    atomicOr(p.status, ST_HIST_OVERFLOW);
+                }
+            }
+        }
+        if (sub == 0) {
+            // plane walls on the faces of non-periodic axes
+            const double xa[3] = {xi.x, xi.y, xi.z};
+            for (int a = 0; a < 3; ++a) {
+                if (p.g.per[a]) continue;
+                for (int side = 0; side < 2; ++side) {
+                    const int face = 2 * a + side;
+                    V3 nw = mk(0, 0, 0);
+                    const double sgn = side == 0 ? 1.0 : -1.0;
+                    if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
+                    const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
+                    const double delta = (xa[a] - xw) * sgn - Ri;
+                    const double* uwp = p.g.wall_vel[side][a];
+                    const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
+                    const V3 uij = ui - uw;
+                    if (p.lubrication) {
+                        const double dmin = (p.min_a + p.min_b * Ri) * Ri;
+                        lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
+                    }
+                    if (!init) P.wact[hout][6 * i + face] = 0;
+                    if (delta < 0.0) {
+                        const V3 ri = (-(Ri + 0.5 * delta)) * nw;
+                        const V3 ucp = (ui + cross(omi, ri)) - uw;
+                        const double Tc = collision_time(2.0 * Ri, p.Tc);
+                        V3 old = mk(0, 0, 0);
+                        if (P.wact[hin][6 * i + face]) {
+                            const double* s = P.whist[hin] + 3 * (6 * i + face);
+                            old = mk(s[0], s[1], s[2]);
+                        }
+                        V3 Fn, Ft, dnew;
+                        contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
+                        F = F + (Fn + Ft);
+                        T = T + cross(ri, Ft);
+                        if (!init) {
+                            double* s = P.whist[hout] + 3 * (6 * i + face);
+                            s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
+                            P.wact[hout][6 * i + face] = 1;
+                        }
+                    }
                 }
             }
         }
     }
-    // plane walls on the faces of non-periodic axes
-    const double xa[3] = {xi.x, xi.y, xi.z};
-    for (int a = 0; a < 3; ++a) {
-        if (p.g.per[a]) continue;
-        for (int side = 0; side < 2; ++side) {
-            const int face = 2 * a + side;
-            V3 nw = mk(0, 0, 0);
-            const double sgn = side == 0 ? 1.0 : -1.0;
-            if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
-            const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
-            const double delta = (xa[a] - xw) * sgn - Ri;
-            const double* uwp = p.g.wall_vel[side][a];
-            const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
-            const V3 uij = ui - uw;
-            if (p.lubrication) {
-                const double dmin = (p.min_a + p.min_b * Ri) * Ri;
-                lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
-            }
-            if (!init) P.wact[hout][6 * i + face] = 0;
-            if (delta < 0.0) {
-                const V3 ri = (-(Ri + 0.5 * delta)) * nw;
-                const V3 ucp = (ui + cross(omi, ri)) - uw;
-                const double Tc = collision_time(2.0 * Ri, p.Tc);
-                V3 old = mk(0, 0, 0);
-                if (P.wact[hin][6 * i + face]) {
-                    const double* s = P.whist[hin] + 3 * (6 * i + face);
-                    old = mk(s[0], s[1], s[2]);
-                }
-                V3 Fn, Ft, dnew;
-                contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
-                F = F + (Fn + Ft);
-                T = T + cross(ri, Ft);
-                if (!init) {
-                    double* s = P.whist[hout] + 3 * (6 * i + face);
-                    s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
-                    P.wact[hout][6 * i + face] = 1;
-                }
-            }
-        }
+    // sum the four lanes of the particle
+#pragma unroll
+    for (int o = 1; o < GROUP; o <<= 1) {
+        F.x += __shfl_xor_sync(0xffffffffu, F.x, o);
+        F.y += __shfl_xor_sync(0xffffffffu, F.y, o);
+        F.z += __shfl_xor_sync(0xffffffffu, F.z, o);
+        T.x += __shfl_xor_sync(0xffffffffu, T.x, o);
+        T.y += __shfl_xor_sync(0xffffffffu, T.y, o);
+        T.z += __shfl_xor_sync(0xffffffffu, T.z, o);
     }
+    if (!act || sub != 0) return;
+    const double vol = P.m[i] / P.rho[i];
+    F = F + mk(P.fbar[6 * i], P.fbar[6 * i + 1], P.fbar[6 * i + 2]) +
+        (vol * (P.rho[i] - 1.0)) * mk(p.gravity[0], p.gravity[1], p.gravity[2]);
+    T = T + mk(P.fbar[6 * i + 3], P.fbar[6 * i + 4], P.fbar[6 * i + 5]);
     if (init) {
         st3(P.F_prev, i, F);
         st3(P.T_prev, i, T);
-    } else {
-        P.hist_n[hout][i] = nout;
-        st3(P.F_new, i, F);
-        st3(P.T_new, i, T);
+        return;
+    }
+    P.hist_n[hout][i] = P.nbr_count[i];
+    // Eq. (38) for u and its rotational analogue for omega
+    const double m = P.m[i], I = P.I[i];
+    const double cu = p.dt / (2.0 * m), co = p.dt / (2.0 * I);
+    const V3 Fp = ld3(P.F_prev, i), Tp = ld3(P.T_prev, i);
+    const V3 u = ld3(Uv, i) + cu * (Fp + F);
+    const V3 om = ld3(Om, i) + co * (Tp + T);
+    st3(P.F_prev, i, F);
+    st3(P.T_prev, i, T);
+    if (!(dot(u, u) < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
+    const int nxt = 1 - cur;
+    st3(P.us[nxt], i, u);
+    st3(P.oms[nxt], i, om);
+    const double ua[3] = {u.x, u.y, u.z};
+    const double Fa[3] = {F.x, F.y, F.z};
+    const double c = p.dt * p.dt / (2.0 * m);
+    PartView v;
+    for (int d = 0; d < 3; ++d) {
+        // Eq. (37) for the next subcycle; the last subcycle keeps its positions
+        double x = X[3 * i + d];
+        if (!last) x = wrap_pos(x + p.dt * ua[d] + c * Fa[d], p.g.n[d], p.g.per[d]);
+        P.xs[nxt][3 * i + d] = x;
+        P.xfs[nxt][3 * i + d] = (float)x;
+        if (last) {
+            const double b = floor(x);
+            v.base[d] = (int)b;
+            v.frac[d] = (float)(x - b);
+            v.u[d] = (float)ua[d];
+            v.om[d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
+        }
+    }
+    if (last) {
+        v.R = (float)P.R[i];
+        v.pad = 0.f;
+        P.view[i] = v;
     }
 }
 
-void launch_dem_force(const DemParams& p, int init, cudaStream_t st) {
+void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st) {
     if (p.P.n == 0) return;
-    force_kernel<<<(p.P.n + 63) / 64, 64, 0, st>>>(p, init);
+    const int threads = 128;
+    const long long total = (long long)p.P.n * GROUP;
+    subcycle_kernel<<<(int)((total + threads - 1) / threads), threads, 0, st>>>(p, cur, init, last);
+}
+
+// copy state buffer 1 into buffer 0 (after an odd number of subcycles)
+__global__ void state_copy_kernel(const Particles P) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * P.n) return;
+    P.xs[0][k] = P.xs[1][k];
+    P.us[0][k] = P.us[1][k];
+    P.oms[0][k] = P.oms[1][k];
+    P.xfs[0][k] = P.xfs[1][k];
+}
+
+void launch_state_copy(const Particles& P, cudaStream_t st) {
+    if (P.n == 0) return;
+    state_copy_kernel<<<(3 * P.n + 255) / 256, 256, 0, st>>>(P);
 }
 
 }  // namespace lbmdem

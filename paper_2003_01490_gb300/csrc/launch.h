@@ -1,6 +1,8 @@
 // launch.h -- host-side launchers of the device kernels (internal to the library).
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace lbmdem {
@@ -21,14 +23,18 @@ struct LbmStepParams {
     Particles P;
     int missing_links;
     int* status;
-    const unsigned int* near_list;   // near-boundary cells from the mapping
+    const unsigned int* near_list;   // fluid cells with possible particle links
     const int* near_count;
     int near_cap;
+    const unsigned int* miss_list;   // solid cells with possible missing links
+    const int* miss_count;
+    int miss_cap;
     int near_blocks;                 // grid of the boundary kernel
     double* accel_d;                 // out: fluid body force of the step [3]
     float* accel_f;
 };
-void launch_lbm_step(const LbmStepParams& p, cudaStream_t st);
+void launch_boundary(const LbmStepParams& p, cudaStream_t st);
+void launch_stream_collide(const LbmStepParams& p, cudaStream_t st);
 
 struct MapParams {
     Geom g;
@@ -46,6 +52,9 @@ struct MapParams {
     unsigned int* near_list;
     int* near_count;
     int near_cap;
+    unsigned int* miss_list;
+    int* miss_count;
+    int miss_cap;
     int small[3];           // periodic axis too short for one image per tile
     int* status;
 };
@@ -105,8 +114,11 @@ struct DemParams {
 void launch_bins(const DemParams& p, cudaStream_t st);
 void launch_neighbours(const DemParams& p, cudaStream_t st);
 void launch_dem_position(const DemParams& p, cudaStream_t st);
-void launch_dem_force(const DemParams& p, int init, cudaStream_t st);
-void launch_dem_velocity(const DemParams& p, int last, cudaStream_t st);
+void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st);
+void launch_state_copy(const Particles& P, cudaStream_t st);
 void launch_view_update(const Particles& P, cudaStream_t st);
+
+// message returned by lbm_last_error(NULL)
+void set_global_error(const std::string& msg);
 
 }  // namespace lbmdem

@@ -1,16 +1,18 @@
 // lbm_step.cu -- the two kernels of one lattice Boltzmann step with moving
 // particles (Algorithm 1, lines 1-3).
 //
-// boundary_kernel: one thread per cell of the near-boundary list built by the
-//   mapping. For a fluid cell x and a direction q whose upstream cell
-//   y = x - c_q is solid (particle i), the CLI moving no-slip condition of
-//   Eq. (14) along the link p = qbar (link fraction delta_p from the
-//   ray-sphere intersection; bounce-back, delta = 1/2 in the coefficients,
-//   when x + c_q is not fluid) gives f_q(x, t+1). That value is written into
-//   the slot f_q(y) of the solid cell, the one slot the pull of x reads, so the
-//   dense kernel needs no boundary logic. The link force of Eq. (15) and its
-//   torque are summed per particle (Eqs. (16)-(17)). Solid cells of the list
-//   add F_q = 2 w_q c_q for missing links from cells of other bodies (Sec. 2.2).
+// boundary_kernel: the near-boundary list of the mapping holds fluid cells
+//   that may have particle links. For a fluid cell x and a direction q whose
+//   upstream cell y = x - c_q is solid (particle i), the CLI moving no-slip
+//   condition of Eq. (14) along the link p = qbar (link fraction delta_p from
+//   the ray-sphere intersection; bounce-back, delta = 1/2 in the coefficients,
+//   when x + c_q is not fluid) gives f_q(x, t+1). The value is written into
+//   the slot f_q(y) of the solid cell, the one slot the pull of x reads, so
+//   the dense kernel needs no boundary logic. The link force of Eq. (15) and
+//   its torque are summed per particle (Eqs. (16)-(17)). The links of a warp's
+//   cells are spread evenly over its lanes. The missing-link list holds solid
+//   cells next to another body; each missing link adds F_q = 2 w_q c_q
+//   (Sec. 2.2).
 // stream_collide_kernel: one thread per cell, pull streaming (Eq. (2)) with
 //   halfway bounce-back on the walls of the box (Eq. (14), delta = 1/2, wall
 //   velocity), then the two-relaxation-time collision (Eq. (10), magic
@@ -19,12 +21,25 @@
 //   (Eq. (12)) through a rank-2 correction in moment space.
 //
 // PDFs are stored shifted (f_q - w_q) in SoA layout f[q][z][y][x], read from
-// one buffer and written to the other. The per-particle sums use a warp-level
-// reduction and one atomic per warp: float64 atomics for float64 storage,
-// exact 64-bit fixed point (scale 2^32) for the float32 compute path. The
-// float32 path runs no float64 instruction per cell.
+// one buffer and written to the other.
+//
+// Per-particle sums. Float64 storage: float64 partial sums per warp, float64
+// atomics. Float32 compute: the link force is split into the constant part
+// 2 w_p c_p, which is an integer multiple of c_p / 36, and the small
+// remainder c_p (f~_p + f_q) - u_b (f~_p - f_q). The constant part and its
+// torque 2 w_p (n + g) x c_p (n the integer cell offset from the particle's
+// base cell, g its fractional offset, common to all links) are summed exactly
+// in integers; the remainder is summed per warp in float32 and per particle
+// in 64-bit fixed point (scale 2^32) through integer atomics. No float64
+// instruction runs per cell on the float32 path.
 #include "common.cuh"
 #include "launch.h"
+
+// minimum resident blocks per SM requested for the stream/collide kernel
+// (a register cap); tuned on GB300, see the design notes
+#ifndef LBM_SC_MIN_BLOCKS
+#define LBM_SC_MIN_BLOCKS 1
+#endif
 
 namespace lbmdem {
 
@@ -34,9 +49,12 @@ struct BcArgs {
     const uint8_t* __restrict__ flags;
     const int* __restrict__ owner;
     Geom g;
-    const unsigned int* __restrict__ list;   // near-boundary cells (bit 31: solid cell)
+    const unsigned int* __restrict__ list;   // fluid cells with possible particle links
     const int* count;
     int cap;
+    const unsigned int* __restrict__ miss;   // solid cells with possible missing links
+    const int* miss_count;
+    int miss_cap;
     const double* __restrict__ px;
     const double* __restrict__ pu;
     const double* __restrict__ pom;
@@ -44,6 +62,7 @@ struct BcArgs {
     const PartView* __restrict__ view;
     double* acc_d;
     long long* acc_i;
+    long long* acc_k;
     int missing_links;
     int* status;
     // fluid body force of the step: a_user - ext_total / N_fluid (counter force)
@@ -87,53 +106,88 @@ __device__ __forceinline__ long long to_fixed(float v, int* status) {
     return (long long)(h << 32) + m * 65536LL + l;
 }
 
-__device__ __forceinline__ void add_particle(double* acc_d, long long*, int i, int c, double v, int*) {
-    atomicAdd(acc_d + 6 * i + c, v);
+// per-lane partial sums of one particle's link forces and torques
+template <typename T>
+struct Acc {
+    int key = -1;                  // particle index, -1 = nothing accumulated
+    T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int k[6] = {0, 0, 0, 0, 0, 0}; // float32 path: 36 x constant force, 36 x (n x c) torque
+};
+
+struct Sinks {
+    double* acc_d;
+    long long* acc_i;
+    long long* acc_k;
+    int* status;
+};
+
+__device__ __forceinline__ void add_float(const Sinks& s, int i, int c, double v) { atomicAdd(s.acc_d + 6 * i + c, v); }
+__device__ __forceinline__ void add_float(const Sinks& s, int i, int c, float v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_i + 6 * i + c), (unsigned long long)to_fixed(v, s.status));
 }
-__device__ __forceinline__ void add_particle(double*, long long* acc_i, int i, int c, float v, int* st) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(acc_i + 6 * i + c),
-              (unsigned long long)to_fixed(v, st));
+__device__ __forceinline__ void add_int(const Sinks& s, int i, int c, int v) {
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_k + 6 * i + c), (unsigned long long)(long long)v);
 }
 
-// warp-level commit of per-lane (particle key, F, T) partial sums
 template <typename T>
-__device__ __forceinline__ void commit_forces(int key, T (&acc)[6], double* acc_d, long long* acc_i,
-                                              int* status) {
+__device__ __forceinline__ void flush(Acc<T>& a, const Sinks& s) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        add_float(s, a.key, c, a.f[c]);
+        if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+        a.f[c] = T(0);
+        a.k[c] = 0;
+    }
+}
+
+// warp-level commit of the per-lane partial sums: lanes holding the same
+// particle (found with match_any) are reduced by a tree over their ranks and
+// the lowest lane of each group issues the atomics
+template <typename T>
+__device__ __forceinline__ void commit(Acc<T>& a, const Sinks& s) {
     const unsigned full = 0xffffffffu;
-    unsigned act = __ballot_sync(full, key >= 0);
-    if (act == 0) return;
-    int leader = __ffs(act) - 1;
-    int k0 = __shfl_sync(full, key, leader);
-    bool uni = __all_sync(full, key < 0 || key == k0);
-    if (uni) {
-        int lane = threadIdx.x & 31;
+    if (__ballot_sync(full, a.key >= 0) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(full, a.key);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int size = __popc(peers);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        // partner: the peer whose rank is rank + off (only read when it exists)
+        const int pr = rank + off;
+        const int src = pr < size ? (int)__fns(peers, 0, pr + 1) : lane;
+        const bool take = (rank & (2 * off - 1)) == 0 && pr < size;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            T v = key >= 0 ? acc[c] : T(0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
-            if (lane == leader) add_particle(acc_d, acc_i, k0, c, v, status);
+            const T v = __shfl_sync(full, a.f[c], src);
+            if (take) a.f[c] += v;
+            if (sizeof(T) == 4) {
+                const int iv = __shfl_sync(full, a.k[c], src);
+                if (take) a.k[c] += iv;
+            }
         }
-    } else if (key >= 0) {
+    }
+    if (rank == 0 && a.key >= 0) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) add_particle(acc_d, acc_i, key, c, acc[c], status);
+        for (int c = 0; c < 6; ++c) {
+            add_float(s, a.key, c, a.f[c]);
+            if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+        }
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void lane_accumulate(int i, const T (&F)[3], const T (&Tq)[3], int& key,
-                                                T (&acc)[6], double* acc_d, long long* acc_i,
-                                                int* status) {
-    if (key >= 0 && key != i) {  // a second particle in the same cell: flush the first
+__device__ __forceinline__ void accumulate(int i, const T (&F)[3], const T (&Tq)[3], const int (&K)[6], Acc<T>& a,
+                                           const Sinks& s) {
+    if (a.key >= 0 && a.key != i) flush(a, s);   // a second particle in the same lane
+    a.key = i;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            add_particle(acc_d, acc_i, key, c, acc[c], status);
-            acc[c] = T(0);
-        }
+    for (int c = 0; c < 3; ++c) {
+        a.f[c] += F[c];
+        a.f[3 + c] += Tq[c];
     }
-    key = i;
-    acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
-    acc[3] += Tq[0]; acc[4] += Tq[1]; acc[5] += Tq[2];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a.k[c] += K[c];
 }
 
 __device__ __forceinline__ double min_image_d(double d, int n, int per) {
@@ -144,26 +198,20 @@ __device__ __forceinline__ double min_image_d(double d, int n, int per) {
     }
     return d;
 }
-__device__ __forceinline__ float min_image_f(float d, int n, int per) {
-    if (per) {
-        float half = 0.5f * (float)n;
-        if (d > half) d -= (float)n;
-        if (d < -half) d += (float)n;
-    }
-    return d;
-}
 
-// offset (cell centre - particle centre) with minimum image, and the rigid
-// body data of particle i, in the compute precision T
+// offset r = (cell centre - particle centre) with minimum image, the integer
+// part n of that offset from the particle's base cell (float32 path), and the
+// rigid body data of particle i, in the compute precision T
 template <typename T> struct PartOps;
 template <> struct PartOps<double> {
     template <typename A>
-    __device__ static void load(const A& a, int i, int x, int y, int z, double (&r)[3], double& R,
+    __device__ static void load(const A& a, int i, int x, int y, int z, double (&r)[3], int (&n)[3], double& R,
                                 double (&u)[3], double (&om)[3]) {
         const int c[3] = {x, y, z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             r[d] = min_image_d(((double)c[d] + 0.5) - a.px[3 * i + d], a.g.n[d], a.g.per[d]);
+            n[d] = 0;
             u[d] = a.pu[3 * i + d];
             om[d] = a.pom[3 * i + d];
         }
@@ -172,13 +220,22 @@ template <> struct PartOps<double> {
 };
 template <> struct PartOps<float> {
     template <typename A>
-    __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], float& R,
+    __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float& R,
                                 float (&u)[3], float (&om)[3]) {
         const PartView v = a.view[i];
         const int c[3] = {x, y, z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            r[d] = min_image_f((float)(c[d] - v.base[d]) + (0.5f - v.frac[d]), a.g.n[d], a.g.per[d]);
+            int nd = c[d] - v.base[d];
+            const float g = 0.5f - v.frac[d];
+            if (a.g.per[d]) {
+                const float half = 0.5f * (float)a.g.n[d];
+                const float rd = (float)nd + g;
+                if (rd > half) nd -= a.g.n[d];
+                else if (rd < -half) nd += a.g.n[d];
+            }
+            n[d] = nd;
+            r[d] = (float)nd + g;
             u[d] = v.u[d];
             om[d] = v.om[d];
         }
@@ -233,8 +290,8 @@ __constant__ signed char k_opp[Q] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 16, 15, 1
 // CLI condition and momentum exchange of one particle link: fluid cell
 // (x, y, z), pull direction q, solid upstream cell x - c_q
 template <typename S, typename T>
-__device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, int z, int q, int& key,
-                                              T (&acc)[6]) {
+__device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, int z, int q, Acc<T>& acc,
+                                              const Sinks& sk) {
     const int nx = a.g.n[0], ny = a.g.n[1];
     const long long plane = (long long)nx * ny;
     const long long N = a.g.ncells;
@@ -259,8 +316,10 @@ __device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, 
     if (cli) cli = !(a.flags[down] & FL_SOLID);
     const T fdown = cli ? Store<S>::load(a.src + (long long)p * N + down) : T(0);
     T r[3], R, u[3], om[3];
-    PartOps<T>::load(a, i, x, y, z, r, R, u, om);
-    const T cp0 = (T)(-c[0]), cp1 = (T)(-c[1]), cp2 = (T)(-c[2]);
+    int n[3];
+    PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
+    const int cp[3] = {-c[0], -c[1], -c[2]};
+    const T cp0 = (T)cp[0], cp1 = (T)cp[1], cp2 = (T)cp[2];
     const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
     const T delta = link_fraction<T>(r, cp0, cp1, cp2, (T)cc2, R);
@@ -274,11 +333,92 @@ __device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, 
     // the pull of x in direction q reads exactly this solid-cell slot
     Store<S>::store(a.src + (long long)q * N + up, v);
     // Eq. (15) on shifted PDFs: F = c_p (2 w + f~_p + f_q) - u_b (f~_p - f_q)
-    const T sum = T(2) * w + fout + v;
     const T dif = fout - v;
+    int K[6] = {0, 0, 0, 0, 0, 0};
+    T sum;
+    if (sizeof(T) == 4) {
+        // 2 w_p c_p and its torque 2 w_p (n x c_p) as exact integers (x 36)
+        const int kw = cc2 == 1 ? 4 : 2;
+        sum = fout + v;
+        K[0] = kw * cp[0]; K[1] = kw * cp[1]; K[2] = kw * cp[2];
+        K[3] = kw * (n[1] * cp[2] - n[2] * cp[1]);
+        K[4] = kw * (n[2] * cp[0] - n[0] * cp[2]);
+        K[5] = kw * (n[0] * cp[1] - n[1] * cp[0]);
+    } else {
+        sum = T(2) * w + fout + v;
+    }
     const T F[3] = {cp0 * sum - ub[0] * dif, cp1 * sum - ub[1] * dif, cp2 * sum - ub[2] * dif};
     const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
-    lane_accumulate<T>(i, F, Tq, key, acc, a.acc_d, a.acc_i, a.status);
+    accumulate<T>(i, F, Tq, K, acc, sk);
+}
+
+// missing links of a solid cell s of particle i: links x -> s from cells x of
+// another body whose centre is not inside sphere i
+template <typename S, typename T>
+__device__ __forceinline__ void missing_links(const BcArgs<S>& a, long long idx, Acc<T>& acc, const Sinks& sk) {
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    const long long plane = (long long)nx * ny;
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / plane);
+    const int cpos[3] = {x, y, z};
+    const int i = a.owner[idx];
+    unsigned cand = 0, solidm = 0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        int v[3];
+        bool outside = false;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            v[d] = cpos[d] - (d == 0 ? cx(q) : d == 1 ? cy(q) : cz(q));
+            if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
+            v[d] = wrap_idx(v[d], a.g.n[d]);
+        }
+        if (outside) cand |= 1u << q;
+        else if (a.flags[(long long)v[2] * plane + (long long)v[1] * nx + v[0]] & FL_SOLID) solidm |= 1u << q;
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        if (!(solidm & (1u << q))) continue;
+        const int v0 = wrap_idx(x - cx(q), nx), v1 = wrap_idx(y - cy(q), ny), v2 = wrap_idx(z - cz(q), a.g.n[2]);
+        if (a.owner[(long long)v2 * plane + (long long)v1 * nx + v0] != i) cand |= 1u << q;
+    }
+    while (cand) {
+        const int q = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int c[3] = {k_c[q][0], k_c[q][1], k_c[q][2]};
+        // exact float64 inside test of the far cell centre against sphere i,
+        // in the operation order of the mapping
+        double dd[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            dd[d] = min_image_d(((double)(cpos[d] - c[d]) + 0.5) - a.px[3 * i + d], a.g.n[d], a.g.per[d]);
+        const double Ri = a.pR[i];
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
+        if (!(d2 > __dmul_rn(Ri, Ri))) continue;
+        T r[3], R, u[3], om[3];
+        int n[3];
+        PartOps<T>::load(a, i, x - c[0], y - c[1], z - c[2], r, n, R, u, om);
+        const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        int K[6] = {0, 0, 0, 0, 0, 0};
+        T F[3] = {T(0), T(0), T(0)}, Tq[3] = {T(0), T(0), T(0)};
+        if (sizeof(T) == 4) {
+            // F = 2 w_q c_q and torque 2 w_q (r x c_q), r = n + g: exact integers (x 36)
+            const int kw = cc2 == 1 ? 4 : 2;
+            K[0] = kw * c[0]; K[1] = kw * c[1]; K[2] = kw * c[2];
+            K[3] = kw * (n[1] * c[2] - n[2] * c[1]);
+            K[4] = kw * (n[2] * c[0] - n[0] * c[2]);
+            K[5] = kw * (n[0] * c[1] - n[1] * c[0]);
+        } else {
+            const T cf0 = (T)c[0], cf1 = (T)c[1], cf2 = (T)c[2];
+            const T t = link_fraction<T>(r, cf0, cf1, cf2, (T)cc2, R);
+            const T rb[3] = {r[0] + t * cf0, r[1] + t * cf1, r[2] + t * cf2};
+            const T w2 = cc2 == 1 ? T(2) / T(18) : T(2) / T(36);
+            F[0] = w2 * cf0; F[1] = w2 * cf1; F[2] = w2 * cf2;
+            Tq[0] = rb[1] * F[2] - rb[2] * F[1];
+            Tq[1] = rb[2] * F[0] - rb[0] * F[2];
+            Tq[2] = rb[0] * F[1] - rb[1] * F[0];
+        }
+        accumulate<T>(i, F, Tq, K, acc, sk);
+    }
 }
 
 template <typename S>
@@ -286,6 +426,7 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
     using T = typename Store<S>::T;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double acc3[3] = {a.a_user[0], a.a_user[1], a.a_user[2]};
         if (a.counterforce) {
@@ -297,80 +438,33 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
             a.accel_f[d] = (float)acc3[d];
         }
     }
-    const int count = min(*a.count, a.cap);
     const int nx = a.g.n[0], ny = a.g.n[1];
     const long long plane = (long long)nx * ny;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < count;
-         base += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+
+    // ------------------------------------------- particle links of fluid cells
+    const int count = min(*a.count, a.cap);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < count; base += stride) {
         const long long k = base + threadIdx.x;
-        int key = -1;
-        T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        unsigned mask = 0;          // particle links of this lane's fluid cell
+        Acc<T> acc;
+        unsigned mask = 0;          // directions with a solid upstream cell
         int x = 0, y = 0, z = 0;
         if (k < count) {
-            const unsigned int e = a.list[k];
-            const bool solid_entry = (e & 0x80000000u) != 0;
-            const long long idx = (long long)(e & 0x7fffffffu);
+            const long long idx = (long long)a.list[k];
             x = (int)(idx % nx);
             y = (int)((idx / nx) % ny);
             z = (int)(idx / plane);
-            const int cpos[3] = {x, y, z};
-            if (solid_entry) {
-                // ------------------------------- missing links (Sec. 2.2)
-                const int i = a.owner[idx];
 #pragma unroll
-                for (int q = 1; q < Q; ++q) {
-                    const int c[3] = {cx(q), cy(q), cz(q)};
-                    bool outside = false;
-                    int v[3];
+            for (int q = 1; q < Q; ++q) {
+                int v[3] = {x - cx(q), y - cy(q), z - cz(q)};
+                bool outside = false;
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        v[d] = cpos[d] - c[d];
-                        if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
-                        v[d] = wrap_idx(v[d], a.g.n[d]);
-                    }
-                    bool cand = outside;
-                    if (!outside) {
-                        const long long xo = (long long)v[2] * plane + (long long)v[1] * nx + v[0];
-                        cand = (a.flags[xo] & FL_SOLID) && a.owner[xo] != i;
-                    }
-                    if (!cand) continue;
-                    // exact float64 inside test of the far cell centre against
-                    // sphere i, in the operation order of the mapping
-                    double dd[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        dd[d] = min_image_d(((double)(cpos[d] - c[d]) + 0.5) - a.px[3 * i + d], a.g.n[d],
-                                            a.g.per[d]);
-                    const double Ri = a.pR[i];
-                    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
-                                                __dmul_rn(dd[2], dd[2]));
-                    if (!(d2 > __dmul_rn(Ri, Ri))) continue;
-                    T r[3], R, u[3], om[3];
-                    PartOps<T>::load(a, i, x - c[0], y - c[1], z - c[2], r, R, u, om);
-                    const T cf0 = (T)c[0], cf1 = (T)c[1], cf2 = (T)c[2];
-                    const T t = link_fraction<T>(r, cf0, cf1, cf2, (T)c2(q), R);
-                    const T rb[3] = {r[0] + t * cf0, r[1] + t * cf1, r[2] + t * cf2};
-                    const T w2 = T(2) * wq<T>(q);
-                    const T F[3] = {w2 * cf0, w2 * cf1, w2 * cf2};
-                    const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2],
-                                     rb[0] * F[1] - rb[1] * F[0]};
-                    lane_accumulate<T>(i, F, Tq, key, acc, a.acc_d, a.acc_i, a.status);
+                for (int d = 0; d < 3; ++d) {
+                    if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
+                    v[d] = wrap_idx(v[d], a.g.n[d]);
                 }
-            } else {
-                // link mask: directions whose upstream cell is solid
-#pragma unroll
-                for (int q = 1; q < Q; ++q) {
-                    int v[3] = {x - cx(q), y - cy(q), z - cz(q)};
-                    bool outside = false;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
-                        v[d] = wrap_idx(v[d], a.g.n[d]);
-                    }
-                    if (!outside && (a.flags[(long long)v[2] * plane + (long long)v[1] * nx + v[0]] & FL_SOLID))
-                        mask |= 1u << q;
-                }
+                if (!outside && (a.flags[(long long)v[2] * plane + (long long)v[1] * nx + v[0]] & FL_SOLID))
+                    mask |= 1u << q;
             }
         }
         // spread the warp's links evenly over its lanes: inclusive prefix sum
@@ -398,127 +492,145 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
             const int sz = __shfl_sync(FULL, z, src);
             const unsigned sm = __shfl_sync(FULL, mask, src);
             const int sex = __shfl_sync(FULL, excl, src);
-            if (kk < total) {
-                const int q = (int)__fns(sm, 0, kk - sex + 1);
-                particle_link<S, T>(a, sx, sy, sz, q, key, acc);
-            }
+            if (kk < total) particle_link<S, T>(a, sx, sy, sz, (int)__fns(sm, 0, kk - sex + 1), acc, sk);
         }
-        commit_forces<T>(key, acc, a.acc_d, a.acc_i, a.status);
+        commit<T>(acc, sk);
+    }
+
+    // ------------------------------------------- missing links (Sec. 2.2)
+    if (!a.missing_links) return;
+    const int mcount = min(*a.miss_count, a.miss_cap);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < mcount; base += stride) {
+        const long long k = base + threadIdx.x;
+        Acc<T> acc;
+        if (k < mcount) missing_links<S, T>(a, (long long)a.miss[k], acc, sk);
+        commit<T>(acc, sk);
     }
 }
 
 // ------------------------------------------------------------------ stream + collide
 
 template <typename S, typename T>
-__global__ void __launch_bounds__(256) stream_collide_kernel(const SCArgs<S, T> a) {
+__global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x >= nx || y >= ny) return;
+    const bool valid = x < nx && y < ny;
     const long long plane = (long long)nx * ny;
     const long long N = a.g.ncells;
     const long long idx = (long long)z * plane + (long long)y * nx + x;
-    const uint8_t fl = a.flags[idx];
-    if (fl & FL_SOLID) return;
+    const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
+    const bool fluid = !(fl & FL_SOLID);
+    // Solid cells that share a 32-byte sector with fluid cells also write
+    // (zeros; solid slots are never read before the boundary kernel rewrites
+    // them), so every written sector is complete and L2 needs no fill read.
+    constexpr int G = 32 / (int)sizeof(S);
+    const unsigned bal = __ballot_sync(0xffffffffu, fluid && valid);
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = (G >= 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
 
-    const int X3[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-    const int Y3[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-    const int Z3[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-#define NB(dx, dy, dz) ((long long)Z3[1 + (dz)] * plane + (long long)Y3[1 + (dy)] * nx + X3[1 + (dx)])
-    T f[Q];
+    if (!fluid) {
+        if (valid && (bal & gmask)) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) f[q] = Store<S>::load(a.src + (long long)q * N + NB(-cx(q), -cy(q), -cz(q)));
-#undef NB
-    // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
-    const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
-    const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
-    const bool wz = !a.g.per[2] && (z == 0 || z == nz - 1);
-    if (wx || wy || wz) {
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            const int u0 = x - cx(q), u1 = y - cy(q), u2 = z - cz(q);
-            int axis = -1, side = 0;
-            if (wz && (u2 < 0 || u2 >= nz)) { axis = 2; side = u2 < 0 ? 0 : 1; }
-            else if (wy && (u1 < 0 || u1 >= ny)) { axis = 1; side = u1 < 0 ? 0 : 1; }
-            else if (wx && (u0 < 0 || u0 >= nx)) { axis = 0; side = u0 < 0 ? 0 : 1; }
-            if (axis < 0) continue;
-            const int p = opp(q);
-            const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
-                          a.uw[side][axis][2] * (T)(-cz(q));
-            f[q] = Store<S>::load(a.src + (long long)p * N + idx) - T(6) * wq<T>(p) * ucp;
+            for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, T(0));
         }
+        return;
     }
-
-    // ------------------------------------------- TRT+aB collision
-    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        drho += f[q];
-        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
-        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
-        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
-    }
-    const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
-    const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
-    const T usq = ux * ux + uy * uy + uz * uz;
-    const T ua = ux * ax + uy * ay + uz * az;
-    const T sp = a.s_plus, sm = a.s_minus;
-    const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
-    T fo[Q];
     {
-        const T w0 = wq<T>(0);
-        const T feq0 = w0 * (drho - T(1.5) * usq);
-        fo[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua));
-    }
+        const int X3[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int Y3[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        const int Z3[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+#define NB(dx, dy, dz) ((long long)Z3[1 + (dz)] * plane + (long long)Y3[1 + (dy)] * nx + X3[1 + (dx)])
+        T f[Q];
 #pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const int qb = opp(q);
-        if (qb < q) continue;
-        const T w = wq<T>(q);
-        const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
-        const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
-        const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
-        const T em = w * (T(3) * cu);
-        const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
-        const T Fm = w * (T(3) * ca);
-        const T fp = T(0.5) * (f[q] + f[qb]);
-        const T fm = T(0.5) * (f[q] - f[qb]);
-        const T dp = -sp * (fp - ep) + gp * Fp;
-        const T dm = -sm * (fm - em) + gm * Fm;
-        fo[q] = f[q] + dp + dm;
-        fo[qb] = f[qb] + dp - dm;
-    }
-    const bool shell = (fl & FL_SHELL) != 0;
-    if (shell || a.bulk_corr) {
-        // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) relax with s_b
-        const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
-        T saxis = T(0), sdiag = T(0);
+        for (int q = 0; q < Q; ++q) f[q] = Store<S>::load(a.src + (long long)q * N + NB(-cx(q), -cy(q), -cz(q)));
+#undef NB
+        // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
+        const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
+        const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
+        const bool wz = !a.g.per[2] && (z == 0 || z == nz - 1);
+        if (wx || wy || wz) {
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const int u0 = x - cx(q), u1 = y - cy(q), u2 = z - cz(q);
+                int axis = -1, side = 0;
+                if (wz && (u2 < 0 || u2 >= nz)) { axis = 2; side = u2 < 0 ? 0 : 1; }
+                else if (wy && (u1 < 0 || u1 >= ny)) { axis = 1; side = u1 < 0 ? 0 : 1; }
+                else if (wx && (u0 < 0 || u0 >= nx)) { axis = 0; side = u0 < 0 ? 0 : 1; }
+                if (axis < 0) continue;
+                const int p = opp(q);
+                const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
+                              a.uw[side][axis][2] * (T)(-cz(q));
+                f[q] = Store<S>::load(a.src + (long long)p * N + idx) - T(6) * wq<T>(p) * ucp;
+            }
+        }
+
+        // ------------------------------------------- TRT+aB collision (in place)
+        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            drho += f[q];
+            if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
+            if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
+            if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
+        }
+        const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
+        const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
+        const T usq = ux * ux + uy * uy + uz * uz;
+        const T ua = ux * ax + uy * ay + uz * az;
+        const T sp = a.s_plus, sm = a.s_minus;
+        const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
+        // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) of the streamed
+        // PDFs relax with s_b in shell cells (and everywhere when Lambda_b,bulk != 1)
+        const bool shell = (fl & FL_SHELL) != 0;
+        const bool bulk = shell || a.bulk_corr;
+        T k4 = T(0), k5 = T(0);
+        if (bulk) {
+            const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
+            T saxis = T(0), sdiag = T(0);
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
+            }
+            const T m4 = -f[0] + sdiag;
+            const T m5 = f[0] - T(2) * saxis + sdiag;
+            // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
+            k4 = T(1.5) * (ds * ((usq - m4) - ua));
+            k5 = T(0.5) * (ds * (-m5));
+        }
+        {
+            const T w0 = wq<T>(0);
+            const T feq0 = w0 * (drho - T(1.5) * usq);
+            f[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua)) + w0 * (k5 - k4);
+        }
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
-            if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
+            const int qb = opp(q);
+            if (qb < q) continue;
+            const T w = wq<T>(q);
+            const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
+            const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
+            const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
+            const T em = w * (T(3) * cu);
+            const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
+            const T Fm = w * (T(3) * ca);
+            const T fp = T(0.5) * (f[q] + f[qb]);
+            const T fm = T(0.5) * (f[q] - f[qb]);
+            const T corr = c2(q) == 1 ? w * (T(-2) * k5) : w * (k4 + k5);
+            const T dp = -sp * (fp - ep) + gp * Fp + corr;
+            const T dm = -sm * (fm - em) + gm * Fm;
+            f[q] = f[q] + dp + dm;
+            f[qb] = f[qb] + dp - dm;
         }
-        const T m4 = -f[0] + sdiag;
-        const T m5 = f[0] - T(2) * saxis + sdiag;
-        const T dm4 = ds * ((usq - m4) - ua);
-        const T dm5 = ds * (-m5);
-        // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
-        const T k4 = T(1.5) * dm4, k5 = T(0.5) * dm5;
-        fo[0] += wq<T>(0) * (-k4 + k5);
+        if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
 #pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            if (c2(q) == 1) fo[q] += wq<T>(q) * (T(-2) * k5);
-            else fo[q] += wq<T>(q) * (k4 + k5);
-        }
+        for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, f[q]);
     }
-    if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, fo[q]);
 }
 
 template <typename S>
-void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
-    using T = typename Store<S>::T;
+void launch_boundary_t(const LbmStepParams& p, cudaStream_t st) {
     BcArgs<S> b;
     b.src = static_cast<S*>(const_cast<void*>(p.src));
     b.flags = p.flags;
@@ -527,6 +639,9 @@ void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
     b.list = p.near_list;
     b.count = p.near_count;
     b.cap = p.near_cap;
+    b.miss = p.miss_list;
+    b.miss_count = p.miss_count;
+    b.miss_cap = p.miss_cap;
     b.px = p.P.x;
     b.pu = p.P.u;
     b.pom = p.P.om;
@@ -534,6 +649,7 @@ void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
     b.view = p.P.view;
     b.acc_d = p.P.acc_d;
     b.acc_i = p.P.acc_i;
+    b.acc_k = p.P.acc_k;
     b.missing_links = p.missing_links;
     b.status = p.status;
     for (int d = 0; d < 3; ++d) {
@@ -546,7 +662,11 @@ void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
     b.accel_f = p.accel_f;
     const int bblocks = p.near_blocks > 0 ? p.near_blocks : 1;
     boundary_kernel<S><<<bblocks, 256, 0, st>>>(b);
+}
 
+template <typename S>
+void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
+    using T = typename Store<S>::T;
     SCArgs<S, T> a;
     a.src = static_cast<const S*>(p.src);
     a.dst = static_cast<S*>(p.dst);
@@ -570,12 +690,21 @@ void launch_step_t(const LbmStepParams& p, cudaStream_t st) {
     stream_collide_kernel<S, T><<<grid, block, 0, st>>>(a);
 }
 
-void launch_lbm_step(const LbmStepParams& p, cudaStream_t st) {
+void launch_boundary(const LbmStepParams& p, cudaStream_t st) {
     switch (p.storage) {
-        case 0: launch_step_t<double>(p, st); break;
-        case 1: launch_step_t<float>(p, st); break;
-        case 2: launch_step_t<__half>(p, st); break;
-        default: launch_step_t<__nv_bfloat16>(p, st); break;
+        case 0: launch_boundary_t<double>(p, st); break;
+        case 1: launch_boundary_t<float>(p, st); break;
+        case 2: launch_boundary_t<__half>(p, st); break;
+        default: launch_boundary_t<__nv_bfloat16>(p, st); break;
+    }
+}
+
+void launch_stream_collide(const LbmStepParams& p, cudaStream_t st) {
+    switch (p.storage) {
+        case 0: launch_stream_collide_t<double>(p, st); break;
+        case 1: launch_stream_collide_t<float>(p, st); break;
+        case 2: launch_stream_collide_t<__half>(p, st); break;
+        default: launch_stream_collide_t<__nv_bfloat16>(p, st); break;
     }
 }
 

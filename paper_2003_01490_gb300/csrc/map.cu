@@ -103,13 +103,43 @@ void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
 
 // ------------------------------------------------------------ mapping
 
-// per candidate: offset of the tile's first cell centre from the particle
-// centre (image nearest to the tile unless the axis is short) and R^2;
-// thresholds of the shell and near tests and the float32 tolerances
+// block-aggregated append: one global atomic per block and list
+__device__ __forceinline__ void block_append(bool take, unsigned int entry, unsigned int* list, int* count, int cap,
+                                             int* status, int* s_warp, int* s_base) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    const unsigned am = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) s_warp[warp] = __popc(am);
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            const int c = s_warp[w];
+            s_warp[w] = tot;
+            tot += c;
+        }
+        *s_base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (take) {
+        const int slot = *s_base + s_warp[warp] + __popc(am & ((1u << lane) - 1u));
+        if (slot < cap) list[slot] = entry;
+        else atomicOr(status, ST_REFILL_OVERFLOW);
+    }
+    __syncthreads();
+}
+
+// Per candidate: integer offset n0 of the tile's first cell from the
+// particle's base cell (for long periodic axes already moved to the image
+// nearest to the tile), the common fractional offset g = 1/2 - frac, R^2, and
+// the thresholds of the shell and near tests with their float32 tolerances.
+// A cell's offset is (float)(n0 + l) + g: integer first, so no float32
+// intermediate is larger than the offset itself.
 __global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
+    __shared__ int4 cn[TILE_CAP];
     __shared__ float4 ca[TILE_CAP];
     __shared__ float4 cb[TILE_CAP];
-    __shared__ int cid[TILE_CAP];
     __shared__ int ncand;
     __shared__ unsigned int nsolid_blk;
     const long long t = ((long long)blockIdx.z * p.ntile[1] + blockIdx.y) * p.ntile[0] + blockIdx.x;
@@ -125,24 +155,26 @@ __global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
         const int i = p.tile_list[t * TILE_CAP + tid];
         const PartView v = p.P.view[i];
         const int ts[3] = {TILE_X, TILE_Y, TILE_Z};
-        float r[3];
+        int n0[3];
+        float g[3];
         for (int d = 0; d < 3; ++d) {
-            r[d] = (float)(org[d] - v.base[d]) + (0.5f - v.frac[d]);
+            n0[d] = org[d] - v.base[d];
+            g[d] = 0.5f - v.frac[d];
             if (p.g.per[d] && !p.small[d]) {
                 // image nearest to the tile centre
-                const float L = (float)p.g.n[d];
-                const float c = r[d] + 0.5f * (float)(ts[d] - 1);
-                if (c > 0.5f * L) r[d] -= L;
-                else if (c < -0.5f * L) r[d] += L;
+                const int L = p.g.n[d];
+                const float c = (float)(2 * n0[d] + ts[d] - 1) + 2.0f * g[d];   // twice the centre offset
+                if (c > (float)L) n0[d] -= L;
+                else if (c < -(float)L) n0[d] += L;
             }
         }
         const float R = v.R;
         const float Rs = R + (float)p.shell_width;
         const float Rn = R + 1.4142135f + 0.02f;
         const float R2 = R * R, Rs2 = Rs * Rs;
-        ca[tid] = make_float4(r[0], r[1], r[2], R2);
+        cn[tid] = make_int4(n0[0], n0[1], n0[2], i);
+        ca[tid] = make_float4(g[0], g[1], g[2], R2);
         cb[tid] = make_float4(Rs2, Rn * Rn, 1e-5f * (R2 + 1.0f), 1e-5f * (Rs2 + 1.0f));
-        cid[tid] = i;
     }
     __syncthreads();
 
@@ -151,31 +183,41 @@ __global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
     const int z = org[2] + threadIdx.z;
     const bool valid = x < p.g.n[0] && y < p.g.n[1] && z < p.g.n[2];
     bool solid = false;
-    bool append = false;       // into the near-boundary list of the next step
+    bool near_fluid = false;   // into the particle-link list of the next step
+    bool miss_solid = false;   // into the missing-link list of the next step
     unsigned int entry = 0;
     if (valid) {
         const long long idx = ((long long)z * p.g.n[1] + y) * p.g.n[0] + x;
         const int cpos[3] = {x, y, z};
-        const float lx = (float)threadIdx.x, ly = (float)threadIdx.y, lz = (float)threadIdx.z;
+        const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
         const bool any_small = p.small[0] | p.small[1] | p.small[2];
         int own = 0x7fffffff;
         bool shell = false;
         int nnear = 0;
         for (int k = 0; k < ncand; ++k) {
+            const int4 Nn = cn[k];
             const float4 A = ca[k];
-            float dx = A.x + lx, dy = A.y + ly, dz = A.z + lz;
+            int n[3] = {Nn.x + lx, Nn.y + ly, Nn.z + lz};
             if (any_small) {
-                dx = p.small[0] ? min_image_ff(dx, p.g.n[0], 1) : dx;
-                dy = p.small[1] ? min_image_ff(dy, p.g.n[1], 1) : dy;
-                dz = p.small[2] ? min_image_ff(dz, p.g.n[2], 1) : dz;
+                const float gg[3] = {A.x, A.y, A.z};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (!p.small[d]) continue;
+                    // minimum image decided on 2 (n + g) against L
+                    const int L = p.g.n[d];
+                    const float tw = (float)(2 * n[d]) + 2.0f * gg[d];
+                    if (tw > (float)L) n[d] -= L;
+                    else if (tw < -(float)L) n[d] += L;
+                }
             }
+            const float dx = (float)n[0] + A.x, dy = (float)n[1] + A.y, dz = (float)n[2] + A.z;
             const float d2f = (dx * dx + dy * dy) + dz * dz;
             const float4 B = cb[k];
             if (d2f <= B.y) ++nnear;
             if (d2f > B.x + B.w) continue;
             const bool exact_needed = fabsf(d2f - A.w) <= B.z || fabsf(d2f - B.x) <= B.w;
             bool inside, in_shell;
-            const int id = cid[k];
+            const int id = Nn.w;
             if (!exact_needed) {
                 inside = d2f < A.w;
                 in_shell = !inside && d2f < B.x;
@@ -205,16 +247,14 @@ __global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
             nf = FL_SOLID;
             if (nnear >= 2 || wall_adj) {
                 nf |= FL_MISS;
-                append = true;
-                entry = 0x80000000u | (unsigned int)idx;
+                miss_solid = true;
             }
             p.owner[idx] = own;
         } else {
             if (shell) nf |= FL_SHELL;
             if (nnear >= 1) {
                 nf |= FL_NEAR;
-                append = true;
-                entry = (unsigned int)idx;
+                near_fluid = true;
             }
             if (old & FL_SOLID) {
                 nf |= FL_NEWFLUID;
@@ -224,21 +264,13 @@ __global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
             }
         }
         p.flags[idx] = nf;
+        entry = (unsigned int)idx;
     }
-    // warp-aggregated append to the near-boundary list
-    const unsigned am = __ballot_sync(0xffffffffu, append);
-    if (am) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(am) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(p.near_count, __popc(am));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (append) {
-            const int slot = base + __popc(am & ((1u << lane) - 1u));
-            if (slot < p.near_cap) p.near_list[slot] = entry;
-            else atomicOr(p.status, ST_REFILL_OVERFLOW);
-        }
-    }
+    // block-aggregated appends to the particle-link and missing-link lists
+    __shared__ int s_warp[16];
+    __shared__ int s_base;
+    block_append(near_fluid, entry, p.near_list, p.near_count, p.near_cap, p.status, s_warp, &s_base);
+    block_append(miss_solid, entry, p.miss_list, p.miss_count, p.miss_cap, p.status, s_warp, &s_base);
     unsigned bal = __ballot_sync(0xffffffffu, solid);
     if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&nsolid_blk, (unsigned)__popc(bal));
     __syncthreads();
@@ -269,7 +301,7 @@ __global__ void refill_kernel(const RefillParams p) {
         const int z = (int)(idx / ((long long)nx * ny));
         const int cpos[3] = {x, y, z};
         const int i = p.owner[idx];
-        T rho_sum = T(0);
+        T drho_sum = T(0);    // neighbour densities minus rho0 (shifted, no cancellation)
         int nnb = 0;
         T uax[6][3];      // velocities of the axis neighbours +x -x +y -y +z -z
         bool okax[6] = {false, false, false, false, false, false};
@@ -295,7 +327,7 @@ __global__ void refill_kernel(const RefillParams p) {
                 jy += (T)cy(r) * v;
                 jz += (T)cz(r) * v;
             }
-            rho_sum += T(1) + dr;
+            drho_sum += dr;
             ++nnb;
             const int slot = c2(q) != 1 ? -1 : (cx(q) == 1 ? 0 : cx(q) == -1 ? 1 : cy(q) == 1 ? 2 : cy(q) == -1 ? 3 : cz(q) == 1 ? 4 : 5);
             if (slot >= 0) {
@@ -305,7 +337,8 @@ __global__ void refill_kernel(const RefillParams p) {
                 uax[slot][2] = jz - T(0.5) * az;
             }
         }
-        const T rb = nnb ? rho_sum / (T)nnb : T(1);
+        const T drb = nnb ? drho_sum / (T)nnb : T(0);
+        const T rb = T(1) + drb;
         // velocity of the former particle at the cell centre (rigid body)
         T ut[3], rr[3];
 #pragma unroll
@@ -347,8 +380,9 @@ __global__ void refill_kernel(const RefillParams p) {
                     second += pab * (c[a] * c[b] - (a == b ? T(1) / T(3) : T(0)));
                 }
             const T cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
-            const T fq = wq<T>(q) * (rb + T(3) * rb * cu + T(4.5) * second);
-            Store<S>::store(fw + (long long)q * N + idx, fq - wq<T>(q));
+            // f_q - w_q written without forming f_q: w_q (rho_bar - 1) + ...
+            const T dfq = wq<T>(q) * (drb + T(3) * rb * cu + T(4.5) * second);
+            Store<S>::store(fw + (long long)q * N + idx, dfq);
         }
     }
 }

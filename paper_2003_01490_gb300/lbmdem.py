@@ -255,7 +255,7 @@ def lbm_set_pdfs(ctx, f):
     _check(load_library().lbm_set_pdfs(ctx.handle, _dptr(f)), ctx.handle)
 
 
-PHASES = ('stream_collide', 'force_finalize', 'dem', 'mapping', 'refill')
+PHASES = ('boundary', 'stream_collide', 'force_finalize', 'dem', 'mapping', 'refill')
 
 
 def lbm_profile(ctx, enable):
@@ -264,7 +264,7 @@ def lbm_profile(ctx, enable):
 
 def lbm_profile_read(ctx):
     """Return ({phase: total ms}, timed steps) of the CUDA-event phase timing."""
-    ms = (c_double * 5)()
+    ms = (c_double * len(PHASES))()
     steps = ctypes.c_longlong(0)
     _check(load_library().lbm_profile_read(ctx.handle, ms, ctypes.byref(steps)), ctx.handle)
     return dict(zip(PHASES, list(ms))), steps.value
