@@ -195,6 +195,9 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(8 * 3 * n);                            // 51 u
     L.add(8 * 3 * n);                            // 52 om
     L.add(4 * 3 * n);                            // 53 xf
+    L.add(8 * n);                                // 54 hm
+    L.add(8 * n);                                // 55 hI
+    L.add(8 * 3 * n);                            // 56 ext
     (void)g;
 }
 
@@ -297,6 +300,9 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->P.us[1] = (double*)at(51);
     ctx->P.oms[1] = (double*)at(52);
     ctx->P.xfs[1] = (float*)at(53);
+    ctx->P.hm = (double*)at(54);
+    ctx->P.hI = (double*)at(55);
+    ctx->P.ext = (double*)at(56);
     ctx->scratch = (double*)at(11);
     ctx->scratch_cells = s.scratch_cells;
     ctx->bin_cap = s.bin_cap;
@@ -560,7 +566,8 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
         return LBM_OK;
     }
     const double pi = 3.14159265358979323846;
-    std::vector<double> x(3 * n), u(3 * n, 0.0), om(3 * n, 0.0), R(n), rho(n), m(n), I(n);
+    std::vector<double> x(3 * n), u(3 * n, 0.0), om(3 * n, 0.0), R(n), rho(n), m(n), I(n), hm(n), hI(n),
+        ext(3 * n);
     for (int k = 0; k < n; ++k) {
         for (int a = 0; a < 3; ++a) {
             x[3 * k + a] = pos[3 * k + a];
@@ -573,7 +580,12 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
         const double V = pi * D * D * D / 6.0;
         m[k] = rho[k] * V;
         I[k] = 0.4 * m[k] * R[k] * R[k];
-        for (int a = 0; a < 3; ++a) ctx->ext_total[a] += V * (rho[k] - 1.0) * ctx->dem.gravity[a];
+        hm[k] = 0.5 / m[k];
+        hI[k] = 0.5 / I[k];
+        for (int a = 0; a < 3; ++a) {
+            ext[3 * k + a] = V * (rho[k] - 1.0) * ctx->dem.gravity[a];
+            ctx->ext_total[a] += ext[3 * k + a];
+        }
         if (R[k] > ctx->r_max) ctx->r_max = R[k];
     }
     cudaStream_t sm = ctx->stream;
@@ -585,6 +597,9 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     CK(cudaMemcpyAsync(P.rho + n0, rho.data(), 8 * n, cudaMemcpyHostToDevice, sm));
     CK(cudaMemcpyAsync(P.m + n0, m.data(), 8 * n, cudaMemcpyHostToDevice, sm));
     CK(cudaMemcpyAsync(P.I + n0, I.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.hm + n0, hm.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.hI + n0, hI.data(), 8 * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(P.ext + 3 * n0, ext.data(), 8 * 3 * n, cudaMemcpyHostToDevice, sm));
     P.n = n0 + n;
     ctx->hx.swap(hx);
     ctx->hR.swap(hR);

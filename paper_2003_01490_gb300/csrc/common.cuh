@@ -114,6 +114,9 @@ struct Particles {
     double* rho;           // [n]  density ratios rho_p / rho_f
     double* m;             // [n]  masses rho_p pi D^3 / 6
     double* I;             // [n]  moments of inertia 2/5 m R^2
+    double* hm;            // [n]  1 / (2 m)
+    double* hI;            // [n]  1 / (2 I)
+    double* ext;           // [3n] external force V (rho_p - rho_f) g
     double* F_prev;        // [3n] total force of the last subcycle
     double* T_prev;        // [3n]
     double* F_new;         // [3n] total force of the current subcycle

@@ -86,7 +86,7 @@ __global__ void finalize_kernel(const FinalizeParams p) {
         // with g = 1/2 - (x - floor(x)) the common fractional cell offset
         double k[6], g[3];
         for (int c = 0; c < 6; ++c) {
-            k[c] = (double)p.P.acc_k[6 * i + c] / 36.0;
+            k[c] = (double)p.P.acc_k[6 * i + c] * (1.0 / 36.0);
             p.P.acc_k[6 * i + c] = 0;
         }
         for (int d = 0; d < 3; ++d) {
@@ -206,9 +206,8 @@ __device__ __forceinline__ double wrap_pos(double x, int n, int per) {
 
 __device__ __forceinline__ void position_update(const DemParams& p, int i) {
     // Eq. (37): x += dt u + dt^2 / (2 m) F
-    const double m = p.P.m[i];
     const double dt = p.dt;
-    const double c = dt * dt / (2.0 * m);
+    const double c = dt * dt * p.P.hm[i];
     for (int d = 0; d < 3; ++d) {
         const double x = wrap_pos(p.P.x[3 * i + d] + dt * p.P.u[3 * i + d] + c * p.P.F_prev[3 * i + d],
                                   p.g.n[d], p.g.per[d]);
@@ -432,49 +431,65 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
             }
         }
     }
-    // sum the four lanes of the particle
+    // sum the four lanes of a particle, in warps where any lane interacted
+    const unsigned FULL = 0xffffffffu;
+    const bool hit = F.x != 0.0 || F.y != 0.0 || F.z != 0.0 || T.x != 0.0 || T.y != 0.0 || T.z != 0.0;
+    if (__ballot_sync(FULL, hit)) {
 #pragma unroll
-    for (int o = 1; o < GROUP; o <<= 1) {
-        F.x += __shfl_xor_sync(0xffffffffu, F.x, o);
-        F.y += __shfl_xor_sync(0xffffffffu, F.y, o);
-        F.z += __shfl_xor_sync(0xffffffffu, F.z, o);
-        T.x += __shfl_xor_sync(0xffffffffu, T.x, o);
-        T.y += __shfl_xor_sync(0xffffffffu, T.y, o);
-        T.z += __shfl_xor_sync(0xffffffffu, T.z, o);
+        for (int o = 1; o < GROUP; o <<= 1) {
+            F.x += __shfl_xor_sync(FULL, F.x, o);
+            F.y += __shfl_xor_sync(FULL, F.y, o);
+            F.z += __shfl_xor_sync(FULL, F.z, o);
+            T.x += __shfl_xor_sync(FULL, T.x, o);
+            T.y += __shfl_xor_sync(FULL, T.y, o);
+            T.z += __shfl_xor_sync(FULL, T.z, o);
+        }
     }
-    if (!act || sub != 0) return;
-    const double vol = P.m[i] / P.rho[i];
-    F = F + mk(P.fbar[6 * i], P.fbar[6 * i + 1], P.fbar[6 * i + 2]) +
-        (vol * (P.rho[i] - 1.0)) * mk(p.gravity[0], p.gravity[1], p.gravity[2]);
-    T = T + mk(P.fbar[6 * i + 3], P.fbar[6 * i + 4], P.fbar[6 * i + 5]);
+    // hand the sums to one lane per particle (warp 0 of the block), so the
+    // float64 integration runs with every lane of the warp busy
+    constexpr int PPB = 128 / GROUP;   // particles per block
+    __shared__ double sFT[PPB][6];
+    const int local = threadIdx.x / GROUP;
+    if (sub == 0) {
+        sFT[local][0] = F.x; sFT[local][1] = F.y; sFT[local][2] = F.z;
+        sFT[local][3] = T.x; sFT[local][4] = T.y; sFT[local][5] = T.z;
+    }
+    __syncthreads();
+    if (threadIdx.x >= PPB) return;
+    const int ip = blockIdx.x * PPB + threadIdx.x;
+    if (ip >= P.n) return;
+    const V3 Fs = mk(sFT[threadIdx.x][0] + P.fbar[6 * ip] + P.ext[3 * ip],
+                     sFT[threadIdx.x][1] + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
+                     sFT[threadIdx.x][2] + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
+    const V3 Ts = mk(sFT[threadIdx.x][3] + P.fbar[6 * ip + 3], sFT[threadIdx.x][4] + P.fbar[6 * ip + 4],
+                     sFT[threadIdx.x][5] + P.fbar[6 * ip + 5]);
     if (init) {
-        st3(P.F_prev, i, F);
-        st3(P.T_prev, i, T);
+        st3(P.F_prev, ip, Fs);
+        st3(P.T_prev, ip, Ts);
         return;
     }
-    P.hist_n[hout][i] = P.nbr_count[i];
-    // Eq. (38) for u and its rotational analogue for omega
-    const double m = P.m[i], I = P.I[i];
-    const double cu = p.dt / (2.0 * m), co = p.dt / (2.0 * I);
-    const V3 Fp = ld3(P.F_prev, i), Tp = ld3(P.T_prev, i);
-    const V3 u = ld3(Uv, i) + cu * (Fp + F);
-    const V3 om = ld3(Om, i) + co * (Tp + T);
-    st3(P.F_prev, i, F);
-    st3(P.T_prev, i, T);
+    P.hist_n[hout][ip] = P.nbr_count[ip];
+    // Eq. (38) for u and its rotational analogue for omega (hm = 1/(2m), hI = 1/(2I))
+    const double cu = p.dt * P.hm[ip], co = p.dt * P.hI[ip];
+    const V3 Fp = ld3(P.F_prev, ip), Tp = ld3(P.T_prev, ip);
+    const V3 u = ld3(Uv, ip) + cu * (Fp + Fs);
+    const V3 om = ld3(Om, ip) + co * (Tp + Ts);
+    st3(P.F_prev, ip, Fs);
+    st3(P.T_prev, ip, Ts);
     if (!(dot(u, u) < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
     const int nxt = 1 - cur;
-    st3(P.us[nxt], i, u);
-    st3(P.oms[nxt], i, om);
+    st3(P.us[nxt], ip, u);
+    st3(P.oms[nxt], ip, om);
     const double ua[3] = {u.x, u.y, u.z};
-    const double Fa[3] = {F.x, F.y, F.z};
-    const double c = p.dt * p.dt / (2.0 * m);
+    const double Fa[3] = {Fs.x, Fs.y, Fs.z};
+    const double c = p.dt * cu;
     PartView v;
     for (int d = 0; d < 3; ++d) {
         // Eq. (37) for the next subcycle; the last subcycle keeps its positions
-        double x = X[3 * i + d];
+        double x = X[3 * ip + d];
         if (!last) x = wrap_pos(x + p.dt * ua[d] + c * Fa[d], p.g.n[d], p.g.per[d]);
-        P.xs[nxt][3 * i + d] = x;
-        P.xfs[nxt][3 * i + d] = (float)x;
+        P.xs[nxt][3 * ip + d] = x;
+        P.xfs[nxt][3 * ip + d] = (float)x;
         if (last) {
             const double b = floor(x);
             v.base[d] = (int)b;
@@ -484,9 +499,9 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
         }
     }
     if (last) {
-        v.R = (float)P.R[i];
+        v.R = (float)P.R[ip];
         v.pad = 0.f;
-        P.view[i] = v;
+        P.view[ip] = v;
     }
 }
 
