@@ -190,6 +190,37 @@ lbm_status lbm_sync(lbm_ctx *ctx);
 lbm_status lbm_profile(lbm_ctx *ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
 
+/* Sphere-to-cell mapping that allocates no device memory. The paper has no
+ * counterpart of this call; it serves callers that cannot call cudaMalloc,
+ * for instance a host framework that owns all device memory through its own
+ * pool and forbids other allocations, or a loop that cannot afford the device
+ * synchronisation an allocation may cause.
+ *
+ * Unlike the other calls, every array argument is DEVICE memory owned by the
+ * caller: d_pos (n x 3 doubles) and d_radius (n doubles) are read; d_flags
+ * (nx*ny*nz bytes, LBM_FLAG_SOLID/SHELL/NEAR/MISS bits) and d_owner (nx*ny*nz
+ * int32, the lowest sphere index whose sphere holds the cell centre, -1 for
+ * fluid) are cleared and written, x fastest, as lbm_add_spheres() maps the same
+ * spheres into a new context (Sec. 2.2 solid test, Sec. 2.3.2 shell of width
+ * shell_width). grid->wall_vel_* are ignored.
+ *
+ * The temporary tile lists live in one file-scope device array of about 29 MB
+ * that every GPU which loads the library holds until the process exits.
+ * Limits: at most 98,304 mapping tiles of 32 x 4 x 4 cells (for example
+ * 256 x 256 x 512 cells) and 65,536 spheres; larger inputs return
+ * LBM_ERR_INVALID before any work. The first call on a device looks up the
+ * device address of that array with the device current; make that first call
+ * before any stream capture. All calls share the array and it keeps the
+ * contents of the last call, so calls that overlap on the GPU (different
+ * streams or devices sharing a context) race: serialise them. The call queues
+ * its work on cuda_stream (a cudaStream_t, NULL = legacy default stream) and
+ * synchronises that stream before returning. Errors: LBM_ERR_INVALID,
+ * LBM_ERR_CAPACITY (more than 64 spheres reach one tile), LBM_ERR_CUDA; the
+ * message is returned by lbm_last_error(NULL). */
+lbm_status lbm_map_spheres_noalloc(const lbm_grid *grid, double shell_width, int n,
+                                   const double *d_pos, const double *d_radius,
+                                   unsigned char *d_flags, int *d_owner, void *cuda_stream);
+
 /* Number of kernel launches this context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);
 

@@ -24,7 +24,8 @@ STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CU
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
-           'lbm_profile_read', 'lbm_launch_count', 'lbm_last_error', 'lbm_destroy')
+           'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
+           'lbm_destroy')
 
 c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -85,6 +86,8 @@ def load_library(path=LIB_PATH):
     lib.lbm_sync.argtypes = [c_void_p]
     lib.lbm_profile.argtypes = [c_void_p, c_int]
     lib.lbm_profile_read.argtypes = [c_void_p, dp, P(ctypes.c_longlong)]
+    lib.lbm_map_spheres_noalloc.argtypes = [P(LbmGrid), c_double, c_int, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p]
     lib.lbm_launch_count.argtypes = [c_void_p]
     lib.lbm_launch_count.restype = ctypes.c_longlong
     lib.lbm_last_error.argtypes = [c_void_p]
@@ -268,6 +271,24 @@ def lbm_profile_read(ctx):
     steps = ctypes.c_longlong(0)
     _check(load_library().lbm_profile_read(ctx.handle, ms, ctypes.byref(steps)), ctx.handle)
     return dict(zip(PHASES, list(ms))), steps.value
+
+
+def lbm_map_spheres_noalloc(grid, shell_width, pos, radius, flags, owner):
+    """Map spheres into caller-owned device buffers without any device allocation.
+
+    pos (n x 3 float64), radius (n float64), flags (cells uint8) and owner
+    (cells int32) are CUDA tensors; the work runs on PyTorch's current stream.
+    """
+    import torch
+    n = radius.numel()
+    for t, dt in ((pos, torch.float64), (radius, torch.float64), (flags, torch.uint8), (owner, torch.int32)):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
+            raise ValueError('expected contiguous CUDA tensors of the documented dtypes')
+    stream = torch.cuda.current_stream(pos.device).cuda_stream
+    _check(load_library().lbm_map_spheres_noalloc(ctypes.byref(grid), float(shell_width), int(n),
+                                                  c_void_p(pos.data_ptr()), c_void_p(radius.data_ptr()),
+                                                  c_void_p(flags.data_ptr()), c_void_p(owner.data_ptr()),
+                                                  c_void_p(stream)))
 
 
 def lbm_launch_count(ctx):
