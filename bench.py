@@ -309,7 +309,7 @@ def run_ours(args, rank, world, local):
     share = {k: round(v / sum(phases.values()), 4) for k, v in phases.items()} if sum(phases.values()) else {}
     roofline = {'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
                 'frac': round(achieved / peak, 4), 'traffic': traffic,
-                'kernel': 'lbm_step_kernel (fused stream + boundaries + momentum exchange + TRT+aB)',
+                'kernel': 'stream_collide_kernel (pull stream, wall bounce-back, TRT+aB collision)',
                 'kernel_ms_per_launch': round(k_ms, 5), 'alg_bytes_per_launch': int(alg_bytes),
                 'peak_source': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
                 else 'fallback 6.8 TB/s', 'phase_share': share}

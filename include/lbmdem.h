@@ -118,8 +118,8 @@ lbm_status lbm_required_bytes(const lbm_grid *grid, lbm_storage storage, int max
  * cudaStream_t (NULL = legacy default stream); all work of the context is
  * queued on it. The fluid starts at rest with rho = 1 and no particles.
  * Device memory is allocated by the library and released by lbm_destroy().
- * Errors: LBM_ERR_INVALID (bad sizes, tau <= 1/2, non-positive max_particles),
- * LBM_ERR_OOM, LBM_ERR_CUDA. */
+ * Errors: LBM_ERR_INVALID (bad sizes, a box of more than 2^31 - 2^24 cells,
+ * tau <= 1/2, non-positive max_particles), LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_grid *grid, const lbm_relax *relax, const double *body_force,
                       const lbm_dem *dem, lbm_storage storage, int max_particles,
                       void *cuda_stream, lbm_ctx **out);

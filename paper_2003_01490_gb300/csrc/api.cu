@@ -11,6 +11,11 @@
 #include "common.cuh"
 #include "launch.h"
 
+// resident boundary-kernel blocks per multiprocessor (grid-stride loop)
+#ifndef LBM_BC_BLOCKS_PER_SM
+#define LBM_BC_BLOCKS_PER_SM 8
+#endif
+
 using namespace lbmdem;
 
 // phases of lbm_profile(): boundary, stream+collide, force finalisation, DEM,
@@ -57,6 +62,7 @@ struct lbm_ctx {
     int hcur = 0;
     bool stepped = false;
     long long launches = 0;
+    int num_sms = 152;             // multiprocessors of the device (grid sizing)
     double ext_total[3] = {0, 0, 0};
     double r_max = 0.0;
     std::vector<double> hx, hR;    // host copies for insertion checks
@@ -150,8 +156,8 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(4 * s.ntiles);                // 4 tile_count
     L.add(4 * s.ntiles * TILE_CAP);     // 5 tile_list
     L.add(4 * (size_t)s.refill_cap);    // 6 refill_list
-    L.add(4);                           // 7 refill_count
-    L.add(8);                           // 8 n_solid
+    L.add(4);                           // 7 (unused)
+    L.add(32);                          // 8 counters: n_solid, near, miss, refill counts
     L.add(4);                           // 9 status
     L.add(8 * 3);                       // 10 accel
     L.add(8 * 4 * (size_t)s.scratch_cells);  // 11 scratch
@@ -185,11 +191,11 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
         L.add(6 * n);                            // 37/42 wact
     }
     L.add(4 * N);                                // 43 near_list
-    L.add(4);                                    // 44 near_count
+    L.add(4);                                    // 44 (unused)
     L.add(4 * 3);                                // 45 accel_f
     L.add(4 * 3 * n);                            // 46 xf
     L.add(4 * N);                                // 47 miss_list
-    L.add(4);                                    // 48 miss_count
+    L.add(4);                                    // 48 (unused)
     L.add(8 * 6 * n);                            // 49 acc_k
     L.add(8 * 3 * n);                            // 50 x (second subcycle buffer)
     L.add(8 * 3 * n);                            // 51 u
@@ -206,7 +212,9 @@ lbm_status validate(const lbm_grid* g, const lbm_relax* r, const lbm_dem* d, lbm
     if (!g || !r || !d) return fail(nullptr, LBM_ERR_INVALID, "null parameter struct");
     if (g->nx < 3 || g->ny < 3 || g->nz < 3) return fail(nullptr, LBM_ERR_INVALID, "box must be at least 3 cells per axis");
     long long nc = (long long)g->nx * g->ny * g->nz;
-    if (nc >= (1LL << 31)) return fail(nullptr, LBM_ERR_INVALID, "box has 2^31 cells or more");
+    // 32-bit cell indices in the kernels, with room for a grid-stride step
+    if (nc > (1LL << 31) - (1LL << 24))
+        return fail(nullptr, LBM_ERR_INVALID, "box has more than 2^31 - 2^24 cells");
     if (g->nz > 65535 || g->ny > 65535 * 2) return fail(nullptr, LBM_ERR_INVALID, "ny or nz too large");
     if (!(r->tau > 0.5)) return fail(nullptr, LBM_ERR_INVALID, "tau must be > 1/2");
     if (!(r->magic > 0.0) || !(r->lambda_b_shell > 0.0) || !(r->lambda_b_bulk > 0.0) || !(r->shell_width >= 0.0))
@@ -236,6 +244,12 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->elem = elem_size(st);
     ctx->max_particles = max_particles;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            ctx->num_sms = sms;
+    }
     ctx->g.n[0] = g->nx; ctx->g.n[1] = g->ny; ctx->g.n[2] = g->nz;
     for (int a = 0; a < 3; ++a) {
         ctx->g.per[a] = g->periodic[a] ? 1 : 0;
@@ -282,18 +296,21 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->tile_count = (int*)at(4);
     ctx->tile_list = (int*)at(5);
     ctx->refill_list = (unsigned int*)at(6);
-    ctx->refill_count = (int*)at(7);
     ctx->refill_cap = s.refill_cap;
+    // one 32-byte block of counters, cleared by one memset per remap; the
+    // near and missing-link counts share one 8-byte word (one 64-bit atomic
+    // of the mapping reserves slots in both lists)
     ctx->n_solid = (unsigned long long*)at(8);
+    ctx->near_count = (int*)((char*)at(8) + 8);
+    ctx->miss_count = (int*)((char*)at(8) + 12);
+    ctx->refill_count = (int*)((char*)at(8) + 16);
     ctx->status = (int*)at(9);
     ctx->accel = (double*)at(10);
     ctx->near_list = (unsigned int*)at(43);
-    ctx->near_count = (int*)at(44);
     ctx->near_cap = (int)s.ncells;
     ctx->accel_f = (float*)at(45);
     ctx->P.xf = (float*)at(46);
     ctx->miss_list = (unsigned int*)at(47);
-    ctx->miss_count = (int*)at(48);
     ctx->miss_cap = (int)s.ncells;
     ctx->P.acc_k = (long long*)at(49);
     ctx->P.xs[1] = (double*)at(50);
@@ -389,11 +406,8 @@ MapParams map_params(lbm_ctx* ctx) {
 // remap all particles: clear tile lists and counters, scatter, map
 lbm_status remap(lbm_ctx* ctx) {
     cudaStream_t sm = ctx->stream;
-    CK(cudaMemsetAsync(ctx->tile_count, 0, sizeof(int) * ctx->ntiles, sm));
-    CK(cudaMemsetAsync(ctx->refill_count, 0, sizeof(int), sm));
-    CK(cudaMemsetAsync(ctx->n_solid, 0, sizeof(unsigned long long), sm));
-    CK(cudaMemsetAsync(ctx->near_count, 0, sizeof(int), sm));
-    CK(cudaMemsetAsync(ctx->miss_count, 0, sizeof(int), sm));
+    // tile counts are zero here: the mapping kernel resets each one it reads
+    CK(cudaMemsetAsync(ctx->n_solid, 0, 24, sm));
     MapParams mp = map_params(ctx);
     launch_tile_scatter(mp, sm);
     launch_map(mp, sm);
@@ -668,7 +682,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
         lp.miss_list = ctx->miss_list;
         lp.miss_count = ctx->miss_count;
         lp.miss_cap = ctx->miss_cap;
-        lp.near_blocks = ctx->P.n > 0 ? 152 * 8 : 1;
+        lp.near_blocks = ctx->P.n > 0 ? ctx->num_sms * LBM_BC_BLOCKS_PER_SM : 1;
         lp.accel_d = ctx->accel;
         lp.accel_f = ctx->accel_f;
         launch_boundary(lp, sm);

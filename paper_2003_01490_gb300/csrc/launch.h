@@ -50,10 +50,10 @@ struct MapParams {
     int refill_cap;
     unsigned long long* n_solid;
     unsigned int* near_list;
-    int* near_count;
-    int near_cap;
+    int* near_count;        // near_count[0] and near_count[1] (= *miss_count) form one
+    int near_cap;           // 8-byte aligned word: one 64-bit atomic reserves both lists
     unsigned int* miss_list;
-    int* miss_count;
+    int* miss_count;        // near_count + 1
     int miss_cap;
     int small[3];           // periodic axis too short for one image per tile
     int* status;

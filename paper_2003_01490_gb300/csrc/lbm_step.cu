@@ -38,7 +38,16 @@
 // minimum resident blocks per SM requested for the stream/collide kernel
 // (a register cap); tuned on GB300, see the design notes
 #ifndef LBM_SC_MIN_BLOCKS
-#define LBM_SC_MIN_BLOCKS 1
+#define LBM_SC_MIN_BLOCKS 4
+#endif
+// the same for the boundary kernel
+#ifndef LBM_BC_MIN_BLOCKS
+#define LBM_BC_MIN_BLOCKS 4
+#endif
+// cache policy of the dense kernel: 0 default loads and stores, 1 streaming
+// (evict-first) stores, 2 streaming loads and stores
+#ifndef LBM_SC_HINTS
+#define LBM_SC_HINTS 0
 #endif
 
 namespace lbmdem {
@@ -293,7 +302,7 @@ template <typename S, typename T>
 __device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, int z, int q, Acc<T>& acc,
                                               const Sinks& sk) {
     const int nx = a.g.n[0], ny = a.g.n[1];
-    const long long plane = (long long)nx * ny;
+    const int plane = nx * ny;
     const long long N = a.g.ncells;
     const int c[3] = {k_c[q][0], k_c[q][1], k_c[q][2]};
     const int p = k_opp[q];
@@ -307,14 +316,14 @@ __device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, 
         if (!a.g.per[d] && (dv[d] < 0 || dv[d] >= a.g.n[d])) cli = false;
         dv[d] = wrap_idx(dv[d], a.g.n[d]);
     }
-    const long long idx = (long long)z * plane + (long long)y * nx + x;
-    const long long up = (long long)uv[2] * plane + (long long)uv[1] * nx + uv[0];
-    const long long down = (long long)dv[2] * plane + (long long)dv[1] * nx + dv[0];
+    const int idx = z * plane + y * nx + x;
+    const int up = uv[2] * plane + uv[1] * nx + uv[0];
+    const int down = dv[2] * plane + dv[1] * nx + dv[0];
     const int i = a.owner[up];
-    const T fout = Store<S>::load(a.src + (long long)p * N + idx);
-    const T fin = Store<S>::load(a.src + (long long)q * N + idx);
+    const T fout = Store<S>::load(a.src + p * N + idx);
+    const T fin = Store<S>::load(a.src + q * N + idx);
     if (cli) cli = !(a.flags[down] & FL_SOLID);
-    const T fdown = cli ? Store<S>::load(a.src + (long long)p * N + down) : T(0);
+    const T fdown = cli ? Store<S>::load(a.src + p * N + down) : T(0);
     T r[3], R, u[3], om[3];
     int n[3];
     PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
@@ -331,7 +340,7 @@ __device__ __forceinline__ void particle_link(const BcArgs<S>& a, int x, int y, 
     const T ubc = ub[0] * cp0 + ub[1] * cp1 + ub[2] * cp2;
     const T v = fout + kappa * (fdown - fin) - (T(12) * w / (T(1) + T(2) * dbc)) * ubc;
     // the pull of x in direction q reads exactly this solid-cell slot
-    Store<S>::store(a.src + (long long)q * N + up, v);
+    Store<S>::store(a.src + q * N + up, v);
     // Eq. (15) on shifted PDFs: F = c_p (2 w + f~_p + f_q) - u_b (f~_p - f_q)
     const T dif = fout - v;
     int K[6] = {0, 0, 0, 0, 0, 0};
@@ -422,7 +431,7 @@ __device__ __forceinline__ void missing_links(const BcArgs<S>& a, long long idx,
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
+__global__ void __launch_bounds__(256, LBM_BC_MIN_BLOCKS) boundary_kernel(const BcArgs<S> a) {
     using T = typename Store<S>::T;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -439,21 +448,22 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
         }
     }
     const int nx = a.g.n[0], ny = a.g.n[1];
-    const long long plane = (long long)nx * ny;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int plane = nx * ny;
+    const int stride = gridDim.x * blockDim.x;
 
     // ------------------------------------------- particle links of fluid cells
     const int count = min(*a.count, a.cap);
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < count; base += stride) {
-        const long long k = base + threadIdx.x;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int k = base + threadIdx.x;
         Acc<T> acc;
         unsigned mask = 0;          // directions with a solid upstream cell
         int x = 0, y = 0, z = 0;
         if (k < count) {
-            const long long idx = (long long)a.list[k];
-            x = (int)(idx % nx);
-            y = (int)((idx / nx) % ny);
-            z = (int)(idx / plane);
+            const int idx = (int)a.list[k];
+            z = idx / plane;
+            const int rem = idx - z * plane;
+            y = rem / nx;
+            x = rem - y * nx;
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 int v[3] = {x - cx(q), y - cy(q), z - cz(q)};
@@ -463,36 +473,40 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
                     if (!a.g.per[d] && (v[d] < 0 || v[d] >= a.g.n[d])) outside = true;
                     v[d] = wrap_idx(v[d], a.g.n[d]);
                 }
-                if (!outside && (a.flags[(long long)v[2] * plane + (long long)v[1] * nx + v[0]] & FL_SOLID))
+                if (!outside && (a.flags[v[2] * plane + v[1] * nx + v[0]] & FL_SOLID))
                     mask |= 1u << q;
             }
         }
-        // spread the warp's links evenly over its lanes: inclusive prefix sum
-        // of the link counts, then lane l takes links l, l + 32, ...
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - cnt;
+        // the warp's links in direction-major order: for q = 1..18 the cells
+        // with a link in direction q, in lane order, packed 32 links to a
+        // round, so that the lanes of a round mostly read and write
+        // neighbouring cells of the same PDF arrays
+        const int total = __reduce_add_sync(FULL, __popc(mask));
+        int q = 1, done = 0;
+        unsigned bal = __ballot_sync(FULL, (mask >> 1) & 1u);
+        int cnt = __popc(bal);
         for (int r0 = 0; r0 < total; r0 += 32) {
-            const int kk = r0 + lane;
-            int src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int v = __shfl_sync(FULL, incl, src + step - 1);
-                if (v <= kk) src += step;
+            int my_q = 0, my_src = 0, filled = 0;
+            while (filled < 32 && q < Q) {   // warp-uniform
+                const int take = min(cnt - done, 32 - filled);
+                const int j = lane - filled;
+                if (j >= 0 && j < take) {
+                    my_q = q;
+                    my_src = (int)__fns(bal, 0, done + j + 1);
+                }
+                filled += take;
+                done += take;
+                if (done == cnt) {
+                    ++q;
+                    done = 0;
+                    bal = __ballot_sync(FULL, q < Q ? (mask >> q) & 1u : 0u);
+                    cnt = __popc(bal);
+                }
             }
-            src = src > 31 ? 31 : src;
-            const int sx = __shfl_sync(FULL, x, src);
-            const int sy = __shfl_sync(FULL, y, src);
-            const int sz = __shfl_sync(FULL, z, src);
-            const unsigned sm = __shfl_sync(FULL, mask, src);
-            const int sex = __shfl_sync(FULL, excl, src);
-            if (kk < total) particle_link<S, T>(a, sx, sy, sz, (int)__fns(sm, 0, kk - sex + 1), acc, sk);
+            const int sx = __shfl_sync(FULL, x, my_src);
+            const int sy = __shfl_sync(FULL, y, my_src);
+            const int sz = __shfl_sync(FULL, z, my_src);
+            if (my_q) particle_link<S, T>(a, sx, sy, sz, my_q, acc, sk);
         }
         commit<T>(acc, sk);
     }
@@ -500,8 +514,8 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
     // ------------------------------------------- missing links (Sec. 2.2)
     if (!a.missing_links) return;
     const int mcount = min(*a.miss_count, a.miss_cap);
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < mcount; base += stride) {
-        const long long k = base + threadIdx.x;
+    for (int base = blockIdx.x * blockDim.x; base < mcount; base += stride) {
+        const int k = base + threadIdx.x;
         Acc<T> acc;
         if (k < mcount) missing_links<S, T>(a, (long long)a.miss[k], acc, sk);
         commit<T>(acc, sk);
@@ -510,6 +524,30 @@ __global__ void __launch_bounds__(256) boundary_kernel(const BcArgs<S> a) {
 
 // ------------------------------------------------------------------ stream + collide
 
+// loads and stores of the dense kernel with the cache policy LBM_SC_HINTS
+template <typename S>
+__device__ __forceinline__ typename Store<S>::T sc_load(const S* p) {
+#if LBM_SC_HINTS >= 2
+    if constexpr (sizeof(S) == 8) return (typename Store<S>::T)__ldcs(reinterpret_cast<const double*>(p));
+    else if constexpr (sizeof(S) == 4) return (typename Store<S>::T)__ldcs(reinterpret_cast<const float*>(p));
+    else return Store<S>::load(p);
+#else
+    return Store<S>::load(p);
+#endif
+}
+template <typename S>
+__device__ __forceinline__ void sc_store(S* p, typename Store<S>::T v) {
+#if LBM_SC_HINTS >= 1
+    if constexpr (sizeof(S) == 8) __stcs(reinterpret_cast<double*>(p), (double)v);
+    else if constexpr (sizeof(S) == 4) __stcs(reinterpret_cast<float*>(p), (float)v);
+    else Store<S>::store(p, v);
+#else
+    Store<S>::store(p, v);
+#endif
+}
+
+// Cell indices are 32-bit (the library limits boxes to fewer than 2^31
+// cells); each PDF array q starts at the uniform pointer src + q N.
 template <typename S, typename T>
 __global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
@@ -517,9 +555,9 @@ __global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     const bool valid = x < nx && y < ny;
-    const long long plane = (long long)nx * ny;
+    const int plane = nx * ny;
     const long long N = a.g.ncells;
-    const long long idx = (long long)z * plane + (long long)y * nx + x;
+    const int idx = z * plane + y * nx + x;
     const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
     const bool fluid = !(fl & FL_SOLID);
     // Solid cells that share a 32-byte sector with fluid cells also write
@@ -533,19 +571,19 @@ __global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(
     if (!fluid) {
         if (valid && (bal & gmask)) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, T(0));
+            for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, T(0));
         }
         return;
     }
     {
-        const int X3[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int Y3[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-        const int Z3[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-#define NB(dx, dy, dz) ((long long)Z3[1 + (dz)] * plane + (long long)Y3[1 + (dy)] * nx + X3[1 + (dx)])
+        // neighbour offsets with periodic wrap (walls are handled below)
+        const int OX[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
+        const int OY[3] = {y == 0 ? plane - nx : -nx, 0, y == ny - 1 ? nx - plane : nx};
+        const int OZ[3] = {z == 0 ? (nz - 1) * plane : -plane, 0, z == nz - 1 ? (1 - nz) * plane : plane};
         T f[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) f[q] = Store<S>::load(a.src + (long long)q * N + NB(-cx(q), -cy(q), -cz(q)));
-#undef NB
+        for (int q = 0; q < Q; ++q)
+            f[q] = sc_load<S>(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
         // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
         const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
         const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
@@ -562,7 +600,7 @@ __global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(
                 const int p = opp(q);
                 const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
                               a.uw[side][axis][2] * (T)(-cz(q));
-                f[q] = Store<S>::load(a.src + (long long)p * N + idx) - T(6) * wq<T>(p) * ucp;
+                f[q] = Store<S>::load(a.src + p * N + idx) - T(6) * wq<T>(p) * ucp;
             }
         }
 
@@ -625,7 +663,7 @@ __global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS) stream_collide_kernel(
         }
         if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + (long long)q * N + idx, f[q]);
+        for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
     }
 }
 

@@ -17,6 +17,11 @@
 #include "common.cuh"
 #include "launch.h"
 
+// minimum resident mapping blocks per SM (a register cap)
+#ifndef LBM_MAP_MIN_BLOCKS
+#define LBM_MAP_MIN_BLOCKS 16
+#endif
+
 namespace lbmdem {
 
 __device__ __forceinline__ double min_image_dd(double d, int n, int per) {
@@ -103,182 +108,258 @@ void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
 
 // ------------------------------------------------------------ mapping
 
-// block-aggregated append: one global atomic per block and list
-__device__ __forceinline__ void block_append(bool take, unsigned int entry, unsigned int* list, int* count, int cap,
-                                             int* status, int* s_warp, int* s_base) {
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
-    const unsigned am = __ballot_sync(0xffffffffu, take);
-    if (lane == 0) s_warp[warp] = __popc(am);
-    __syncthreads();
-    if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            const int c = s_warp[w];
-            s_warp[w] = tot;
-            tot += c;
-        }
-        *s_base = tot ? atomicAdd(count, tot) : 0;
-    }
-    __syncthreads();
-    if (take) {
-        const int slot = *s_base + s_warp[warp] + __popc(am & ((1u << lane) - 1u));
-        if (slot < cap) list[slot] = entry;
-        else atomicOr(status, ST_REFILL_OVERFLOW);
-    }
-    __syncthreads();
+// Exact float64 decision of the solid and shell tests for a cell centre whose
+// float32 distance lies within the tolerance of a threshold (kept out of line:
+// it runs for a tiny fraction of the tests). Returns bit 0 inside, bit 1 shell.
+__device__ __noinline__ int exact_tests(const MapParams& p, int id, int x, int y, int z) {
+    const int cpos[3] = {x, y, z};
+    const double R = p.P.R[id];
+    double dd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        dd[d] = min_image_dd(((double)cpos[d] + 0.5) - p.P.x[3 * id + d], p.g.n[d], p.g.per[d]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
+    const double rs = __dadd_rn(R, p.shell_width);
+    const bool inside = d2 <= __dmul_rn(R, R);
+    const bool in_shell = !inside && d2 <= __dmul_rn(rs, rs);
+    return (inside ? 1 : 0) | (in_shell ? 2 : 0);
 }
 
-// Per candidate: integer offset n0 of the tile's first cell from the
-// particle's base cell (for long periodic axes already moved to the image
-// nearest to the tile), the common fractional offset g = 1/2 - frac, R^2, and
+// minimum image on a short periodic axis, decided on 2 (n + g) against L
+__device__ __forceinline__ float short_axis_image(float n, float g, int L) {
+    const float tw = 2.0f * n + 2.0f * g;
+    const float fl = (float)L;
+    return tw > fl ? n - fl : (tw < -fl ? n + fl : n);
+}
+
+// One block per 32x4x4 tile, 128 threads; thread (x, y) handles the column
+// of the tile's four z cells. Per candidate the shared arrays hold the
+// integer offset n0 of the tile's first cell from the particle's base cell
+// (as an exact float; on long periodic axes already moved to the image
+// nearest to the tile), the common fractional offset g = 1/2 - frac, R^2 and
 // the thresholds of the shell and near tests with their float32 tolerances.
-// A cell's offset is (float)(n0 + l) + g: integer first, so no float32
-// intermediate is larger than the offset itself.
-__global__ void __launch_bounds__(512) map_kernel(const MapParams p) {
-    __shared__ int4 cn[TILE_CAP];
+// A cell's offset is (n0 + l) + g with the integer part formed first, so no
+// float32 intermediate is larger than the offset itself. Each warp first
+// drops the candidates that cannot reach its 32 x 1 x 4 cells.
+__global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __grid_constant__ MapParams p) {
+    __shared__ float4 cn[TILE_CAP];
     __shared__ float4 ca[TILE_CAP];
     __shared__ float4 cb[TILE_CAP];
-    __shared__ int ncand;
-    __shared__ unsigned int nsolid_blk;
+    __shared__ unsigned int s_cnt[4];          // per warp: near count | miss count << 16
+    __shared__ unsigned int s_solid[4];
+    __shared__ unsigned long long s_base;
     const long long t = ((long long)blockIdx.z * p.ntile[1] + blockIdx.y) * p.ntile[0] + blockIdx.x;
-    const int tid = threadIdx.x + TILE_X * (threadIdx.y + TILE_Y * threadIdx.z);
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int tid = lx + TILE_X * ly, warp = ly;
     const int org[3] = {(int)blockIdx.x * TILE_X, (int)blockIdx.y * TILE_Y, (int)blockIdx.z * TILE_Z};
-    if (tid == 0) {
-        int c = p.tile_count[t];
-        ncand = c < TILE_CAP ? c : TILE_CAP;
-        nsolid_blk = 0;
-    }
-    __syncthreads();
+    const int x = org[0] + lx, y = org[1] + ly;
+    const int nx = p.g.n[0], ny = p.g.n[1], nz = p.g.n[2];
+    const long long plane = (long long)nx * ny;
+    const bool valid_xy = x < nx && y < ny;
+    const long long idx0 = (long long)org[2] * plane + (long long)y * nx + x;
+    // previous flags of the column, loaded before the candidate tests
+    unsigned old4 = 0;
+#pragma unroll
+    for (int j = 0; j < TILE_Z; ++j)
+        if (valid_xy && org[2] + j < nz) old4 |= (unsigned)p.flags[idx0 + j * plane] << (8 * j);
+    const int c = p.tile_count[t];
+    const int ncand = c < TILE_CAP ? c : TILE_CAP;
     if (tid < ncand) {
         const int i = p.tile_list[t * TILE_CAP + tid];
         const PartView v = p.P.view[i];
         const int ts[3] = {TILE_X, TILE_Y, TILE_Z};
-        int n0[3];
-        float g[3];
+        float n0[3], g[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            n0[d] = org[d] - v.base[d];
+            int n = org[d] - v.base[d];
             g[d] = 0.5f - v.frac[d];
             if (p.g.per[d] && !p.small[d]) {
                 // image nearest to the tile centre
                 const int L = p.g.n[d];
-                const float c = (float)(2 * n0[d] + ts[d] - 1) + 2.0f * g[d];   // twice the centre offset
-                if (c > (float)L) n0[d] -= L;
-                else if (c < -(float)L) n0[d] += L;
+                const float cc = (float)(2 * n + ts[d] - 1) + 2.0f * g[d];   // twice the centre offset
+                if (cc > (float)L) n -= L;
+                else if (cc < -(float)L) n += L;
             }
+            n0[d] = (float)n;
         }
         const float R = v.R;
         const float Rs = R + (float)p.shell_width;
         const float Rn = R + 1.4142135f + 0.02f;
         const float R2 = R * R, Rs2 = Rs * Rs;
-        cn[tid] = make_int4(n0[0], n0[1], n0[2], i);
+        cn[tid] = make_float4(n0[0], n0[1], n0[2], __int_as_float(i));
         ca[tid] = make_float4(g[0], g[1], g[2], R2);
         cb[tid] = make_float4(Rs2, Rn * Rn, 1e-5f * (R2 + 1.0f), 1e-5f * (Rs2 + 1.0f));
     }
     __syncthreads();
+    // the tile's candidate count is consumed: reset it for the next scatter
+    if (tid == 0) p.tile_count[t] = 0;
 
-    const int x = org[0] + threadIdx.x;
-    const int y = org[1] + threadIdx.y;
-    const int z = org[2] + threadIdx.z;
-    const bool valid = x < p.g.n[0] && y < p.g.n[1] && z < p.g.n[2];
-    bool solid = false;
-    bool near_fluid = false;   // into the particle-link list of the next step
-    bool miss_solid = false;   // into the missing-link list of the next step
-    unsigned int entry = 0;
-    if (valid) {
-        const long long idx = ((long long)z * p.g.n[1] + y) * p.g.n[0] + x;
-        const int cpos[3] = {x, y, z};
-        const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
-        const bool any_small = p.small[0] | p.small[1] | p.small[2];
-        int own = 0x7fffffff;
-        bool shell = false;
-        int nnear = 0;
-        for (int k = 0; k < ncand; ++k) {
-            const int4 Nn = cn[k];
-            const float4 A = ca[k];
-            int n[3] = {Nn.x + lx, Nn.y + ly, Nn.z + lz};
+    const bool any_small = p.small[0] | p.small[1] | p.small[2];
+    const float flx = (float)lx, fly = (float)ly;
+    // candidates that may reach this warp's cells (conservative float bound)
+    unsigned relm[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = (threadIdx.x & 31) + 32 * h;
+        bool rel = false;
+        if (k < ncand) {
             if (any_small) {
-                const float gg[3] = {A.x, A.y, A.z};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    if (!p.small[d]) continue;
-                    // minimum image decided on 2 (n + g) against L
-                    const int L = p.g.n[d];
-                    const float tw = (float)(2 * n[d]) + 2.0f * gg[d];
-                    if (tw > (float)L) n[d] -= L;
-                    else if (tw < -(float)L) n[d] += L;
-                }
-            }
-            const float dx = (float)n[0] + A.x, dy = (float)n[1] + A.y, dz = (float)n[2] + A.z;
-            const float d2f = (dx * dx + dy * dy) + dz * dz;
-            const float4 B = cb[k];
-            if (d2f <= B.y) ++nnear;
-            if (d2f > B.x + B.w) continue;
-            const bool exact_needed = fabsf(d2f - A.w) <= B.z || fabsf(d2f - B.x) <= B.w;
-            bool inside, in_shell;
-            const int id = Nn.w;
-            if (!exact_needed) {
-                inside = d2f < A.w;
-                in_shell = !inside && d2f < B.x;
+                rel = true;
             } else {
-                const double R = p.P.R[id];
-                double dd[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    dd[d] = min_image_dd(((double)cpos[d] + 0.5) - p.P.x[3 * id + d], p.g.n[d], p.g.per[d]);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
-                                            __dmul_rn(dd[2], dd[2]));
-                const double rs = __dadd_rn(R, p.shell_width);
-                inside = d2 <= __dmul_rn(R, R);
-                in_shell = !inside && d2 <= __dmul_rn(rs, rs);
+                const float4 Nn = cn[k], A = ca[k], B = cb[k];
+                const float xlo = Nn.x + A.x, xhi = (Nn.x + (float)(TILE_X - 1)) + A.x;
+                const float zlo = Nn.z + A.z, zhi = (Nn.z + (float)(TILE_Z - 1)) + A.z;
+                const float dx = xlo > 0.f ? xlo : (xhi < 0.f ? -xhi : 0.f);
+                const float dz = zlo > 0.f ? zlo : (zhi < 0.f ? -zhi : 0.f);
+                const float dy = (Nn.y + fly) + A.y;
+                const float reach = fmaxf(B.y, B.x + B.w) * 1.0001f + 0.01f;
+                rel = dx * dx + dy * dy + dz * dz <= reach;
             }
-            if (inside) { if (id < own) own = id; }
-            else if (in_shell) shell = true;
         }
-        bool wall_adj = false;
+        relm[h] = __ballot_sync(0xffffffffu, rel);
+    }
+
+    int own[TILE_Z];
+    unsigned shell4 = 0, nnear4 = 0;   // per z: shell bit; near count (saturating at 2) in 2 bits
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if (!p.g.per[d] && (cpos[d] == 0 || cpos[d] == p.g.n[d] - 1)) wall_adj = true;
-        const uint8_t old = p.flags[idx];
-        uint8_t nf = 0;
-        if (own != 0x7fffffff) {
-            solid = true;
-            nf = FL_SOLID;
-            if (nnear >= 2 || wall_adj) {
-                nf |= FL_MISS;
-                miss_solid = true;
+    for (int j = 0; j < TILE_Z; ++j) own[j] = 0x7fffffff;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned mm = relm[h];
+        while (mm) {
+            const int k = __ffs(mm) - 1 + 32 * h;
+            mm &= mm - 1;
+            const float4 Nn = cn[k], A = ca[k], B = cb[k];
+            const int id = __float_as_int(Nn.w);
+            float fx = Nn.x + flx, fy = Nn.y + fly;
+            if (any_small) {
+                if (p.small[0]) fx = short_axis_image(fx, A.x, nx);
+                if (p.small[1]) fy = short_axis_image(fy, A.y, ny);
             }
-            p.owner[idx] = own;
+            const float dx = fx + A.x, dy = fy + A.y;
+            const float sxy = dx * dx + dy * dy;
+#pragma unroll
+            for (int j = 0; j < TILE_Z; ++j) {
+                float fz = Nn.z + (float)j;
+                if (any_small && p.small[2]) fz = short_axis_image(fz, A.z, nz);
+                const float dz = fz + A.z;
+                const float d2f = sxy + dz * dz;
+                if (d2f <= B.y) {
+                    const unsigned cur = (nnear4 >> (2 * j)) & 3u;
+                    if (cur < 2u) nnear4 += 1u << (2 * j);
+                }
+                if (d2f > B.x + B.w) continue;
+                const bool exact_needed = fabsf(d2f - A.w) <= B.z || fabsf(d2f - B.x) <= B.w;
+                bool inside, in_shell;
+                if (!exact_needed) {
+                    inside = d2f < A.w;
+                    in_shell = !inside && d2f < B.x;
+                } else {
+                    const int r = exact_tests(p, id, x, y, org[2] + j);
+                    inside = r & 1;
+                    in_shell = (r & 2) != 0;
+                }
+                if (inside) { if (id < own[j]) own[j] = id; }
+                else if (in_shell) shell4 |= 1u << j;
+            }
+        }
+    }
+
+    bool wall_xy = false;
+    if (!p.g.per[0] && (x == 0 || x == nx - 1)) wall_xy = true;
+    if (!p.g.per[1] && (y == 0 || y == ny - 1)) wall_xy = true;
+    unsigned near_bits = 0, miss_bits = 0, solid_bits = 0;
+#pragma unroll
+    for (int j = 0; j < TILE_Z; ++j) {
+        const int z = org[2] + j;
+        if (!valid_xy || z >= nz) continue;
+        const long long idx = idx0 + j * plane;
+        const bool wall_adj = wall_xy || (!p.g.per[2] && (z == 0 || z == nz - 1));
+        const unsigned nn = (nnear4 >> (2 * j)) & 3u;
+        const uint8_t old = (uint8_t)(old4 >> (8 * j));
+        uint8_t nf = 0;
+        if (own[j] != 0x7fffffff) {
+            nf = FL_SOLID;
+            solid_bits |= 1u << j;
+            if (nn >= 2u || wall_adj) {
+                nf |= FL_MISS;
+                miss_bits |= 1u << j;
+            }
+            p.owner[idx] = own[j];
         } else {
-            if (shell) nf |= FL_SHELL;
-            if (nnear >= 1) {
+            if (shell4 & (1u << j)) nf |= FL_SHELL;
+            if (nn >= 1u) {
                 nf |= FL_NEAR;
-                near_fluid = true;
+                near_bits |= 1u << j;
             }
             if (old & FL_SOLID) {
                 nf |= FL_NEWFLUID;
-                int slot = atomicAdd(p.refill_count, 1);
+                const int slot = atomicAdd(p.refill_count, 1);
                 if (slot < p.refill_cap) p.refill_list[slot] = (unsigned int)idx;
                 else atomicOr(p.status, ST_REFILL_OVERFLOW);
             }
         }
         p.flags[idx] = nf;
-        entry = (unsigned int)idx;
     }
-    // block-aggregated appends to the particle-link and missing-link lists
-    __shared__ int s_warp[16];
-    __shared__ int s_base;
-    block_append(near_fluid, entry, p.near_list, p.near_count, p.near_cap, p.status, s_warp, &s_base);
-    block_append(miss_solid, entry, p.miss_list, p.miss_count, p.miss_cap, p.status, s_warp, &s_base);
-    unsigned bal = __ballot_sync(0xffffffffu, solid);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&nsolid_blk, (unsigned)__popc(bal));
+
+    // block-aggregated appends: one 64-bit atomic reserves the slots of both
+    // lists (near count in the low word, missing-link count in the high word)
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned nb[TILE_Z], mb[TILE_Z];
+    unsigned wn = 0, wm = 0, ws = 0;
+#pragma unroll
+    for (int j = 0; j < TILE_Z; ++j) {
+        nb[j] = __ballot_sync(FULL, (near_bits >> j) & 1u);
+        mb[j] = __ballot_sync(FULL, (miss_bits >> j) & 1u);
+        wn += __popc(nb[j]);
+        wm += __popc(mb[j]);
+        ws += __popc(__ballot_sync(FULL, (solid_bits >> j) & 1u));
+    }
+    if (lane == 0) {
+        s_cnt[warp] = wn | (wm << 16);
+        s_solid[warp] = ws;
+    }
     __syncthreads();
-    if (tid == 0 && nsolid_blk) atomicAdd(p.n_solid, (unsigned long long)nsolid_blk);
+    if (tid == 0) {
+        unsigned long long tn = 0, tm = 0, tsol = 0;
+        for (int w = 0; w < 4; ++w) {
+            const unsigned v = s_cnt[w];
+            s_cnt[w] = (unsigned)tn | ((unsigned)tm << 16);
+            tn += v & 0xffffu;
+            tm += v >> 16;
+            tsol += s_solid[w];
+        }
+        s_base = (tn | tm) ? atomicAdd(reinterpret_cast<unsigned long long*>(p.near_count), tn | (tm << 32)) : 0ull;
+        if (tsol) atomicAdd(p.n_solid, tsol);
+    }
+    __syncthreads();
+    if (near_bits | miss_bits) {
+        const unsigned long long base = s_base;
+        int sn = (int)(unsigned)base + (int)(s_cnt[warp] & 0xffffu);
+        int sm = (int)(unsigned)(base >> 32) + (int)(s_cnt[warp] >> 16);
+#pragma unroll
+        for (int j = 0; j < TILE_Z; ++j) {
+            const unsigned entry = (unsigned)(idx0 + j * plane);
+            if ((near_bits >> j) & 1u) {
+                const int slot = sn + __popc(nb[j] & lt);
+                if (slot < p.near_cap) p.near_list[slot] = entry;
+                else atomicOr(p.status, ST_REFILL_OVERFLOW);
+            }
+            if ((miss_bits >> j) & 1u) {
+                const int slot = sm + __popc(mb[j] & lt);
+                if (slot < p.miss_cap) p.miss_list[slot] = entry;
+                else atomicOr(p.status, ST_REFILL_OVERFLOW);
+            }
+            sn += __popc(nb[j]);
+            sm += __popc(mb[j]);
+        }
+    }
 }
 
 void launch_map(const MapParams& p, cudaStream_t st) {
-    dim3 block(TILE_X, TILE_Y, TILE_Z);
+    dim3 block(TILE_X, TILE_Y, 1);
     dim3 grid(p.ntile[0], p.ntile[1], p.ntile[2]);
     map_kernel<<<grid, block, 0, st>>>(p);
 }
