@@ -136,7 +136,9 @@ lbm_status lbm_create_in_arena(const lbm_grid *grid, const lbm_relax *relax,
  * doubles; radius, density: n doubles, density = rho_p / rho_f. Allowed only
  * before the first lbm_step(). Errors: LBM_ERR_INVALID if a centre lies
  * outside the box, a radius is < 1 cell, a density is <= 0, two spheres
- * overlap (centre distance < R_i + R_j) or a sphere crosses a wall;
+ * overlap (centre distance < R_i + R_j), a sphere crosses a wall or a
+ * periodic side is not longer than 2 R + 4 cells (a sphere and its own
+ * periodic image would share boundary cells);
  * LBM_ERR_CAPACITY if the total exceeds max_particles; LBM_ERR_STATE after the
  * first step. *first_id_out (may be NULL) receives the index of the first new
  * sphere; spheres are numbered in insertion order. */
@@ -163,8 +165,8 @@ lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *
  * the last step; both are 0 in solid cells. Synchronises the stream. */
 lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho, double *u, unsigned char *flags);
 
-/* Copy the owning particle index of every cell (int32, -1 for a cell that has
- * never been solid; for a fluid cell that was solid it holds the last owner). */
+/* Copy the owning particle index of every cell (int32; -1 for fluid cells).
+ * Synchronises the stream. */
 lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);
 
 /* Copy / replace the post-collision PDFs f_q (unshifted values), 19 x cells

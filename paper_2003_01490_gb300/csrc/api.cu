@@ -11,10 +11,6 @@
 #include "common.cuh"
 #include "launch.h"
 
-// resident boundary-kernel blocks per multiprocessor (grid-stride loop)
-#ifndef LBM_BC_BLOCKS_PER_SM
-#define LBM_BC_BLOCKS_PER_SM 8
-#endif
 
 using namespace lbmdem;
 
@@ -43,15 +39,13 @@ struct lbm_ctx {
     int* tile_count = nullptr;
     int* tile_list = nullptr;
     unsigned int* refill_list = nullptr;
+    int* refill_owner = nullptr;
     int* refill_count = nullptr;
     int refill_cap = 0;
     unsigned long long* n_solid = nullptr;
     int* status = nullptr;
     double* accel = nullptr;
     float* accel_f = nullptr;
-    unsigned int* near_list = nullptr;
-    int* near_count = nullptr;
-    int near_cap = 0;
     unsigned int* miss_list = nullptr;
     int* miss_count = nullptr;
     int miss_cap = 0;
@@ -157,7 +151,7 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(4 * s.ntiles * TILE_CAP);     // 5 tile_list
     L.add(4 * (size_t)s.refill_cap);    // 6 refill_list
     L.add(4);                           // 7 (unused)
-    L.add(32);                          // 8 counters: n_solid, near, miss, refill counts
+    L.add(32);                          // 8 counters: n_solid, missing-link and refill counts
     L.add(4);                           // 9 status
     L.add(8 * 3);                       // 10 accel
     L.add(8 * 4 * (size_t)s.scratch_cells);  // 11 scratch
@@ -190,7 +184,7 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
         L.add(8 * 3 * 6 * n);                    // 36/41 whist
         L.add(6 * n);                            // 37/42 wact
     }
-    L.add(4 * N);                                // 43 near_list
+    L.add(4);                                    // 43 (unused)
     L.add(4);                                    // 44 (unused)
     L.add(4 * 3);                                // 45 accel_f
     L.add(4 * 3 * n);                            // 46 xf
@@ -204,6 +198,7 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(8 * n);                                // 54 hm
     L.add(8 * n);                                // 55 hI
     L.add(8 * 3 * n);                            // 56 ext
+    L.add(4 * (size_t)s.refill_cap);             // 57 refill_owner
     (void)g;
 }
 
@@ -296,18 +291,14 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->tile_count = (int*)at(4);
     ctx->tile_list = (int*)at(5);
     ctx->refill_list = (unsigned int*)at(6);
+    ctx->refill_owner = (int*)at(57);
     ctx->refill_cap = s.refill_cap;
-    // one 32-byte block of counters, cleared by one memset per remap; the
-    // near and missing-link counts share one 8-byte word (one 64-bit atomic
-    // of the mapping reserves slots in both lists)
+    // one 32-byte block of counters, cleared by one memset per remap
     ctx->n_solid = (unsigned long long*)at(8);
-    ctx->near_count = (int*)((char*)at(8) + 8);
-    ctx->miss_count = (int*)((char*)at(8) + 12);
-    ctx->refill_count = (int*)((char*)at(8) + 16);
+    ctx->miss_count = (int*)((char*)at(8) + 8);
+    ctx->refill_count = (int*)((char*)at(8) + 12);
     ctx->status = (int*)at(9);
     ctx->accel = (double*)at(10);
-    ctx->near_list = (unsigned int*)at(43);
-    ctx->near_cap = (int)s.ncells;
     ctx->accel_f = (float*)at(45);
     ctx->P.xf = (float*)at(46);
     ctx->miss_list = (unsigned int*)at(47);
@@ -366,9 +357,9 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
     mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
     mp.shell_width = ctx->relax.shell_width;
-    mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
+    mp.refill_list = ctx->refill_list; mp.refill_owner = ctx->refill_owner;
+    mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
     mp.n_solid = ctx->n_solid; mp.status = ctx->status;
-    mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
     mp.miss_list = ctx->miss_list; mp.miss_count = ctx->miss_count; mp.miss_cap = ctx->miss_cap;
     launch_map(mp, sm);
     ctx->launches += 1;
@@ -396,9 +387,9 @@ MapParams map_params(lbm_ctx* ctx) {
     for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
     mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
     mp.shell_width = ctx->relax.shell_width;
-    mp.refill_list = ctx->refill_list; mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
+    mp.refill_list = ctx->refill_list; mp.refill_owner = ctx->refill_owner;
+    mp.refill_count = ctx->refill_count; mp.refill_cap = ctx->refill_cap;
     mp.n_solid = ctx->n_solid; mp.status = ctx->status;
-    mp.near_list = ctx->near_list; mp.near_count = ctx->near_count; mp.near_cap = ctx->near_cap;
     mp.miss_list = ctx->miss_list; mp.miss_count = ctx->miss_count; mp.miss_cap = ctx->miss_cap;
     return mp;
 }
@@ -407,7 +398,7 @@ MapParams map_params(lbm_ctx* ctx) {
 lbm_status remap(lbm_ctx* ctx) {
     cudaStream_t sm = ctx->stream;
     // tile counts are zero here: the mapping kernel resets each one it reads
-    CK(cudaMemsetAsync(ctx->n_solid, 0, 24, sm));
+    CK(cudaMemsetAsync(ctx->n_solid, 0, 16, sm));
     MapParams mp = map_params(ctx);
     launch_tile_scatter(mp, sm);
     launch_map(mp, sm);
@@ -555,7 +546,8 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
             if (!(x >= 0.0 && x < L)) return fail(ctx, LBM_ERR_INVALID, "sphere centre outside the box");
             if (!ctx->g.per[a] && (x - R < 0.0 || x + R > L))
                 return fail(ctx, LBM_ERR_INVALID, "sphere crosses a wall");
-            if (ctx->g.per[a] && 2.0 * R >= L) return fail(ctx, LBM_ERR_INVALID, "sphere wider than a periodic box");
+            if (ctx->g.per[a] && 2.0 * R + 4.0 >= L)
+                return fail(ctx, LBM_ERR_INVALID, "periodic side not longer than 2 R + 4 cells");
         }
         const int m = (int)hR.size();
         for (int j = 0; j < m; ++j) {
@@ -676,13 +668,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
         lp.P = ctx->P;
         lp.missing_links = d.missing_links && ctx->P.n > 0;
         lp.status = ctx->status;
-        lp.near_list = ctx->near_list;
-        lp.near_count = ctx->near_count;
-        lp.near_cap = ctx->near_cap;
         lp.miss_list = ctx->miss_list;
         lp.miss_count = ctx->miss_count;
         lp.miss_cap = ctx->miss_cap;
-        lp.near_blocks = ctx->P.n > 0 ? ctx->num_sms * LBM_BC_BLOCKS_PER_SM : 1;
+        lp.num_sms = ctx->num_sms;
         lp.accel_d = ctx->accel;
         lp.accel_f = ctx->accel_f;
         launch_boundary(lp, sm);
@@ -727,7 +716,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
             rp.storage = ctx->storage;
             rp.f = ctx->f[1 - ctx->cur];
             rp.flags = ctx->flags;
-            rp.owner = ctx->owner;
+            rp.list_owner = ctx->refill_owner;
             rp.g = ctx->g;
             rp.P = ctx->P;
             rp.list = ctx->refill_list;

@@ -12,7 +12,7 @@ struct LbmStepParams {
     const void* src;
     void* dst;
     const uint8_t* flags;
-    const int* owner;
+    const int* owner;                // particle of a solid cell, -1 for fluid
     Geom g;
     double s_plus, s_minus, s_b_shell, s_b_bulk;
     int bulk_corr;
@@ -23,13 +23,10 @@ struct LbmStepParams {
     Particles P;
     int missing_links;
     int* status;
-    const unsigned int* near_list;   // fluid cells with possible particle links
-    const int* near_count;
-    int near_cap;
     const unsigned int* miss_list;   // solid cells with possible missing links
     const int* miss_count;
     int miss_cap;
-    int near_blocks;                 // grid of the boundary kernel
+    int num_sms;                     // multiprocessors of the device (grid sizing)
     double* accel_d;                 // out: fluid body force of the step [3]
     float* accel_f;
 };
@@ -46,14 +43,12 @@ struct MapParams {
     int* tile_list;
     double shell_width;
     unsigned int* refill_list;
+    int* refill_owner;      // former particle of each refill-list cell
     int* refill_count;
     int refill_cap;
     unsigned long long* n_solid;
-    unsigned int* near_list;
-    int* near_count;        // near_count[0] and near_count[1] (= *miss_count) form one
-    int near_cap;           // 8-byte aligned word: one 64-bit atomic reserves both lists
     unsigned int* miss_list;
-    int* miss_count;        // near_count + 1
+    int* miss_count;
     int miss_cap;
     int small[3];           // periodic axis too short for one image per tile
     int* status;
@@ -65,7 +60,7 @@ struct RefillParams {
     int storage;
     void* f;
     const uint8_t* flags;
-    const int* owner;
+    const int* list_owner;  // former particle of each list cell
     Geom g;
     Particles P;
     const unsigned int* list;

@@ -3,17 +3,18 @@
 //
 // Mapping: every particle registers itself in the candidate list of each
 // 32x4x4 tile that its influence sphere (R + max(delta_aB, sqrt 2)) touches;
-// then one thread per cell tests the tile's candidates. The solid test
-// |x_c - x_p|^2 <= R^2 and the shell test R^2 < |x_c - x_p|^2 <= (R + delta_aB)^2
-// are decided in float32 when the margin is clear and re-evaluated in float64
-// with round-to-nearest and no contraction, ((dx dx + dy dy) + dz dz), when a
-// value lies within 1e-5 (relative) of a threshold, so the flags are exactly
-// those of a plain float64 evaluation. The lowest particle index owns a cell
-// inside several spheres. Cells that were solid and are now fluid are
-// appended to the refill list; the owner field keeps their former particle.
-// Fluid cells within R + sqrt(2) of a particle (candidates for particle links)
-// and solid cells next to another body (candidates for missing links) go to
-// the near-boundary list that the boundary kernel of the next step reads.
+// then one thread per (x, y) column of the tile tests the tile's candidates
+// against its four cells. The solid test |x_c - x_p|^2 <= R^2 and the shell
+// test R^2 < |x_c - x_p|^2 <= (R + delta_aB)^2 are decided in float32 when the
+// margin is clear and re-evaluated in float64 with round-to-nearest and no
+// contraction, ((dx dx + dy dy) + dz dz), when a value lies within 1e-5
+// (relative) of a threshold, so the flags are exactly those of a plain float64
+// evaluation. The lowest particle index owns a cell inside several spheres;
+// fluid cells have owner -1. Cells that were solid and are now fluid go to the
+// refill list with their former particle. Fluid cells within R + sqrt(2) of a
+// particle get the NEAR flag; solid cells next to another body (candidates for
+// missing links) go to the missing-link list that the boundary kernel of the
+// next step reads.
 #include "common.cuh"
 #include "launch.h"
 
@@ -145,9 +146,9 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     __shared__ float4 cn[TILE_CAP];
     __shared__ float4 ca[TILE_CAP];
     __shared__ float4 cb[TILE_CAP];
-    __shared__ unsigned int s_cnt[4];          // per warp: near count | miss count << 16
+    __shared__ unsigned int s_cnt[4];          // per warp: missing-link cells
     __shared__ unsigned int s_solid[4];
-    __shared__ unsigned long long s_base;
+    __shared__ unsigned int s_base;
     const long long t = ((long long)blockIdx.z * p.ntile[1] + blockIdx.y) * p.ntile[0] + blockIdx.x;
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int tid = lx + TILE_X * ly, warp = ly;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     bool wall_xy = false;
     if (!p.g.per[0] && (x == 0 || x == nx - 1)) wall_xy = true;
     if (!p.g.per[1] && (y == 0 || y == ny - 1)) wall_xy = true;
-    unsigned near_bits = 0, miss_bits = 0, solid_bits = 0;
+    unsigned miss_bits = 0, solid_bits = 0;
 #pragma unroll
     for (int j = 0; j < TILE_Z; ++j) {
         const int z = org[2] + j;
@@ -288,71 +289,63 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
             p.owner[idx] = own[j];
         } else {
             if (shell4 & (1u << j)) nf |= FL_SHELL;
-            if (nn >= 1u) {
-                nf |= FL_NEAR;
-                near_bits |= 1u << j;
-            }
+            if (nn >= 1u) nf |= FL_NEAR;
             if (old & FL_SOLID) {
+                // uncovered this step: refill with the former particle's velocity
                 nf |= FL_NEWFLUID;
+                const int prev = p.owner[idx];
+                p.owner[idx] = -1;
                 const int slot = atomicAdd(p.refill_count, 1);
-                if (slot < p.refill_cap) p.refill_list[slot] = (unsigned int)idx;
-                else atomicOr(p.status, ST_REFILL_OVERFLOW);
+                if (slot < p.refill_cap) {
+                    p.refill_list[slot] = (unsigned int)idx;
+                    p.refill_owner[slot] = prev;
+                } else {
+                    atomicOr(p.status, ST_REFILL_OVERFLOW);
+                }
             }
         }
         p.flags[idx] = nf;
     }
 
-    // block-aggregated appends: one 64-bit atomic reserves the slots of both
-    // lists (near count in the low word, missing-link count in the high word)
+    // block-aggregated append to the missing-link list and solid count
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned nb[TILE_Z], mb[TILE_Z];
-    unsigned wn = 0, wm = 0, ws = 0;
+    unsigned mb[TILE_Z];
+    unsigned wm = 0, ws = 0;
 #pragma unroll
     for (int j = 0; j < TILE_Z; ++j) {
-        nb[j] = __ballot_sync(FULL, (near_bits >> j) & 1u);
         mb[j] = __ballot_sync(FULL, (miss_bits >> j) & 1u);
-        wn += __popc(nb[j]);
         wm += __popc(mb[j]);
         ws += __popc(__ballot_sync(FULL, (solid_bits >> j) & 1u));
     }
     if (lane == 0) {
-        s_cnt[warp] = wn | (wm << 16);
+        s_cnt[warp] = wm;
         s_solid[warp] = ws;
     }
     __syncthreads();
     if (tid == 0) {
-        unsigned long long tn = 0, tm = 0, tsol = 0;
+        unsigned tm = 0;
+        unsigned long long tsol = 0;
         for (int w = 0; w < 4; ++w) {
-            const unsigned v = s_cnt[w];
-            s_cnt[w] = (unsigned)tn | ((unsigned)tm << 16);
-            tn += v & 0xffffu;
-            tm += v >> 16;
+            const unsigned c = s_cnt[w];
+            s_cnt[w] = tm;
+            tm += c;
             tsol += s_solid[w];
         }
-        s_base = (tn | tm) ? atomicAdd(reinterpret_cast<unsigned long long*>(p.near_count), tn | (tm << 32)) : 0ull;
+        s_base = tm ? (unsigned)atomicAdd(p.miss_count, (int)tm) : 0u;
         if (tsol) atomicAdd(p.n_solid, tsol);
     }
     __syncthreads();
-    if (near_bits | miss_bits) {
-        const unsigned long long base = s_base;
-        int sn = (int)(unsigned)base + (int)(s_cnt[warp] & 0xffffu);
-        int sm = (int)(unsigned)(base >> 32) + (int)(s_cnt[warp] >> 16);
+    if (miss_bits) {
+        int sm = (int)(s_base + s_cnt[warp]);
 #pragma unroll
         for (int j = 0; j < TILE_Z; ++j) {
-            const unsigned entry = (unsigned)(idx0 + j * plane);
-            if ((near_bits >> j) & 1u) {
-                const int slot = sn + __popc(nb[j] & lt);
-                if (slot < p.near_cap) p.near_list[slot] = entry;
-                else atomicOr(p.status, ST_REFILL_OVERFLOW);
-            }
             if ((miss_bits >> j) & 1u) {
                 const int slot = sm + __popc(mb[j] & lt);
-                if (slot < p.miss_cap) p.miss_list[slot] = entry;
+                if (slot < p.miss_cap) p.miss_list[slot] = (unsigned)(idx0 + j * plane);
                 else atomicOr(p.status, ST_REFILL_OVERFLOW);
             }
-            sn += __popc(nb[j]);
             sm += __popc(mb[j]);
         }
     }
@@ -381,7 +374,7 @@ __global__ void refill_kernel(const RefillParams p) {
         const int y = (int)((idx / nx) % ny);
         const int z = (int)(idx / ((long long)nx * ny));
         const int cpos[3] = {x, y, z};
-        const int i = p.owner[idx];
+        const int i = p.list_owner[k];
         T drho_sum = T(0);    // neighbour densities minus rho0 (shifted, no cancellation)
         int nnb = 0;
         T uax[6][3];      // velocities of the axis neighbours +x -x +y -y +z -z

@@ -26,7 +26,7 @@ struct NoallocScratch {
     PartView view[NOALLOC_MAX_SPHERES];
     float xf[3 * NOALLOC_MAX_SPHERES];
     unsigned long long n_solid;
-    int counters[4];          // near, miss (one 8-byte word), refill counts; the lists are disabled
+    int counters[4];          // refill and missing-link counts (the lists are disabled)
     int status;
     unsigned int dummy_list[4];
 };
@@ -130,9 +130,9 @@ extern "C" lbm_status lbm_map_spheres_noalloc(const lbm_grid* grid, double shell
     mp.tile_count = s->tile_count;
     mp.tile_list = s->tile_list;
     mp.shell_width = shell_width;
-    // the refill and boundary lists of the time stepper are not produced here
-    mp.refill_list = s->dummy_list; mp.refill_count = &s->counters[2]; mp.refill_cap = 0;
-    mp.near_list = s->dummy_list; mp.near_count = &s->counters[0]; mp.near_cap = 0;
+    // the refill and missing-link lists of the time stepper are not produced here
+    mp.refill_list = s->dummy_list; mp.refill_owner = reinterpret_cast<int*>(s->dummy_list);
+    mp.refill_count = &s->counters[0]; mp.refill_cap = 0;
     mp.miss_list = s->dummy_list; mp.miss_count = &s->counters[1]; mp.miss_cap = 0;
     mp.n_solid = &s->n_solid;
     mp.status = &s->status;
