@@ -170,8 +170,10 @@ lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho, double *u, unsigned char *f
 lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);
 
 /* Copy / replace the post-collision PDFs f_q (unshifted values), 19 x cells
- * doubles, direction-major (q = 0..18 in the order fixed by App. A). Values in
- * solid cells are ignored by the method. Synchronises the stream. */
+ * doubles, direction-major (q = 0..18 in the order fixed by App. A). Solid
+ * cells read as NaN: every PDF slot of a solid cell holds a NaN marker, by
+ * which the dense kernel finds particle links; values given for solid cells
+ * are replaced by that marker. Synchronises the stream. */
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *f);
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
 

@@ -354,6 +354,7 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     // the wall-adjacent cells need the NEAR flag even without particles
     MapParams mp{};
     mp.g = ctx->g; mp.P = ctx->P; mp.flags = ctx->flags; mp.owner = ctx->owner;
+    mp.pdf[0] = ctx->f[0]; mp.pdf[1] = ctx->f[1]; mp.elem = (int)ctx->elem;
     for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
     mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
     mp.shell_width = ctx->relax.shell_width;
@@ -384,6 +385,7 @@ MapParams map_params(lbm_ctx* ctx) {
     for (int a = 0; a < 3; ++a)
         mp.small[a] = ctx->g.per[a] && ctx->g.n[a] <= 2.0 * reach + ts[a] + 2.0;
     mp.g = ctx->g; mp.P = ctx->P; mp.flags = ctx->flags; mp.owner = ctx->owner;
+    mp.pdf[0] = ctx->f[0]; mp.pdf[1] = ctx->f[1]; mp.elem = (int)ctx->elem;
     for (int a = 0; a < 3; ++a) mp.ntile[a] = ctx->ntile[a];
     mp.tile_count = ctx->tile_count; mp.tile_list = ctx->tile_list;
     mp.shell_width = ctx->relax.shell_width;
@@ -855,6 +857,10 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f) {
         }
     }
     CK(cudaMemcpyAsync(ctx->f[ctx->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // solid cells keep their NaN marker whatever was uploaded for them
+    launch_solid_markers(map_params(ctx), ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }

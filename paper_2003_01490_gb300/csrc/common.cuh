@@ -96,7 +96,7 @@ struct Geom {
 // float view of a particle for the float32 kernels: position split into an
 // integer cell base and a fraction so that cell-relative offsets keep full
 // float precision anywhere in the box
-struct PartView {
+struct __align__(16) PartView {
     int base[3];
     float frac[3];
     float R;

@@ -38,6 +38,8 @@ struct MapParams {
     Particles P;
     uint8_t* flags;
     int* owner;
+    void* pdf[2];           // both PDF buffers (NaN markers into cells that turn solid), or NULL
+    int elem;               // bytes per stored PDF value (8, 4 or 2)
     int ntile[3];
     int* tile_count;
     int* tile_list;
@@ -55,6 +57,8 @@ struct MapParams {
 };
 void launch_tile_scatter(const MapParams& p, cudaStream_t st);
 void launch_map(const MapParams& p, cudaStream_t st);
+// NaN markers into every PDF slot of every solid cell of both buffers
+void launch_solid_markers(const MapParams& p, cudaStream_t st);
 
 struct RefillParams {
     int storage;

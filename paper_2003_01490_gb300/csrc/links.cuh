@@ -1,0 +1,226 @@
+// links.cuh -- device helpers shared by the kernels that handle particle
+// links: fixed-point and warp-segmented force sums, the particle view used by
+// the float32 kernels, the link fraction of Eq. (14) and warp prefix sums.
+#pragma once
+
+#include "common.cuh"
+
+namespace lbmdem {
+
+// float -> fixed point with scale 2^32 using float32 and int32 operations only;
+// exact up to the final rounding at 2^-32. |v| must stay below 2^31.
+__device__ __forceinline__ long long to_fixed(float v, int* status) {
+    float hi = truncf(v);
+    float r1 = (v - hi) * 65536.0f;
+    float mid = truncf(r1);
+    float r2 = (r1 - mid) * 65536.0f;
+    if (!(fabsf(hi) < 2147483520.0f)) {
+        atomicOr(status, ST_FIXED_OVERFLOW);
+        return 0;
+    }
+    unsigned long long h = (unsigned long long)(long long)__float2int_rz(hi);
+    long long m = (long long)__float2int_rz(mid);
+    long long l = (long long)__float2int_rn(r2);
+    return (long long)(h << 32) + m * 65536LL + l;
+}
+
+// per-lane partial sums of one particle's link forces and torques
+template <typename T>
+struct Acc {
+    int key = -1;                  // particle index, -1 = nothing accumulated
+    T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int k[6] = {0, 0, 0, 0, 0, 0}; // float32 path: 36 x constant force, 36 x (n x c) torque
+};
+
+struct Sinks {
+    double* acc_d;
+    long long* acc_i;
+    long long* acc_k;
+    int* status;
+};
+
+__device__ __forceinline__ void add_float(const Sinks& s, int i, int c, double v) { atomicAdd(s.acc_d + 6 * i + c, v); }
+__device__ __forceinline__ void add_float(const Sinks& s, int i, int c, float v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_i + 6 * i + c), (unsigned long long)to_fixed(v, s.status));
+}
+__device__ __forceinline__ void add_int(const Sinks& s, int i, int c, int v) {
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_k + 6 * i + c), (unsigned long long)(long long)v);
+}
+
+template <typename T>
+__device__ __forceinline__ void flush(Acc<T>& a, const Sinks& s) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        add_float(s, a.key, c, a.f[c]);
+        if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+        a.f[c] = T(0);
+        a.k[c] = 0;
+    }
+}
+
+// warp-level commit of the per-lane partial sums: lanes holding the same
+// particle (found with match_any) are reduced by a tree over their ranks and
+// the lowest lane of each group issues the atomics
+template <typename T>
+__device__ __forceinline__ void commit(Acc<T>& a, const Sinks& s) {
+    const unsigned full = 0xffffffffu;
+    if (__ballot_sync(full, a.key >= 0) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(full, a.key);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int size = __popc(peers);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        // partner: the peer whose rank is rank + off (only read when it exists)
+        const int pr = rank + off;
+        const int src = pr < size ? (int)__fns(peers, 0, pr + 1) : lane;
+        const bool take = (rank & (2 * off - 1)) == 0 && pr < size;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const T v = __shfl_sync(full, a.f[c], src);
+            if (take) a.f[c] += v;
+            if (sizeof(T) == 4) {
+                const int iv = __shfl_sync(full, a.k[c], src);
+                if (take) a.k[c] += iv;
+            }
+        }
+    }
+    if (rank == 0 && a.key >= 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            add_float(s, a.key, c, a.f[c]);
+            if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void accumulate(int i, const T (&F)[3], const T (&Tq)[3], const int (&K)[6], Acc<T>& a,
+                                           const Sinks& s) {
+    if (a.key >= 0 && a.key != i) flush(a, s);   // a second particle in the same lane
+    a.key = i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.f[c] += F[c];
+        a.f[3 + c] += Tq[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a.k[c] += K[c];
+}
+
+__device__ __forceinline__ double min_image_d(double d, int n, int per) {
+    if (per) {
+        double half = 0.5 * (double)n;
+        if (d > half) d -= (double)n;
+        if (d < -half) d += (double)n;
+    }
+    return d;
+}
+
+// offset r = (cell centre - particle centre) with minimum image, the integer
+// part n of that offset from the particle's base cell (float32 path), and the
+// rigid body data of particle i, in the compute precision T
+template <typename T> struct PartOps;
+template <> struct PartOps<double> {
+    template <typename A>
+    __device__ static void load(const A& a, int i, int x, int y, int z, double (&r)[3], int (&n)[3], double& R,
+                                double (&u)[3], double (&om)[3]) {
+        const int c[3] = {x, y, z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = min_image_d(((double)c[d] + 0.5) - a.px[3 * i + d], a.g.n[d], a.g.per[d]);
+            n[d] = 0;
+            u[d] = a.pu[3 * i + d];
+            om[d] = a.pom[3 * i + d];
+        }
+        R = a.pR[i];
+    }
+};
+template <> struct PartOps<float> {
+    template <typename A>
+    __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float& R,
+                                float (&u)[3], float (&om)[3]) {
+        const PartView v = a.view[i];
+        const int c[3] = {x, y, z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int nd = c[d] - v.base[d];
+            const float g = 0.5f - v.frac[d];
+            if (a.g.per[d]) {
+                const float half = 0.5f * (float)a.g.n[d];
+                const float rd = (float)nd + g;
+                if (rd > half) nd -= a.g.n[d];
+                else if (rd < -half) nd += a.g.n[d];
+            }
+            n[d] = nd;
+            r[d] = (float)nd + g;
+            u[d] = v.u[d];
+            om[d] = v.om[d];
+        }
+        R = v.R;
+    }
+};
+
+// error-free transformations (Knuth's TwoSum, FMA product error)
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename T>
+__device__ __forceinline__ T two_sum(T a, T b, T& err) {
+    const T s = a + b;
+    const T bb = s - a;
+    err += (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// smallest t in [0, 1] with |r + t c| = R (link fraction delta of Eq. (14)).
+// |r|^2 - R^2 cancels strongly near the surface, so it is formed from exact
+// products and compensated sums; the root uses the cancellation-free form
+// t = 2 cc / (-b + sqrt(b^2 - 4 a cc)) of the smaller root.
+template <typename T>
+__device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T cc2, T R) {
+    const T b = T(2) * (r[0] * c0 + r[1] * c1 + r[2] * c2_);
+    T err = T(0);
+    const T p0 = r[0] * r[0], p1 = r[1] * r[1], p2 = r[2] * r[2], pR = R * R;
+    const T e = (fma_t<T>(r[0], r[0], -p0) + fma_t<T>(r[1], r[1], -p1)) +
+                (fma_t<T>(r[2], r[2], -p2) - fma_t<T>(R, R, -pR));
+    T sum = two_sum<T>(p0, p1, err);
+    sum = two_sum<T>(sum, p2, err);
+    sum = two_sum<T>(sum, -pR, err);
+    const T cc = sum + (err + e);
+    const T disc = b * b - T(4) * cc2 * cc;
+    if (disc < T(0)) return T(0.5);
+    const T sq = sqrt(disc);
+    const T t = b < T(0) ? (T(2) * cc) / (sq - b) : (-b - sq) / (T(2) * cc2);
+    return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+}
+
+// lattice directions as run-time tables (for link work distributed over lanes)
+static __constant__ signed char k_c[Q][3] = {{0, 0, 0},   {0, 1, 0},   {0, -1, 0},  {-1, 0, 0},  {1, 0, 0},
+                                      {0, 0, 1},   {0, 0, -1},  {-1, 1, 0},  {1, 1, 0},   {-1, -1, 0},
+                                      {1, -1, 0},  {0, 1, 1},   {0, -1, 1},  {-1, 0, 1},  {1, 0, 1},
+                                      {0, 1, -1},  {0, -1, -1}, {-1, 0, -1}, {1, 0, -1}};
+static __constant__ signed char k_opp[Q] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 16, 15, 18, 17, 12, 11, 14, 13};
+
+
+// inclusive prefix sum over the warp and the lane holding rank k of it
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+__device__ __forceinline__ int owner_lane(int incl, int k) {
+    int src = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int t = __shfl_sync(0xffffffffu, incl, src + step - 1);
+        if (t <= k) src += step;
+    }
+    return src > 31 ? 31 : src;
+}
+
+}  // namespace lbmdem

@@ -14,7 +14,8 @@
 // refill list with their former particle. Fluid cells within R + sqrt(2) of a
 // particle get the NEAR flag; solid cells next to another body (candidates for
 // missing links) go to the missing-link list that the boundary kernel of the
-// next step reads.
+// next step reads. A cell that turns solid gets the NaN marker in all its PDF
+// slots of both buffers.
 #include "common.cuh"
 #include "launch.h"
 
@@ -108,6 +109,21 @@ void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ mapping
+
+// The NaN marker that every PDF slot of a solid cell holds (the dense kernel
+// finds particle links by it): all-ones exponent and mantissa, a NaN in
+// float64, float32, float16 and bfloat16.
+__device__ __forceinline__ void put_markers(void* const (&pdf)[2], int elem, long long ncells, long long idx) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        for (int q = 0; q < Q; ++q) {
+            const long long k = (long long)q * ncells + idx;
+            if (elem == 8) reinterpret_cast<unsigned long long*>(pdf[b])[k] = 0x7fffffffffffffffull;
+            else if (elem == 4) reinterpret_cast<unsigned int*>(pdf[b])[k] = 0x7fffffffu;
+            else reinterpret_cast<unsigned short*>(pdf[b])[k] = (unsigned short)0x7fff;
+        }
+    }
+}
 
 // Exact float64 decision of the solid and shell tests for a cell centre whose
 // float32 distance lies within the tolerance of a threshold (kept out of line:
@@ -287,6 +303,7 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
                 miss_bits |= 1u << j;
             }
             p.owner[idx] = own[j];
+            if (!(old & FL_SOLID) && p.pdf[0]) put_markers(p.pdf, p.elem, p.g.ncells, idx);
         } else {
             if (shell4 & (1u << j)) nf |= FL_SHELL;
             if (nn >= 1u) nf |= FL_NEAR;
@@ -355,6 +372,17 @@ void launch_map(const MapParams& p, cudaStream_t st) {
     dim3 block(TILE_X, TILE_Y, 1);
     dim3 grid(p.ntile[0], p.ntile[1], p.ntile[2]);
     map_kernel<<<grid, block, 0, st>>>(p);
+}
+
+__global__ void solid_markers_kernel(const __grid_constant__ MapParams p) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < p.g.ncells; idx += stride)
+        if (p.flags[idx] & FL_SOLID) put_markers(p.pdf, p.elem, p.g.ncells, idx);
+}
+
+void launch_solid_markers(const MapParams& p, cudaStream_t st) {
+    if (!p.pdf[0]) return;
+    solid_markers_kernel<<<152 * 8, 256, 0, st>>>(p);
 }
 
 // ------------------------------------------------------------ refill

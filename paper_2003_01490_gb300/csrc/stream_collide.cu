@@ -1,22 +1,46 @@
-// stream_collide.cu -- the dense kernel of one lattice Boltzmann step
-// (Algorithm 1, lines 2-3): one thread per cell, pull streaming (Eq. (2)) with
-// halfway bounce-back on the walls of the box (Eq. (14), delta = 1/2, wall
-// velocity), then the two-relaxation-time collision (Eq. (10), magic
-// parameter Eq. (11)) with Guo forcing; in TRT+aB shell cells (Sec. 2.3.2) and
-// for Lambda_b,bulk != 1 the two bulk moments m4, m5 relax with s_b (Eq. (12))
+// stream_collide.cu -- the dense kernel of one lattice Boltzmann step with
+// moving particles (Algorithm 1, lines 1-3): one thread per cell, pull
+// streaming (Eq. (2)), the particle links of the cell (CLI moving no-slip
+// condition, Eq. (14), and momentum exchange, Eqs. (15)-(17)), halfway
+// bounce-back on the walls of the box (Eq. (14), delta = 1/2, wall velocity),
+// then the two-relaxation-time collision (Eq. (10), magic parameter
+// Eq. (11)) with Guo forcing; in TRT+aB shell cells (Sec. 2.3.2) and for
+// Lambda_b,bulk != 1 the two bulk moments m4, m5 relax with s_b (Eq. (12))
 // through a rank-2 correction in moment space.
 //
 // PDFs are stored shifted (f_q - w_q) in SoA layout f[q][z][y][x], read from
-// one buffer and written to the other. Particle links need no logic here: the
-// boundary kernel has already written their CLI values into the solid-cell
-// slots that the pull of a fluid cell reads.
+// one buffer and written to the other. Every PDF slot of a solid cell holds a
+// NaN marker (written by the mapping when the cell turns solid and kept by
+// this kernel), so the pull of a fluid cell x finds its particle links for
+// free: direction q is a link exactly when the value pulled from
+// y = x - c_q is the marker. The warp then spreads its links evenly over its
+// lanes; each link's CLI value f_q(x, t+1) (link fraction delta_p from the
+// ray-sphere intersection; bounce-back, delta = 1/2 in the coefficients, when
+// x + c_q is not fluid) goes through shared memory to the thread of x, and
+// its force and torque are reduced per warp by particle (lanes with the same
+// particle found with match_any) and added atomically.
+//
+// Per-particle sums. Float64 storage: float64 partial sums, float64 atomics.
+// Float32 compute: the link force splits into the constant part 2 w_p c_p,
+// an integer multiple of c_p / 36, and the small remainder
+// c_p (f~_p + f_q) - u_b (f~_p - f_q). The constant part and its torque
+// 2 w_p (n + g) x c_p (n the integer offset of the cell from the particle's
+// base cell, g the fractional offset common to all links) are summed exactly
+// in integers; the remainder is summed per warp in float32 and per particle
+// in 64-bit fixed point (scale 2^32) through integer atomics. No float64
+// instruction runs per cell or link on the float32 path.
 #include "common.cuh"
 #include "launch.h"
+#include "links.cuh"
 
 // minimum resident blocks per SM requested for the kernel with 4-byte or
 // smaller storage (a register cap of 64 at 256 threads); tuned on GB300
 #ifndef LBM_SC_MIN_BLOCKS
 #define LBM_SC_MIN_BLOCKS 4
+#endif
+// consecutive z planes marched by one block
+#ifndef LBM_SC_ZCHUNK
+#define LBM_SC_ZCHUNK 16
 #endif
 // cache policy: 0 default loads and stores, 1 streaming (evict-first) stores,
 // 2 streaming loads and stores
@@ -37,7 +61,94 @@ struct SCArgs {
     int bulk_corr;
     const T* __restrict__ accel;     // [3]
     int* status;
+    // particles (for the links)
+    int np;
+    const int* __restrict__ owner;   // particle of a solid cell, -1 for fluid
+    const double* __restrict__ px;
+    const double* __restrict__ pu;
+    const double* __restrict__ pom;
+    const double* __restrict__ pR;
+    const PartView* __restrict__ view;
+    double* acc_d;
+    long long* acc_i;
+    long long* acc_k;
 };
+
+// NaN marker held by every PDF slot of a solid cell
+template <typename T>
+__device__ __forceinline__ T solid_marker();
+template <> __device__ __forceinline__ float solid_marker<float>() { return __int_as_float(0x7fffffff); }
+template <> __device__ __forceinline__ double solid_marker<double>() { return __longlong_as_double(0x7fffffffffffffffLL); }
+
+// CLI value f_q(x, t+1) of the link of fluid cell (x, y, z) in pull direction
+// q into the solid cell x - c_q, and its force and torque into acc (float32
+// path: the remainder part in floats, the constant part as exact integers)
+template <typename S, typename T>
+__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, Acc<T>& acc,
+                                        const Sinks& sk) {
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    const int plane = nx * ny;
+    const long long N = a.g.ncells;
+    const int c[3] = {k_c[q][0], k_c[q][1], k_c[q][2]};
+    const int p = k_opp[q];
+    const int cpos[3] = {x, y, z};
+    int uv[3], dv[3];
+    bool cli = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        uv[d] = wrap_idx(cpos[d] - c[d], a.g.n[d]);
+        dv[d] = cpos[d] + c[d];
+        if (!a.g.per[d] && (dv[d] < 0 || dv[d] >= a.g.n[d])) cli = false;
+        dv[d] = wrap_idx(dv[d], a.g.n[d]);
+    }
+    const int idx = z * plane + y * nx + x;
+    const int up = uv[2] * plane + uv[1] * nx + uv[0];
+    const int down = dv[2] * plane + dv[1] * nx + dv[0];
+    const int i = a.owner[up];
+    if (i < 0) return solid_marker<T>();   // a NaN from a fluid cell: left for the stability check
+    const T fout = Store<S>::load(a.src + p * N + idx);
+    const T fin = Store<S>::load(a.src + q * N + idx);
+    T fdown = cli ? Store<S>::load(a.src + p * N + down) : T(0);
+    if (fdown != fdown) {   // x + c_q is solid: bounce-back coefficients
+        cli = false;
+        fdown = T(0);
+    }
+    T r[3], R, u[3], om[3];
+    int n[3];
+    PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
+    const int cp[3] = {-c[0], -c[1], -c[2]};
+    const T cp0 = (T)cp[0], cp1 = (T)cp[1], cp2 = (T)cp[2];
+    const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
+    const T delta = link_fraction<T>(r, cp0, cp1, cp2, (T)cc2, R);
+    const T dbc = cli ? delta : T(0.5);
+    const T inv = T(1) / (T(1) + T(2) * dbc);
+    const T kappa = (T(1) - T(2) * dbc) * inv;
+    const T rb[3] = {r[0] + delta * cp0, r[1] + delta * cp1, r[2] + delta * cp2};
+    const T ub[3] = {u[0] + (om[1] * rb[2] - om[2] * rb[1]), u[1] + (om[2] * rb[0] - om[0] * rb[2]),
+                     u[2] + (om[0] * rb[1] - om[1] * rb[0])};
+    const T ubc = ub[0] * cp0 + ub[1] * cp1 + ub[2] * cp2;
+    const T v = fout + kappa * (fdown - fin) - (T(12) * w * inv) * ubc;
+    // Eq. (15) on shifted PDFs: F = c_p (2 w + f~_p + f_q) - u_b (f~_p - f_q)
+    const T dif = fout - v;
+    int K[6] = {0, 0, 0, 0, 0, 0};
+    T sum;
+    if (sizeof(T) == 4) {
+        // 2 w_p c_p and its torque 2 w_p (n x c_p) as exact integers (x 36)
+        const int kw = cc2 == 1 ? 4 : 2;
+        sum = fout + v;
+        K[0] = kw * cp[0]; K[1] = kw * cp[1]; K[2] = kw * cp[2];
+        K[3] = kw * (n[1] * cp[2] - n[2] * cp[1]);
+        K[4] = kw * (n[2] * cp[0] - n[0] * cp[2]);
+        K[5] = kw * (n[0] * cp[1] - n[1] * cp[0]);
+    } else {
+        sum = T(2) * w + fout + v;
+    }
+    const T F[3] = {cp0 * sum - ub[0] * dif, cp1 * sum - ub[1] * dif, cp2 * sum - ub[2] * dif};
+    const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
+    accumulate<T>(i, F, Tq, K, acc, sk);
+    return v;
+}
 
 template <typename S>
 __device__ __forceinline__ typename Store<S>::T sc_load(const S* p) {
@@ -60,127 +171,232 @@ __device__ __forceinline__ void sc_store(S* p, typename Store<S>::T v) {
 #endif
 }
 
-// Cell indices are 32-bit (the library limits boxes to fewer than 2^31
-// cells); each PDF array q starts at the uniform pointer src + q N.
+// TRT+aB collision of one fluid cell (in place) and the store of its PDFs
+template <typename S, typename T>
+__device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], uint8_t fl, long long N, int idx) {
+    // ------------------------------------------- TRT+aB collision (in place)
+    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        drho += f[q];
+        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
+        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
+        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
+    }
+    const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
+    const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T ua = ux * ax + uy * ay + uz * az;
+    const T sp = a.s_plus, sm = a.s_minus;
+    const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
+    // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) of the streamed
+    // PDFs relax with s_b in shell cells (and everywhere when Lambda_b,bulk != 1)
+    const bool shell = (fl & FL_SHELL) != 0;
+    const bool bulk = shell || a.bulk_corr;
+    T k4 = T(0), k5 = T(0);
+    if (bulk) {
+        const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
+        T saxis = T(0), sdiag = T(0);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
+        }
+        const T m4 = -f[0] + sdiag;
+        const T m5 = f[0] - T(2) * saxis + sdiag;
+        // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
+        k4 = T(1.5) * (ds * ((usq - m4) - ua));
+        k5 = T(0.5) * (ds * (-m5));
+    }
+    {
+        const T w0 = wq<T>(0);
+        const T feq0 = w0 * (drho - T(1.5) * usq);
+        f[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua)) + w0 * (k5 - k4);
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int qb = opp(q);
+        if (qb < q) continue;
+        const T w = wq<T>(q);
+        const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
+        const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
+        const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
+        const T em = w * (T(3) * cu);
+        const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
+        const T Fm = w * (T(3) * ca);
+        const T fp = T(0.5) * (f[q] + f[qb]);
+        const T fm = T(0.5) * (f[q] - f[qb]);
+        const T corr = c2(q) == 1 ? w * (T(-2) * k5) : w * (k4 + k5);
+        const T dp = -sp * (fp - ep) + gp * Fp + corr;
+        const T dm = -sm * (fm - em) + gm * Fm;
+        f[q] = f[q] + dp + dm;
+        f[qb] = f[qb] + dp - dm;
+    }
+    if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
+}
+
+// One block per (x, y) tile of 256 cells and a chunk of LBM_SC_ZCHUNK
+// consecutive z planes, marched in order: the links a warp meets in
+// consecutive rows mostly belong to the same spheres, so a lane's force sums
+// (kept in shared memory between rows) rarely change particle and the warp
+// commits them once per chunk. Cell indices are 32-bit (the library limits
+// boxes to 2^31 - 2^24 cells); each PDF array q starts at src + q N.
 template <typename S, typename T>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
     const bool valid = x < nx && y < ny;
     const int plane = nx * ny;
     const long long N = a.g.ncells;
-    const int idx = z * plane + y * nx + x;
-    const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
-    const bool fluid = !(fl & FL_SOLID);
-    // Solid cells that share a 32-byte sector with fluid cells also write
-    // (zeros; solid slots are never read before the boundary kernel rewrites
-    // them), so every written sector is complete and L2 needs no fill read.
-    constexpr int G = 32 / (int)sizeof(S);
-    const unsigned bal = __ballot_sync(0xffffffffu, fluid && valid);
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;   // warps hold 32 consecutive tids
+    // dynamic shared memory (sc_smem_bytes): PDFs of the cells of warps with
+    // links [q][thread]; per lane the particle of its open force sums (-1:
+    // none), the open float sums (F, T) and the exact integer sums (float32
+    // path); per warp the link entries q | lane << 8
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    T (*s_f)[256] = reinterpret_cast<T (*)[256]>(sc_smem);
+    T (*s_sum)[256] = reinterpret_cast<T (*)[256]>(sc_smem + Q * 256 * sizeof(T));
+    int (*s_int)[256] = reinterpret_cast<int (*)[256]>(sc_smem + (Q + 6) * 256 * sizeof(T));
+    int* s_key = reinterpret_cast<int*>(sc_smem + (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0));
+    unsigned short (*s_queue)[32 * (Q - 1)] =
+        reinterpret_cast<unsigned short (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
+    constexpr int G = 32 / (int)sizeof(S);
     const unsigned gmask = (G >= 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
-
-    if (!fluid) {
-        if (valid && (bal & gmask)) {
+    const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
+    s_key[tid] = -1;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, T(0));
-        }
-        return;
+    for (int c = 0; c < 6; ++c) {
+        s_sum[c][tid] = T(0);
+        if (sizeof(T) == 4) s_int[c][tid] = 0;
     }
-    {
-        // neighbour offsets with periodic wrap (walls are handled below)
-        const int OX[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
-        const int OY[3] = {y == 0 ? plane - nx : -nx, 0, y == ny - 1 ? nx - plane : nx};
-        const int OZ[3] = {z == 0 ? (nz - 1) * plane : -plane, 0, z == nz - 1 ? (1 - nz) * plane : plane};
-        T f[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-            f[q] = sc_load<S>(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
-        // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
-        const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
-        const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
-        const bool wz = !a.g.per[2] && (z == 0 || z == nz - 1);
-        if (wx || wy || wz) {
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const int u0 = x - cx(q), u1 = y - cy(q), u2 = z - cz(q);
-                int axis = -1, side = 0;
-                if (wz && (u2 < 0 || u2 >= nz)) { axis = 2; side = u2 < 0 ? 0 : 1; }
-                else if (wy && (u1 < 0 || u1 >= ny)) { axis = 1; side = u1 < 0 ? 0 : 1; }
-                else if (wx && (u0 < 0 || u0 >= nx)) { axis = 0; side = u0 < 0 ? 0 : 1; }
-                if (axis < 0) continue;
-                const int p = opp(q);
-                const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
-                              a.uw[side][axis][2] * (T)(-cz(q));
-                f[q] = Store<S>::load(a.src + p * N + idx) - T(6) * wq<T>(p) * ucp;
-            }
-        }
+    bool open = false;   // warp-uniform: some lane of the warp holds sums
 
-        // ------------------------------------------- TRT+aB collision (in place)
-        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+    const int z_begin = blockIdx.z * LBM_SC_ZCHUNK;
+    const int z_end = min(nz, z_begin + LBM_SC_ZCHUNK);
+    for (int z = z_begin; z < z_end; ++z) {
+        const int idx = z * plane + y * nx + x;
+        const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
+        const bool fluid = !(fl & FL_SOLID);
+        // lanes of a 32-byte sector (G cells) that hold fluid cells
+        const unsigned bal = __ballot_sync(FULL, fluid && valid);
+        T f[Q];
+        unsigned lmask = 0;   // pull directions of this cell that are particle links
+        if (fluid) {
+            // neighbour offsets with periodic wrap (walls are handled below)
+            const int OX[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
+            const int OY[3] = {y == 0 ? plane - nx : -nx, 0, y == ny - 1 ? nx - plane : nx};
+            const int OZ[3] = {z == 0 ? (nz - 1) * plane : -plane, 0, z == nz - 1 ? (1 - nz) * plane : plane};
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            drho += f[q];
-            if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
-            if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
-            if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
-        }
-        const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
-        const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
-        const T usq = ux * ux + uy * uy + uz * uz;
-        const T ua = ux * ax + uy * ay + uz * az;
-        const T sp = a.s_plus, sm = a.s_minus;
-        const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
-        // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) of the streamed
-        // PDFs relax with s_b in shell cells (and everywhere when Lambda_b,bulk != 1)
-        const bool shell = (fl & FL_SHELL) != 0;
-        const bool bulk = shell || a.bulk_corr;
-        T k4 = T(0), k5 = T(0);
-        if (bulk) {
-            const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
-            T saxis = T(0), sdiag = T(0);
+            for (int q = 0; q < Q; ++q)
+                f[q] = sc_load<S>(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
+            for (int q = 1; q < Q; ++q)
+                if (f[q] != f[q]) lmask |= 1u << q;   // marker of a solid upstream cell
+            // halfway bounce-back on the box walls (Eq. (14) with delta = 1/2)
+            const bool wx = !a.g.per[0] && (x == 0 || x == nx - 1);
+            const bool wy = !a.g.per[1] && (y == 0 || y == ny - 1);
+            const bool wz = !a.g.per[2] && (z == 0 || z == nz - 1);
+            if (wx || wy || wz) {
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    const int u0 = x - cx(q), u1 = y - cy(q), u2 = z - cz(q);
+                    int axis = -1, side = 0;
+                    if (wz && (u2 < 0 || u2 >= nz)) { axis = 2; side = u2 < 0 ? 0 : 1; }
+                    else if (wy && (u1 < 0 || u1 >= ny)) { axis = 1; side = u1 < 0 ? 0 : 1; }
+                    else if (wx && (u0 < 0 || u0 >= nx)) { axis = 0; side = u0 < 0 ? 0 : 1; }
+                    if (axis < 0) continue;
+                    const int p = opp(q);
+                    const T ucp = a.uw[side][axis][0] * (T)(-cx(q)) + a.uw[side][axis][1] * (T)(-cy(q)) +
+                                  a.uw[side][axis][2] * (T)(-cz(q));
+                    f[q] = Store<S>::load(a.src + p * N + idx) - T(6) * wq<T>(p) * ucp;
+                    lmask &= ~(1u << q);
+                }
             }
-            const T m4 = -f[0] + sdiag;
-            const T m5 = f[0] - T(2) * saxis + sdiag;
-            // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
-            k4 = T(1.5) * (ds * ((usq - m4) - ua));
-            k5 = T(0.5) * (ds * (-m5));
         }
-        {
-            const T w0 = wq<T>(0);
-            const T feq0 = w0 * (drho - T(1.5) * usq);
-            f[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua)) + w0 * (k5 - k4);
-        }
+        // particle links of the warp, spread evenly over its lanes: each lane
+        // with links queues (direction, lane) entries in shared memory at its
+        // prefix-sum offset
+        if (a.np > 0 && __any_sync(FULL, lmask != 0)) {
+            const int cnt = __popc(lmask);
+            const int incl = warp_incl_scan(cnt, lane);
+            const int total = __shfl_sync(FULL, incl, 31);
+            unsigned short* queue = s_queue[tid >> 5];
+            {
+                unsigned mm = lmask;
+                int pos = incl - cnt;
+                while (mm) {
+                    const int q = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    queue[pos++] = (unsigned short)(q | (lane << 8));
+                }
+            }
+            // the cell's PDFs wait in shared memory (freeing their registers for
+            // the link work); each link's CLI value lands in its cell's slot
 #pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            const int qb = opp(q);
-            if (qb < q) continue;
-            const T w = wq<T>(q);
-            const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
-            const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
-            const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
-            const T em = w * (T(3) * cu);
-            const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
-            const T Fm = w * (T(3) * ca);
-            const T fp = T(0.5) * (f[q] + f[qb]);
-            const T fm = T(0.5) * (f[q] - f[qb]);
-            const T corr = c2(q) == 1 ? w * (T(-2) * k5) : w * (k4 + k5);
-            const T dp = -sp * (fp - ep) + gp * Fp + corr;
-            const T dm = -sm * (fm - em) + gm * Fm;
-            f[q] = f[q] + dp + dm;
-            f[qb] = f[qb] + dp - dm;
-        }
-        if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
+            for (int q = 0; q < Q; ++q) s_f[q][tid] = f[q];
+            __syncwarp();
+            Acc<T> acc;
+            acc.key = s_key[tid];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
+            for (int c = 0; c < 6; ++c) {
+                acc.f[c] = s_sum[c][tid];
+                if (sizeof(T) == 4) acc.k[c] = s_int[c][tid];
+            }
+            // lane l takes the m consecutive entries l m .. l m + m - 1
+            const int m = (total + 31) >> 5;
+            for (int j = 0; j < m; ++j) {
+                const int k = lane * m + j;
+                if (k < total) {
+                    const unsigned e = queue[k];
+                    const int q = (int)(e & 31u), src = (int)(e >> 8);
+                    s_f[q][tid - lane + src] = link_value<S, T>(a, x - lane + src, y, z, q, acc, sk);
+                }
+            }
+            s_key[tid] = acc.key;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                s_sum[c][tid] = acc.f[c];
+                if (sizeof(T) == 4) s_int[c][tid] = acc.k[c];
+            }
+            open = true;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = s_f[q][tid];
+        }
+        if (!fluid) {
+            // Solid cells keep the marker in every slot. Those that share a
+            // 32-byte sector with fluid cells write it again, so every written
+            // sector is complete and L2 needs no fill read.
+            if (valid && (bal & gmask)) {
+                const T mk = solid_marker<T>();
+#pragma unroll
+                for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, mk);
+            }
+        } else {
+            collide_store<S, T>(a, f, fl, N, idx);
+        }
+    }
+    if (open) {   // warp-uniform
+        Acc<T> acc;
+        acc.key = s_key[tid];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            acc.f[c] = s_sum[c][tid];
+            if (sizeof(T) == 4) acc.k[c] = s_int[c][tid];
+        }
+        commit<T>(acc, sk);
     }
 }
 
+// bytes of dynamic shared memory of the kernel (256 threads)
+template <typename T>
+constexpr size_t sc_smem_bytes() {
+    return (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0) + 256 * 4 + 8 * 32 * (Q - 1) * 2;
+}
 
 template <typename S>
 void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
@@ -200,12 +416,25 @@ void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
     a.bulk_corr = p.bulk_corr;
     a.accel = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)p.accel_d : (const void*)p.accel_f);
     a.status = p.status;
+    a.np = p.P.n;
+    a.owner = p.owner;
+    a.px = p.P.x;
+    a.pu = p.P.u;
+    a.pom = p.P.om;
+    a.pR = p.P.R;
+    a.view = p.P.view;
+    a.acc_d = p.P.acc_d;
+    a.acc_i = p.P.acc_i;
+    a.acc_k = p.P.acc_k;
     const int nx = p.g.n[0];
     int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
     int by = 256 / bx;
     dim3 block(bx, by, 1);
-    dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, p.g.n[2]);
-    stream_collide_kernel<S, T><<<grid, block, 0, st>>>(a);
+    dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, (p.g.n[2] + LBM_SC_ZCHUNK - 1) / LBM_SC_ZCHUNK);
+    constexpr size_t smem = sc_smem_bytes<T>();
+    if (smem > 48 * 1024)   // float64 storage: above the default limit (set on the current device)
+        cudaFuncSetAttribute(stream_collide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    stream_collide_kernel<S, T><<<grid, block, smem, st>>>(a);
 }
 
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st) {
