@@ -103,7 +103,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ('stream_collide.cu', 'common.cuh'):
+    for f in ('stream_collide.cu', 'links.cuh', 'common.cuh'):
         with open(os.path.join(ROOT, 'paper_2003_01490_gb300', 'csrc', f), 'rb') as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -434,6 +434,13 @@ DemParams dem_params(lbm_ctx* ctx) {
     dp.e_dry = d.e_dry; dp.Tc = d.Tc; dp.nu_p = d.nu_p; dp.mu_p = d.mu_p;
     dp.cut_n = d.lub_cut_n; dp.cut_tt = d.lub_cut_tt; dp.cut_tr = d.lub_cut_tr;
     dp.min_a = d.lub_min_a; dp.min_b = d.lub_min_b;
+    dp.inv_cut_n = 1.0 / d.lub_cut_n;
+    dp.inv_cut_tt = 1.0 / d.lub_cut_tt;
+    dp.inv_cut_tr = 1.0 / d.lub_cut_tr;
+    dp.log_e = std::log(d.e_dry);
+    dp.pi2_log_e2 = 3.14159265358979323846 * 3.14159265358979323846 + dp.log_e * dp.log_e;
+    dp.kappa = 2.0 * (1.0 - d.nu_p) / (2.0 - d.nu_p);
+    dp.sqrt_kappa = std::sqrt(dp.kappa);
     for (int a = 0; a < 3; ++a) dp.gravity[a] = d.gravity[a];
     dp.mu_f = (ctx->relax.tau - 0.5) / 3.0;
     dp.lubrication = d.lubrication;

@@ -170,7 +170,7 @@ void launch_boundary_t(const LbmStepParams& p, cudaStream_t st) {
     b.n_solid = p.n_solid;
     b.accel_d = p.accel_d;
     b.accel_f = p.accel_f;
-    const int blocks = p.missing_links ? (p.num_sms > 0 ? p.num_sms : 1) : 1;
+    const int blocks = p.missing_links ? 8 * (p.num_sms > 0 ? p.num_sms : 1) : 1;
     boundary_kernel<S><<<blocks, 128, 0, st>>>(b);
 }
 

@@ -243,41 +243,52 @@ __device__ void lubrication_on_i(const DemParams& p, double Ri, double Rj, doubl
         c_n = 1.0; c_ftt = 8.0 / 15.0; c_ttt = 1.0 / 10.0; c_ftr = 2.0 / 15.0; c_ttr = 2.0 / 5.0;
         om_ftr = omi;
         om_ttr = omi;
+    } else if (Rj == Ri) {
+        // k = 1: the coefficients below are exact binary fractions or the
+        // correctly rounded quotients the general formulas give
+        c_n = 0.25; c_ftt = 1.0 / 6.0; c_ttt = 0.125; c_ftr = 1.0 / 30.0; c_ttr = 0.2;
+        const V3 oms = omi + omj;
+        om_ftr = oms + 4.0 * omi + 4.0 * omj;
+        om_ttr = omi + 0.25 * omj;
     } else {
         const double k = Rj / Ri;
         const double k1 = 1.0 + k;
-        c_n = k * k / (k1 * k1);
-        c_ftt = 4.0 * k * (2.0 + k + 2.0 * k * k) / (15.0 * k1 * k1 * k1);
-        c_ttt = k * (4.0 + k) / (10.0 * k1 * k1);
-        c_ftr = 2.0 * k * k / (15.0 * k1 * k1);
-        c_ttr = 2.0 * k / (5.0 * k1);
+        const double i1 = 1.0 / k1;
+        const double i2 = i1 * i1;
+        c_n = k * k * i2;
+        c_ftt = 4.0 * k * (2.0 + k + 2.0 * k * k) * (i2 * i1) * (1.0 / 15.0);
+        c_ttt = k * (4.0 + k) * i2 * 0.1;
+        c_ftr = 2.0 * k * k * i2 * (1.0 / 15.0);
+        c_ttr = 2.0 * k * i1 * 0.2;
         const V3 oms = omi + omj;
-        om_ftr = oms + (4.0 / k) * omi + (4.0 * k) * omj;
-        om_ttr = omi + (k / 4.0) * omj;
+        om_ftr = oms + (4.0 * Ri / Rj) * omi + (4.0 * k) * omj;
+        om_ttr = omi + (k * 0.25) * omj;
     }
     if (delta > 0.0 && delta < p.cut_n)
-        F = F + (-6.0 * pi * mu * Ri * Ri * c_n * (1.0 / dl - 1.0 / p.cut_n)) * un;
-    if (p.tangential && delta > 0.0 && delta < p.cut_tt) {
-        const double lg = log(dl / p.cut_tt);
-        F = F + (6.0 * pi * mu * Ri * c_ftt * lg) * ut;
-        T = T + (8.0 * pi * mu * Ri * Ri * c_ttt * lg) * cross(uij, n);
-    }
-    if (p.tangential && delta > 0.0 && delta < p.cut_tr) {
-        const double lg = log(dl / p.cut_tr);
-        F = F + (-6.0 * pi * mu * Ri * Ri * c_ftr * lg) * cross(om_ftr, n);
-        T = T + (8.0 * pi * mu * Ri * Ri * Ri * c_ttr * lg) * (om_ttr - dot(om_ttr, n) * n);
+        F = F + (-6.0 * pi * mu * Ri * Ri * c_n * (1.0 / dl - p.inv_cut_n)) * un;
+    const bool tt = p.tangential && delta > 0.0 && delta < p.cut_tt;
+    const bool tr = p.tangential && delta > 0.0 && delta < p.cut_tr;
+    if (tt || tr) {
+        const double lg_tt = log(dl * p.inv_cut_tt);
+        const double lg_tr = p.cut_tr == p.cut_tt ? lg_tt : log(dl * p.inv_cut_tr);
+        if (tt) {
+            F = F + (6.0 * pi * mu * Ri * c_ftt * lg_tt) * ut;
+            T = T + (8.0 * pi * mu * Ri * Ri * c_ttt * lg_tt) * cross(uij, n);
+        }
+        if (tr) {
+            F = F + (-6.0 * pi * mu * Ri * Ri * c_ftr * lg_tr) * cross(om_ftr, n);
+            T = T + (8.0 * pi * mu * Ri * Ri * Ri * c_ttr * lg_tr) * (om_ttr - dot(om_ttr, n) * n);
+        }
     }
 }
 
 // normal + Coulomb-limited tangential contact force on i, Eqs. (41)-(50)
 __device__ void contact_force(const DemParams& p, V3 n, double delta, V3 ucp, V3 uij, double m_eff,
                               double Tc, V3 dt_old, V3& Fn, V3& Ft, V3& dt_new) {
-    const double pi = 3.14159265358979323846;
-    const double le = log(p.e_dry);
-    const double kn = m_eff * (pi * pi + le * le) / (Tc * Tc);
-    const double dn = -2.0 * m_eff * le / Tc;
-    const double kappa = 2.0 * (1.0 - p.nu_p) / (2.0 - p.nu_p);
-    const double kt = kappa * kn, dtg = sqrt(kappa) * dn;
+    const double iT = 1.0 / Tc;
+    const double kn = m_eff * p.pi2_log_e2 * (iT * iT);
+    const double dn = -2.0 * m_eff * p.log_e * iT;
+    const double kt = p.kappa * kn, dtg = p.sqrt_kappa * dn;
     const V3 un = dot(uij, n) * n;
     const V3 ut = ucp - un;
     Fn = (-kn * delta) * n - dn * un;

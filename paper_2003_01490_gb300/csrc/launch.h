@@ -103,6 +103,9 @@ struct DemParams {
     double cut_max;         // largest lubrication cut-off
     double e_dry, Tc, nu_p, mu_p;
     double cut_n, cut_tt, cut_tr, min_a, min_b;
+    // derived on the host: 1 / cut-offs, log e_dry, pi^2 + (log e_dry)^2,
+    // kappa = 2 (1 - nu) / (2 - nu) and its square root
+    double inv_cut_n, inv_cut_tt, inv_cut_tr, log_e, pi2_log_e2, kappa, sqrt_kappa;
     double gravity[3];
     double mu_f;            // dynamic fluid viscosity rho0 nu
     int lubrication, tangential;
