@@ -263,6 +263,27 @@ def barrier(world):
         dist.barrier()
 
 
+def count_links(solid, periodic):
+    """Particle links of the mapping: (fluid cell x, direction q) pairs whose
+    upstream cell x - c_q is solid. solid is indexed [z, y, x]; on a
+    non-periodic axis the cells beyond the box are walls, not particles."""
+    import numpy as np
+    c = [(0, 1, 0), (0, -1, 0), (-1, 0, 0), (1, 0, 0), (0, 0, 1), (0, 0, -1), (-1, 1, 0), (1, 1, 0),
+         (-1, -1, 0), (1, -1, 0), (0, 1, 1), (0, -1, 1), (-1, 0, 1), (1, 0, 1), (0, 1, -1), (0, -1, -1),
+         (-1, 0, -1), (1, 0, -1)]
+    fluid = ~solid
+    n = 0
+    for cx, cy, cz in c:
+        up = np.roll(solid, shift=(cz, cy, cx), axis=(0, 1, 2))
+        for axis, cc in ((2, cx), (1, cy), (0, cz)):
+            if cc and not periodic[2 - axis]:
+                sl = [slice(None)] * 3
+                sl[axis] = 0 if cc > 0 else -1
+                up[tuple(sl)] = False
+        n += int(np.count_nonzero(fluid & up))
+    return n
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -295,13 +316,18 @@ def run_ours(args, rank, world, local):
     phases, nsteps = L.lbm_profile_read(ctx)
     L.lbm_profile(ctx, 0)
     _, _, flags = L.lbm_get_fields(ctx)
-    n_solid = int(((flags & L.FLAG_SOLID) != 0).sum())
+    solid = (flags & L.FLAG_SOLID) != 0
+    n_solid = int(solid.sum())
+    n_links = count_links(solid, w['periodic'])
     ms_max = allreduce_max(ms, world)
     value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     bf, bs = bytes_per_cell(storage)
-    alg_bytes = (cells - n_solid) * bf + n_solid * bs
+    # per link the kernel also reads f~_p(x), which no pull reads, and the
+    # owner of the solid cell
+    es = {'f64': 8, 'f32': 4}.get(storage, 2)
+    alg_bytes = (cells - n_solid) * bf + n_solid * bs + n_links * (es + 4)
     k_ms = phases['stream_collide'] / max(nsteps, 1)
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
@@ -309,8 +335,10 @@ def run_ours(args, rank, world, local):
     share = {k: round(v / sum(phases.values()), 4) for k, v in phases.items()} if sum(phases.values()) else {}
     roofline = {'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
                 'frac': round(achieved / peak, 4), 'traffic': traffic,
-                'kernel': 'stream_collide_kernel (pull stream, wall bounce-back, TRT+aB collision)',
+                'kernel': 'stream_collide_kernel (pull stream with the particle links: CLI condition and '
+                          'momentum exchange; wall bounce-back; TRT+aB collision)',
                 'kernel_ms_per_launch': round(k_ms, 5), 'alg_bytes_per_launch': int(alg_bytes),
+                'links_per_launch': int(n_links),
                 'peak_source': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
                 else 'fallback 6.8 TB/s', 'phase_share': share}
 
