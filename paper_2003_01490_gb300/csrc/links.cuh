@@ -174,6 +174,13 @@ __device__ __forceinline__ T two_sum(T a, T b, T& err) {
     return s;
 }
 
+// square root and quotient: hardware approximations (a few ulp) for float32,
+// IEEE for float64
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double fast_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
 // smallest t in [0, 1] with |r + t c| = R (link fraction delta of Eq. (14)).
 // |r|^2 - R^2 cancels strongly near the surface, so it is formed from exact
 // products and compensated sums; the root uses the cancellation-free form
@@ -191,8 +198,8 @@ __device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T
     const T cc = sum + (err + e);
     const T disc = b * b - T(4) * cc2 * cc;
     if (disc < T(0)) return T(0.5);
-    const T sq = sqrt(disc);
-    const T t = b < T(0) ? (T(2) * cc) / (sq - b) : (-b - sq) / (T(2) * cc2);
+    const T sq = fast_sqrt(disc);
+    const T t = b < T(0) ? fast_div(T(2) * cc, sq - b) : fast_div(-b - sq, T(2) * cc2);
     return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
 }
 

@@ -78,34 +78,44 @@ __device__ int axis_tiles(int np, const int (&a)[2], const int (&b)[2], int tsiz
     return 2;
 }
 
+// one warp per particle; the lanes share out the tiles of its box
 __global__ void tile_scatter_kernel(const MapParams p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.P.n) return;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= p.P.n) return;   // warp-uniform
     const double r = p.P.R[i] + fmax(p.shell_width, 1.4142135623730951) + 0.02;
     const int ts[3] = {TILE_X, TILE_Y, TILE_Z};
-    int na[3], t0[3][2], t1[3][2];
+    int na[3], t0[3][2], t1[3][2], cnt[3];
     for (int d = 0; d < 3; ++d) {
         int a[2], b[2];
         int np = axis_pieces(p.P.x[3 * i + d], r, p.g.n[d], p.g.per[d], a, b);
         na[d] = axis_tiles(np, a, b, ts[d], t0[d], t1[d]);
         if (na[d] == 0) return;
+        cnt[d] = 0;
+        for (int k = 0; k < na[d]; ++k) cnt[d] += t1[d][k] - t0[d][k] + 1;
     }
-    for (int pz = 0; pz < na[2]; ++pz)
-        for (int tz = t0[2][pz]; tz <= t1[2][pz]; ++tz)
-            for (int py = 0; py < na[1]; ++py)
-                for (int ty = t0[1][py]; ty <= t1[1][py]; ++ty)
-                    for (int px = 0; px < na[0]; ++px)
-                        for (int tx = t0[0][px]; tx <= t1[0][px]; ++tx) {
-                            long long t = ((long long)tz * p.ntile[1] + ty) * p.ntile[0] + tx;
-                            int slot = atomicAdd(p.tile_count + t, 1);
-                            if (slot < TILE_CAP) p.tile_list[t * TILE_CAP + slot] = i;
-                            else atomicOr(p.status, ST_TILE_OVERFLOW);
-                        }
+    const int total = cnt[0] * cnt[1] * cnt[2];
+    for (int k = lane; k < total; k += 32) {
+        int rest = k;
+        int tt[3];
+        for (int d = 0; d < 3; ++d) {
+            int m = rest % cnt[d];
+            rest /= cnt[d];
+            // the m-th tile of the axis' pieces
+            const int len0 = t1[d][0] - t0[d][0] + 1;
+            tt[d] = m < len0 ? t0[d][0] + m : t0[d][1] + (m - len0);
+        }
+        const long long t = ((long long)tt[2] * p.ntile[1] + tt[1]) * p.ntile[0] + tt[0];
+        const int slot = atomicAdd(p.tile_count + t, 1);
+        if (slot < TILE_CAP) p.tile_list[t * TILE_CAP + slot] = i;
+        else atomicOr(p.status, ST_TILE_OVERFLOW);
+    }
 }
 
 void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
     if (p.P.n == 0) return;
-    tile_scatter_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+    const long long threads = 32LL * p.P.n;
+    tile_scatter_kernel<<<(int)((threads + 127) / 128), 128, 0, st>>>(p);
 }
 
 // ------------------------------------------------------------ mapping

@@ -83,14 +83,19 @@ template <> __device__ __forceinline__ double solid_marker<double>() { return __
 // CLI value f_q(x, t+1) of the link of fluid cell (x, y, z) in pull direction
 // q into the solid cell x - c_q, and its force and torque into acc (float32
 // path: the remainder part in floats, the constant part as exact integers)
+// per-direction word of the link code: c_q + 1 in bits 0-1, 2-3, 4-5, the
+// opposite direction in bits 6-10 (read from shared memory: a warp's lanes
+// hold different directions)
+__host__ __device__ constexpr int qinfo(int q) { return (cx(q) + 1) | ((cy(q) + 1) << 2) | ((cz(q) + 1) << 4) | (opp(q) << 6); }
+
 template <typename S, typename T>
-__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, Acc<T>& acc,
+__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, int qi, Acc<T>& acc,
                                         const Sinks& sk) {
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int plane = nx * ny;
     const long long N = a.g.ncells;
-    const int c[3] = {k_c[q][0], k_c[q][1], k_c[q][2]};
-    const int p = k_opp[q];
+    const int c[3] = {(qi & 3) - 1, ((qi >> 2) & 3) - 1, ((qi >> 4) & 3) - 1};
+    const int p = (qi >> 6) & 31;
     const int cpos[3] = {x, y, z};
     int uv[3], dv[3];
     bool cli = true;
@@ -122,7 +127,7 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
     const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
     const T delta = link_fraction<T>(r, cp0, cp1, cp2, (T)cc2, R);
     const T dbc = cli ? delta : T(0.5);
-    const T inv = T(1) / (T(1) + T(2) * dbc);
+    const T inv = fast_div(T(1), T(1) + T(2) * dbc);
     const T kappa = (T(1) - T(2) * dbc) * inv;
     const T rb[3] = {r[0] + delta * cp0, r[1] + delta * cp1, r[2] + delta * cp2};
     const T ub[3] = {u[0] + (om[1] * rb[2] - om[2] * rb[1]), u[1] + (om[2] * rb[0] - om[0] * rb[2]),
@@ -267,6 +272,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_SC_MIN_BLOCKS) s
     constexpr int G = 32 / (int)sizeof(S);
     const unsigned gmask = (G >= 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
+    __shared__ int s_qi[Q];
+    if (tid < Q) {
+        constexpr int QI[Q] = {qinfo(0), qinfo(1), qinfo(2), qinfo(3), qinfo(4), qinfo(5), qinfo(6),
+                               qinfo(7), qinfo(8), qinfo(9), qinfo(10), qinfo(11), qinfo(12), qinfo(13),
+                               qinfo(14), qinfo(15), qinfo(16), qinfo(17), qinfo(18)};
+        s_qi[tid] = QI[tid];
+    }
+    __syncthreads();
     s_key[tid] = -1;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_SC_MIN_BLOCKS) s
                 if (k < total) {
                     const unsigned e = queue[k];
                     const int q = (int)(e & 31u), src = (int)(e >> 8);
-                    s_f[q][tid - lane + src] = link_value<S, T>(a, x - lane + src, y, z, q, acc, sk);
+                    s_f[q][tid - lane + src] = link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], acc, sk);
                 }
             }
             s_key[tid] = acc.key;
