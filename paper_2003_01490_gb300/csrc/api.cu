@@ -545,6 +545,7 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     if (ctx->P.n + n > ctx->max_particles) return fail(ctx, LBM_ERR_CAPACITY, "max_particles exceeded");
     const int n0 = ctx->P.n;
     std::vector<double> hx(ctx->hx), hR(ctx->hR);
+    double rmax = ctx->r_max;
     for (int k = 0; k < n; ++k) {
         const double R = radius[k], rho = density[k];
         if (!(R >= 1.0)) return fail(ctx, LBM_ERR_INVALID, "radius must be >= 1 cell");
@@ -558,23 +559,77 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
             if (ctx->g.per[a] && 2.0 * R + 4.0 >= L)
                 return fail(ctx, LBM_ERR_INVALID, "periodic side not longer than 2 R + 4 cells");
         }
-        const int m = (int)hR.size();
-        for (int j = 0; j < m; ++j) {
-            double d2 = 0;
-            for (int a = 0; a < 3; ++a) {
-                double d = pos[3 * k + a] - hx[3 * j + a];
-                if (ctx->g.per[a]) {
-                    const double L = ctx->g.n[a];
-                    if (d > 0.5 * L) d -= L;
-                    if (d < -0.5 * L) d += L;
-                }
-                d2 += d * d;
-            }
-            const double rr = R + hR[j];
-            if (d2 < rr * rr) return fail(ctx, LBM_ERR_INVALID, "spheres overlap");
+        if (R > rmax) rmax = R;
+    }
+    // overlap test on a uniform grid of buckets no smaller than 2 R_max: an
+    // overlapping pair (distance < R_i + R_j) lies in neighbouring buckets
+    {
+        int dims[3];
+        long long total = 1;
+        for (int a = 0; a < 3; ++a) {
+            dims[a] = (int)std::floor(ctx->g.n[a] / (2.0 * rmax));
+            if (dims[a] < 1) dims[a] = 1;
+            total *= dims[a];
         }
-        for (int a = 0; a < 3; ++a) hx.push_back(pos[3 * k + a]);
-        hR.push_back(R);
+        while (total > (1LL << 22)) {
+            int amax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (dims[a] > dims[amax]) amax = a;
+            total /= dims[amax];
+            dims[amax] = (dims[amax] + 1) / 2;
+            total *= dims[amax];
+        }
+        auto bucket_of = [&](const double* x, int (&b)[3]) {
+            for (int a = 0; a < 3; ++a) {
+                int v = (int)(x[a] / ctx->g.n[a] * dims[a]);
+                b[a] = v < 0 ? 0 : (v >= dims[a] ? dims[a] - 1 : v);
+            }
+        };
+        std::vector<std::vector<int>> buckets((size_t)total);
+        auto slot = [&](const int (&b)[3]) { return ((size_t)b[2] * dims[1] + b[1]) * dims[0] + b[0]; };
+        const int m0 = (int)hR.size();
+        for (int j = 0; j < m0; ++j) {
+            int b[3];
+            bucket_of(&hx[3 * j], b);
+            buckets[slot(b)].push_back(j);
+        }
+        for (int k = 0; k < n; ++k) {
+            const double R = radius[k];
+            const double* xk = pos + 3 * k;
+            int b[3];
+            bucket_of(xk, b);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int nb[3] = {b[0] + dx, b[1] + dy, b[2] + dz};
+                        bool skip = false;
+                        for (int a = 0; a < 3; ++a) {
+                            if (nb[a] < 0 || nb[a] >= dims[a]) {
+                                if (!ctx->g.per[a]) skip = true;
+                                nb[a] = (nb[a] + dims[a]) % dims[a];
+                            }
+                        }
+                        if (skip) continue;
+                        for (int j : buckets[slot(nb)]) {
+                            double d2 = 0;
+                            for (int a = 0; a < 3; ++a) {
+                                double d = xk[a] - hx[3 * j + a];
+                                if (ctx->g.per[a]) {
+                                    const double L = ctx->g.n[a];
+                                    if (d > 0.5 * L) d -= L;
+                                    if (d < -0.5 * L) d += L;
+                                }
+                                d2 += d * d;
+                            }
+                            const double rr = R + hR[j];
+                            if (d2 < rr * rr) return fail(ctx, LBM_ERR_INVALID, "spheres overlap");
+                        }
+                    }
+            const int j = (int)hR.size();
+            for (int a = 0; a < 3; ++a) hx.push_back(xk[a]);
+            hR.push_back(R);
+            buckets[slot(b)].push_back(j);
+        }
     }
     if (n == 0) {
         if (first_id_out) *first_id_out = n0;

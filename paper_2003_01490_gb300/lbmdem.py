@@ -21,6 +21,7 @@ STORAGE = {'f64': 0, 'f32': 1, 'f16': 2, 'bf16': 3}
 FLAG_SOLID, FLAG_SHELL, FLAG_NEAR, FLAG_MISS, FLAG_NEWFLUID = 0x01, 0x02, 0x04, 0x08, 0x10
 STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CUDA',
           -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -7: 'LBM_ERR_STATE'}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',

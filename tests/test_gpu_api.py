@@ -1,0 +1,82 @@
+"""Argument checks of the C ABI that need a device context (lbm_create
+allocates on the GPU): sphere insertion rules of lbm_add_spheres, capacity,
+state, and the NaN marker that solid cells show through lbm_get_pdfs."""
+import numpy as np
+import pytest
+
+from cases import build_gpu, spheres
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def L():
+    from paper_2003_01490_gb300 import lbmdem
+    lbmdem.load_library()
+    return lbmdem
+
+
+def fresh(L, shape=(40, 36, 30), periodic=(1, 1, 0), max_particles=8, storage='f32'):
+    return build_gpu(dict(shape=shape, periodic=periodic, tau=0.6, storage=storage), max_particles=max_particles)
+
+
+def add(L, ctx, pos, R):
+    sp = spheres(pos, R)
+    return L.lbm_add_spheres(ctx, sp['pos'], sp['vel'], sp['omega'], sp['radius'], sp['density'])
+
+
+def test_overlap_across_the_periodic_side_is_rejected(L):
+    ctx = fresh(L)
+    add(L, ctx, [[2.0, 18.0, 15.0]], [4.0])
+    # centre distance 2 + 40 - 35 = 7 < 8 through the periodic x side
+    with pytest.raises(L.LbmError) as e:
+        add(L, ctx, [[35.0, 18.0, 15.0]], [4.0])
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_INVALID']
+    # 8.5 apart: accepted, also within one call
+    add(L, ctx, [[33.5, 18.0, 15.0], [14.0, 18.0, 15.0]], [4.0, 4.0])
+
+
+def test_overlap_within_one_call_is_rejected(L):
+    ctx = fresh(L)
+    with pytest.raises(L.LbmError):
+        add(L, ctx, [[10.0, 10.0, 10.0], [17.9, 10.0, 10.0]], [4.0, 4.0])
+
+
+def test_wall_crossing_short_periodic_side_and_capacity(L):
+    ctx = fresh(L, max_particles=2)
+    with pytest.raises(L.LbmError):
+        add(L, ctx, [[10.0, 10.0, 2.0]], [3.0])       # crosses the z wall
+    ctx2 = fresh(L, shape=(40, 20, 30), max_particles=2)
+    with pytest.raises(L.LbmError):
+        add(L, ctx2, [[10.0, 10.0, 15.0]], [8.0])     # 2 R + 4 >= 20 on periodic y
+    add(L, ctx, [[10.0, 10.0, 10.0], [25.0, 25.0, 15.0]], [3.0, 3.0])
+    with pytest.raises(L.LbmError) as e:
+        add(L, ctx, [[30.0, 10.0, 15.0]], [3.0])
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_CAPACITY']
+
+
+def test_spheres_only_before_the_first_step(L):
+    ctx = fresh(L)
+    add(L, ctx, [[10.0, 10.0, 10.0]], [3.0])
+    L.lbm_step(ctx, 1)
+    with pytest.raises(L.LbmError) as e:
+        add(L, ctx, [[25.0, 25.0, 15.0]], [3.0])
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_STATE']
+
+
+@pytest.mark.parametrize('storage', ['f64', 'f32', 'f16', 'bf16'])
+def test_solid_cells_hold_the_marker(L, storage):
+    ctx = fresh(L, storage=storage)
+    add(L, ctx, [[12.3, 17.6, 14.9]], [5.2])
+    L.lbm_step(ctx, 3)
+    f = L.lbm_get_pdfs(ctx)
+    solid = L.lbm_get_owner(ctx) >= 0
+    assert solid.sum() > 0
+    assert np.isnan(f[:, solid]).all()
+    assert np.isfinite(f[:, ~solid]).all()
+    # values uploaded for solid cells are replaced by the marker
+    g = np.where(np.isnan(f), 0.05, f)
+    L.lbm_set_pdfs(ctx, g)
+    h = L.lbm_get_pdfs(ctx)
+    assert np.isnan(h[:, solid]).all()
+    assert np.array_equal(h[:, ~solid], g[:, ~solid])
