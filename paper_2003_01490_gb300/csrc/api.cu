@@ -56,6 +56,12 @@ struct lbm_ctx {
     int hcur = 0;
     bool stepped = false;
     long long launches = 0;
+    // captured steady-state steps, one per (PDF buffer, history buffer) parity
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t step_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long long graph_launches[2][2] = {{0, 0}, {0, 0}};   // kernel launches in each graph
+    int graph_hcur[2][2] = {{0, 0}, {0, 0}};            // history parity after each graph
+    bool graphs_off = false;
     int num_sms = 152;             // multiprocessors of the device (grid sizing)
     double ext_total[3] = {0, 0, 0};
     double r_max = 0.0;
@@ -244,6 +250,11 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
             ctx->num_sms = sms;
+        cudaError_t pe = prepare_stream_collide((int)st);
+        if (pe != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, LBM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(pe));
+        }
     }
     ctx->g.n[0] = g->nx; ctx->g.n[1] = g->ny; ctx->g.n[2] = g->nz;
     for (int a = 0; a < 3; ++a) {
@@ -397,8 +408,7 @@ MapParams map_params(lbm_ctx* ctx) {
 }
 
 // remap all particles: clear tile lists and counters, scatter, map
-lbm_status remap(lbm_ctx* ctx) {
-    cudaStream_t sm = ctx->stream;
+lbm_status remap(lbm_ctx* ctx, cudaStream_t sm) {
     // tile counts are zero here: the mapping kernel resets each one it reads
     CK(cudaMemsetAsync(ctx->n_solid, 0, 16, sm));
     MapParams mp = map_params(ctx);
@@ -675,7 +685,7 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     ctx->hR.swap(hR);
     launch_view_update(P, sm);
     ctx->launches += 1;
-    lbm_status s = remap(ctx);
+    lbm_status s = remap(ctx, ctx->stream);
     if (s != LBM_OK) return s;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(sm));
@@ -683,121 +693,183 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     return check_status(ctx);
 }
 
-lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
-    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
-    if (n_steps < 0) return fail(ctx, LBM_ERR_INVALID, "n_steps must be >= 0");
-    cudaStream_t sm = ctx->stream;
+// One time step of Algorithm 1 queued on stream sm; updates the host-side
+// state (buffer parities, launch count) as the launches are queued.
+lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     const lbm_relax& r = ctx->relax;
     const lbm_dem& d = ctx->dem;
     const double s_nu = 1.0 / r.tau;
     const bool move = ctx->P.n > 0 && !d.fixed_particles;
-    DemParams dp = dem_params(ctx);
-    for (int step = 0; step < n_steps; ++step) {
-        const bool first = !ctx->stepped;
-        if (first) {
-            ctx->stepped = true;
-            if (move) {
-                // F(t = 0) for the first Velocity-Verlet position update needs the
-                // neighbour lists of the initial positions
-                dp.hin = ctx->hcur;
-                dp.hout = 1 - ctx->hcur;
-                dp.P = ctx->P;
-                CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
-                launch_bins(dp, sm);
-                launch_neighbours(dp, sm);
-                launch_dem_subcycle(dp, 0, 1, 0, sm);
-                ctx->launches += 3;
-            }
-        }
-        // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
-        CK(prof_mark(ctx));
-        LbmStepParams lp{};
-        lp.storage = ctx->storage;
-        lp.src = ctx->f[ctx->cur];
-        lp.dst = ctx->f[1 - ctx->cur];
-        lp.flags = ctx->flags;
-        lp.owner = ctx->owner;
-        lp.g = ctx->g;
-        lp.s_plus = s_nu;
-        lp.s_minus = s_minus_of(s_nu, r.magic);
-        lp.s_b_shell = s_b_of(s_nu, r.lambda_b_shell);
-        lp.s_b_bulk = s_b_of(s_nu, r.lambda_b_bulk);
-        lp.bulk_corr = r.lambda_b_bulk != 1.0;
-        for (int a = 0; a < 3; ++a) {
-            lp.a_user[a] = ctx->a_user[a];
-            lp.ext_total[a] = ctx->ext_total[a];
-        }
-        lp.n_solid = ctx->n_solid;
-        lp.counterforce = d.fluid_counterforce && ctx->P.n > 0;
-        lp.P = ctx->P;
-        lp.missing_links = d.missing_links && ctx->P.n > 0;
-        lp.status = ctx->status;
-        lp.miss_list = ctx->miss_list;
-        lp.miss_count = ctx->miss_count;
-        lp.miss_cap = ctx->miss_cap;
-        lp.num_sms = ctx->num_sms;
-        lp.accel_d = ctx->accel;
-        lp.accel_f = ctx->accel_f;
-        launch_boundary(lp, sm);
-        CK(prof_mark(ctx));
-        launch_stream_collide(lp, sm);
-        CK(prof_mark(ctx));
-        FinalizeParams fpp{};
-        fpp.P = ctx->P;
-        fpp.use_fixed = ctx->storage != LBM_STORE_F64;
-        fpp.first_step = first;
-        fpp.averaging = d.force_averaging;
-        launch_finalize(fpp, sm);
-        ctx->launches += 2 + (ctx->P.n > 0 ? 1 : 0);
-        CK(prof_mark(ctx));
+    const bool first = !ctx->stepped;
+    if (first) {
+        ctx->stepped = true;
         if (move) {
-            // Algorithm 1, lines 4-10: DEM subcycles
+            // F(t = 0) for the first Velocity-Verlet position update needs the
+            // neighbour lists of the initial positions
+            dp.hin = ctx->hcur;
+            dp.hout = 1 - ctx->hcur;
             dp.P = ctx->P;
             CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
             launch_bins(dp, sm);
             launch_neighbours(dp, sm);
-            launch_dem_position(dp, sm);
+            launch_dem_subcycle(dp, 0, 1, 0, sm);
             ctx->launches += 3;
-            int cur = 0;
-            for (int s = 0; s < d.n_sub; ++s) {
-                dp.hin = ctx->hcur;
-                dp.hout = 1 - ctx->hcur;
-                launch_dem_subcycle(dp, cur, 0, s == d.n_sub - 1, sm);
-                ctx->hcur = 1 - ctx->hcur;
-                cur = 1 - cur;
-                ctx->launches += 1;
-            }
-            if (cur == 1) {
-                launch_state_copy(ctx->P, sm);
-                ctx->launches += 1;
-            }
-            CK(prof_mark(ctx));
-            // Algorithm 1, line 11: mapping update and refill
-            lbm_status st = remap(ctx);
-            if (st != LBM_OK) return st;
-            CK(prof_mark(ctx));
-            RefillParams rp{};
-            rp.storage = ctx->storage;
-            rp.f = ctx->f[1 - ctx->cur];
-            rp.flags = ctx->flags;
-            rp.list_owner = ctx->refill_owner;
-            rp.g = ctx->g;
-            rp.P = ctx->P;
-            rp.list = ctx->refill_list;
-            rp.count = ctx->refill_count;
-            rp.cap = ctx->refill_cap;
-            rp.s_nu = s_nu;
-            rp.accel = ctx->accel;
-            launch_refill(rp, sm);
-            ctx->launches += 1;
-            CK(prof_mark(ctx));
-        } else {
-            CK(prof_mark(ctx));
-            CK(prof_mark(ctx));
-            CK(prof_mark(ctx));
         }
-        if (ctx->profiling) ctx->prof_steps += 1;
-        ctx->cur = 1 - ctx->cur;
+    }
+    // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
+    CK(prof_mark(ctx));
+    LbmStepParams lp{};
+    lp.storage = ctx->storage;
+    lp.src = ctx->f[ctx->cur];
+    lp.dst = ctx->f[1 - ctx->cur];
+    lp.flags = ctx->flags;
+    lp.owner = ctx->owner;
+    lp.g = ctx->g;
+    lp.s_plus = s_nu;
+    lp.s_minus = s_minus_of(s_nu, r.magic);
+    lp.s_b_shell = s_b_of(s_nu, r.lambda_b_shell);
+    lp.s_b_bulk = s_b_of(s_nu, r.lambda_b_bulk);
+    lp.bulk_corr = r.lambda_b_bulk != 1.0;
+    for (int a = 0; a < 3; ++a) {
+        lp.a_user[a] = ctx->a_user[a];
+        lp.ext_total[a] = ctx->ext_total[a];
+    }
+    lp.n_solid = ctx->n_solid;
+    lp.counterforce = d.fluid_counterforce && ctx->P.n > 0;
+    lp.P = ctx->P;
+    lp.missing_links = d.missing_links && ctx->P.n > 0;
+    lp.status = ctx->status;
+    lp.miss_list = ctx->miss_list;
+    lp.miss_count = ctx->miss_count;
+    lp.miss_cap = ctx->miss_cap;
+    lp.num_sms = ctx->num_sms;
+    lp.accel_d = ctx->accel;
+    lp.accel_f = ctx->accel_f;
+    launch_boundary(lp, sm);
+    CK(prof_mark(ctx));
+    launch_stream_collide(lp, sm);
+    CK(prof_mark(ctx));
+    FinalizeParams fpp{};
+    fpp.P = ctx->P;
+    fpp.use_fixed = ctx->storage != LBM_STORE_F64;
+    fpp.first_step = first;
+    fpp.averaging = d.force_averaging;
+    launch_finalize(fpp, sm);
+    ctx->launches += 2 + (ctx->P.n > 0 ? 1 : 0);
+    CK(prof_mark(ctx));
+    if (move) {
+        // Algorithm 1, lines 4-10: DEM subcycles
+        dp.P = ctx->P;
+        CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
+        launch_bins(dp, sm);
+        launch_neighbours(dp, sm);
+        launch_dem_position(dp, sm);
+        ctx->launches += 3;
+        int cur = 0;
+        for (int s = 0; s < d.n_sub; ++s) {
+            dp.hin = ctx->hcur;
+            dp.hout = 1 - ctx->hcur;
+            launch_dem_subcycle(dp, cur, 0, s == d.n_sub - 1, sm);
+            ctx->hcur = 1 - ctx->hcur;
+            cur = 1 - cur;
+            ctx->launches += 1;
+        }
+        if (cur == 1) {
+            launch_state_copy(ctx->P, sm);
+            ctx->launches += 1;
+        }
+        CK(prof_mark(ctx));
+        // Algorithm 1, line 11: mapping update and refill
+        lbm_status st = remap(ctx, sm);
+        if (st != LBM_OK) return st;
+        CK(prof_mark(ctx));
+        RefillParams rp{};
+        rp.storage = ctx->storage;
+        rp.f = ctx->f[1 - ctx->cur];
+        rp.flags = ctx->flags;
+        rp.list_owner = ctx->refill_owner;
+        rp.g = ctx->g;
+        rp.P = ctx->P;
+        rp.list = ctx->refill_list;
+        rp.count = ctx->refill_count;
+        rp.cap = ctx->refill_cap;
+        rp.s_nu = s_nu;
+        rp.accel = ctx->accel;
+        launch_refill(rp, sm);
+        ctx->launches += 1;
+        CK(prof_mark(ctx));
+    } else {
+        CK(prof_mark(ctx));
+        CK(prof_mark(ctx));
+        CK(prof_mark(ctx));
+    }
+    if (ctx->profiling) ctx->prof_steps += 1;
+    ctx->cur = 1 - ctx->cur;
+    return LBM_OK;
+}
+
+// Steady-state steps (after the first, profiling off) run as CUDA graphs: the
+// step's ~20 launches are captured once per (PDF buffer, history buffer)
+// parity on a private stream and replayed on the context stream, which
+// removes the launch overhead that dominates small boxes.
+lbm_status graph_step(lbm_ctx* ctx, DemParams& dp, bool& done) {
+    done = false;
+    if (ctx->graphs_off) return LBM_OK;
+    const int pc = ctx->cur, ph = ctx->hcur;
+    cudaGraphExec_t& ex = ctx->step_graph[pc][ph];
+    if (!ex) {
+        if (!ctx->capture_stream &&
+            cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->graphs_off = true;
+            return LBM_OK;
+        }
+        const long long l0 = ctx->launches;
+        const int cur0 = ctx->cur, h0 = ctx->hcur;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+        lbm_status st = LBM_OK;
+        if (e == cudaSuccess) {
+            st = enqueue_step(ctx, dp, ctx->capture_stream);
+            e = cudaStreamEndCapture(ctx->capture_stream, &g);
+        }
+        // the capture ran nothing: keep its host-side updates for the replays
+        // and undo them here
+        ctx->graph_launches[pc][ph] = ctx->launches - l0;
+        ctx->graph_hcur[pc][ph] = ctx->hcur;
+        ctx->launches = l0;
+        ctx->cur = cur0;
+        ctx->hcur = h0;
+        if (e == cudaSuccess && st == LBM_OK) e = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || st != LBM_OK) {
+            cudaGetLastError();
+            ex = nullptr;
+            ctx->graphs_off = true;   // fall back to plain launches for good
+            return LBM_OK;
+        }
+    }
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    ctx->launches += ctx->graph_launches[pc][ph];
+    ctx->hcur = ctx->graph_hcur[pc][ph];
+    ctx->cur = 1 - ctx->cur;
+    done = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (n_steps < 0) return fail(ctx, LBM_ERR_INVALID, "n_steps must be >= 0");
+    DemParams dp = dem_params(ctx);
+    for (int step = 0; step < n_steps; ++step) {
+        if (ctx->stepped && !ctx->profiling) {
+            bool done = false;
+            lbm_status st = graph_step(ctx, dp, done);
+            if (st != LBM_OK) return st;
+            if (done) continue;
+        }
+        lbm_status st = enqueue_step(ctx, dp, ctx->stream);
+        if (st != LBM_OK) return st;
     }
     CK(cudaGetLastError());
     return LBM_OK;
@@ -964,6 +1036,10 @@ void lbm_destroy(lbm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ctx->step_graph[a][b]) cudaGraphExecDestroy(ctx->step_graph[a][b]);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->own_memory && ctx->base) cudaFree(ctx->base);
     delete ctx;
 }

@@ -32,6 +32,8 @@ struct LbmStepParams {
 };
 void launch_boundary(const LbmStepParams& p, cudaStream_t st);
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st);
+// kernel attributes on the current device (before any launch or capture)
+cudaError_t prepare_stream_collide(int storage);
 
 struct MapParams {
     Geom g;

@@ -39,8 +39,14 @@
 #define LBM_SC_MIN_BLOCKS 4
 #endif
 // consecutive z planes marched by one block
+// longest chunk of consecutive z planes marched by one block (shorter when
+// the box is too small to give every SM several blocks)
 #ifndef LBM_SC_ZCHUNK
 #define LBM_SC_ZCHUNK 16
+#endif
+// the same for float64 storage
+#ifndef LBM_SC_MIN_BLOCKS_F64
+#define LBM_SC_MIN_BLOCKS_F64 2
 #endif
 // cache policy: 0 default loads and stores, 1 streaming (evict-first) stores,
 // 2 streaming loads and stores
@@ -61,6 +67,7 @@ struct SCArgs {
     int bulk_corr;
     const T* __restrict__ accel;     // [3]
     int* status;
+    int zchunk;                      // z planes per block
     // particles (for the links)
     int np;
     const int* __restrict__ owner;   // particle of a solid cell, -1 for fluid
@@ -241,14 +248,14 @@ __device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], 
     for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
 }
 
-// One block per (x, y) tile of 256 cells and a chunk of LBM_SC_ZCHUNK
+// One block per (x, y) tile of 256 cells and a chunk of zchunk (<= LBM_SC_ZCHUNK)
 // consecutive z planes, marched in order: the links a warp meets in
 // consecutive rows mostly belong to the same spheres, so a lane's force sums
 // (kept in shared memory between rows) rarely change particle and the warp
 // commits them once per chunk. Cell indices are 32-bit (the library limits
 // boxes to 2^31 - 2^24 cells); each PDF array q starts at src + q N.
 template <typename S, typename T>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -288,8 +295,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_SC_MIN_BLOCKS) s
     }
     bool open = false;   // warp-uniform: some lane of the warp holds sums
 
-    const int z_begin = blockIdx.z * LBM_SC_ZCHUNK;
-    const int z_end = min(nz, z_begin + LBM_SC_ZCHUNK);
+    const int z_begin = blockIdx.z * a.zchunk;
+    const int z_end = min(nz, z_begin + a.zchunk);
     for (int z = z_begin; z < z_end; ++z) {
         const int idx = z * plane + y * nx + x;
         const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
@@ -443,11 +450,32 @@ void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
     int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
     int by = 256 / bx;
     dim3 block(bx, by, 1);
-    dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, (p.g.n[2] + LBM_SC_ZCHUNK - 1) / LBM_SC_ZCHUNK);
+    const int bxy = ((nx + bx - 1) / bx) * ((p.g.n[1] + by - 1) / by);
+    // at least 4 blocks per SM where the box allows, else shorter chunks
+    const long long want = 4LL * (p.num_sms > 0 ? p.num_sms : 152);
+    int zc = (int)((long long)bxy * p.g.n[2] / want);
+    a.zchunk = zc < 1 ? 1 : (zc > LBM_SC_ZCHUNK ? LBM_SC_ZCHUNK : zc);
+    dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, (p.g.n[2] + a.zchunk - 1) / a.zchunk);
     constexpr size_t smem = sc_smem_bytes<T>();
-    if (smem > 48 * 1024)   // float64 storage: above the default limit (set on the current device)
-        cudaFuncSetAttribute(stream_collide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     stream_collide_kernel<S, T><<<grid, block, smem, st>>>(a);
+}
+
+template <typename S>
+cudaError_t prepare_t() {
+    using T = typename Store<S>::T;
+    constexpr size_t smem = sc_smem_bytes<T>();
+    if (smem <= 48 * 1024) return cudaSuccess;
+    // float64 storage: above the default dynamic shared memory limit
+    return cudaFuncSetAttribute(stream_collide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_stream_collide(int storage) {
+    switch (storage) {
+        case 0: return prepare_t<double>();
+        case 1: return prepare_t<float>();
+        case 2: return prepare_t<__half>();
+        default: return prepare_t<__nv_bfloat16>();
+    }
 }
 
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st) {
