@@ -320,7 +320,11 @@ __device__ __forceinline__ double collision_time(double diameter, double Tc) {
 // positions of the next subcycle (Eq. (37)) into buffer 1 - cur.
 // init = 1 evaluates the initial force F(t = 0) only (no state or history
 // update). Pair terms are evaluated by both partners with mirrored operands.
-constexpr int GROUP = 4;
+// lanes per particle in the subcycle kernel (a power of two up to 32)
+#ifndef LBM_DEM_GROUP
+#define LBM_DEM_GROUP 4
+#endif
+constexpr int GROUP = LBM_DEM_GROUP;
 
 __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;

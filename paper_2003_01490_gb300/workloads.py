@@ -128,3 +128,36 @@ def reduced_suspension(storage='f32', seed=20030149):
     """64 x 64 x 128 cells at the same solid fraction (150 spheres of D = 12)."""
     return suspension(shape=(64, 64, 128), n=150, D=12.0, seed=seed, storage=storage, steps=1000)
 
+
+
+def batched(n=64, seed=20030149, storage='f32', steps_divisor=20):
+    """Many small independent boxes of the sphere-wall family (shape of
+    Sec. 4.4, scaled down): instance k draws from SplitMix64(seed + k) a side
+    s in {32, 40, ..., 96} (box s x s x 2s, no-slip walls at the z faces), a
+    sphere of D = clamp(round(s / 4), 8, 24) at (s/2, s/2, 1.5 s), a density
+    ratio log-uniform in [1.5, 10], tau log-uniform in [0.52, 0.8] and a step
+    count uniform in {2000, ..., 10000} (divided by steps_divisor). Gravity
+    follows the Schiller-Naumann balance of sphere_wall() for a settling speed
+    of 0.02."""
+    out = []
+    for k in range(n):
+        rng = SplitMix64(seed + k)
+        s = 32 + 8 * int(rng.uniform() * 9)
+        s = min(s, 96)
+        D = float(min(24, max(8, int(round(s / 4.0)))))
+        ratio = math.exp(math.log(1.5) + rng.uniform() * (math.log(10.0) - math.log(1.5)))
+        tau = math.exp(math.log(0.52) + rng.uniform() * (math.log(0.8) - math.log(0.52)))
+        steps = 2000 + int(rng.uniform() * 8001)
+        steps = max(1, steps // steps_divisor)
+        nu = (tau - 0.5) / 3.0
+        u_s = 0.02
+        Re = u_s * D / nu
+        g = 18.0 * nu * u_s * (1.0 + 0.15 * Re ** 0.687) / ((ratio - 1.0) * D * D)
+        out.append(dict(
+            name='instance %d: %dx%dx%d, D=%g, ratio %.2f, tau %.3f, %s' % (k, s, s, 2 * s, D, ratio, tau, storage),
+            shape=(s, s, 2 * s), periodic=(1, 1, 0), tau=tau, storage=storage, steps=steps,
+            pos=np.array([[s / 2.0, s / 2.0, 1.5 * s]]), vel=np.zeros((1, 3)), omega=np.zeros((1, 3)),
+            radius=np.array([D / 2]), density=np.array([ratio]),
+            dem=dict(e_dry=0.97, Tc=0.0, nu_p=0.23, mu_p=0.15, n_sub=10, gravity=(0.0, 0.0, -g)),
+            body_force=(0.0, 0.0, 0.0)))
+    return out

@@ -104,3 +104,42 @@ def test_graph_replayed_steps_equal_plain_launches(L):
     for k in ('pos', 'vel', 'omega', 'force_hyd', 'torque_hyd'):
         assert np.array_equal(sa[k], sb[k]), k
     assert L.lbm_launch_count(a) == L.lbm_launch_count(b)
+
+
+def test_concurrent_contexts_equal_each_run_alone(L):
+    """Independent contexts on their own streams (the batched mode of
+    bench.py) give exactly the results of each box run by itself."""
+    import torch
+    from paper_2003_01490_gb300 import workloads
+    inst = workloads.batched(n=3, seed=77, storage='f32', steps_divisor=200)
+
+    def make(w):
+        case = dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage=w['storage'],
+                    spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']),
+                    dem=w['dem'])
+        return build_gpu(case)
+
+    alone = []
+    for w in inst:
+        ctx = make(w)
+        L.lbm_step(ctx, w['steps'])
+        alone.append((L.lbm_get_pdfs(ctx), L.lbm_get_particle_state(ctx)))
+    streams = [torch.cuda.Stream() for _ in inst]
+    ctxs = []
+    for w, st in zip(inst, streams):
+        with torch.cuda.stream(st):
+            ctxs.append(make(w))
+    left = [w['steps'] for w in inst]
+    while any(left):
+        for k, (ctx, st) in enumerate(zip(ctxs, streams)):
+            if left[k]:
+                n = min(3, left[k])
+                with torch.cuda.stream(st):
+                    L.lbm_step(ctx, n)
+                left[k] -= n
+    torch.cuda.synchronize()
+    for (f, s), ctx in zip(alone, ctxs):
+        assert np.array_equal(L.lbm_get_pdfs(ctx), f, equal_nan=True)
+        s2 = L.lbm_get_particle_state(ctx)
+        for k in ('pos', 'vel', 'omega'):
+            assert np.array_equal(s2[k], s[k]), k
