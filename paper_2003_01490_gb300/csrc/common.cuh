@@ -102,7 +102,7 @@ struct __align__(16) PartView {
     float R;
     float u[3];
     float om[3];
-    float pad;
+    float C;               // |g|^2 - R^2 with g = 1/2 - frac (per-axis fractional offsets)
 };
 
 struct Particles {

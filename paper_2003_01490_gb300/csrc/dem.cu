@@ -55,17 +55,20 @@ __global__ void view_kernel(const Particles P) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     PartView v;
+    double gg = 0.0;
     for (int d = 0; d < 3; ++d) {
         const double x = P.x[3 * i + d];
         const double b = floor(x);
         v.base[d] = (int)b;
         v.frac[d] = (float)(x - b);
+        const double g = 0.5 - (x - b);
+        gg += g * g;
         v.u[d] = (float)P.u[3 * i + d];
         v.om[d] = (float)P.om[3 * i + d];
         P.xf[3 * i + d] = (float)x;
     }
     v.R = (float)P.R[i];
-    v.pad = 0.f;
+    v.C = (float)(gg - P.R[i] * P.R[i]);
     P.view[i] = v;
 }
 
@@ -499,6 +502,7 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     const double Fa[3] = {Fs.x, Fs.y, Fs.z};
     const double c = p.dt * cu;
     PartView v;
+    double gg = 0.0;
     for (int d = 0; d < 3; ++d) {
         // Eq. (37) for the next subcycle; the last subcycle keeps its positions
         double x = X[3 * ip + d];
@@ -509,13 +513,15 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
             const double b = floor(x);
             v.base[d] = (int)b;
             v.frac[d] = (float)(x - b);
+            const double g = 0.5 - (x - b);
+            gg += g * g;
             v.u[d] = (float)ua[d];
             v.om[d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
         }
     }
     if (last) {
         v.R = (float)P.R[ip];
-        v.pad = 0.f;
+        v.C = (float)(gg - P.R[ip] * P.R[ip]);
         P.view[ip] = v;
     }
 }

@@ -140,24 +140,32 @@ template <> struct PartOps<float> {
     template <typename A>
     __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float& R,
                                 float (&u)[3], float (&om)[3]) {
+        float g[3], C;
+        load(a, i, x, y, z, r, n, g, C, R, u, om);
+    }
+    // also the fractional offset g and C = |g|^2 - R^2 of the particle
+    template <typename A>
+    __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float (&g)[3],
+                                float& C, float& R, float (&u)[3], float (&om)[3]) {
         const PartView v = a.view[i];
         const int c[3] = {x, y, z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             int nd = c[d] - v.base[d];
-            const float g = 0.5f - v.frac[d];
+            g[d] = 0.5f - v.frac[d];
             if (a.g.per[d]) {
                 const float half = 0.5f * (float)a.g.n[d];
-                const float rd = (float)nd + g;
+                const float rd = (float)nd + g[d];
                 if (rd > half) nd -= a.g.n[d];
                 else if (rd < -half) nd += a.g.n[d];
             }
             n[d] = nd;
-            r[d] = (float)nd + g;
+            r[d] = (float)nd + g[d];
             u[d] = v.u[d];
             om[d] = v.om[d];
         }
         R = v.R;
+        C = v.C;
     }
 };
 
@@ -186,8 +194,18 @@ __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 // products and compensated sums; the root uses the cancellation-free form
 // t = 2 cc / (-b + sqrt(b^2 - 4 a cc)) of the smaller root.
 template <typename T>
-__device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T cc2, T R) {
+__device__ __forceinline__ T link_root(const T (&r)[3], T cc, T c0, T c1, T c2_, T cc2) {
     const T b = T(2) * (r[0] * c0 + r[1] * c1 + r[2] * c2_);
+    const T disc = b * b - T(4) * cc2 * cc;
+    if (disc < T(0)) return T(0.5);
+    const T sq = fast_sqrt(disc);
+    const T t = b < T(0) ? fast_div(T(2) * cc, sq - b) : fast_div(-b - sq, T(2) * cc2);
+    return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+}
+
+// |r|^2 - R^2 from exact products and compensated sums
+template <typename T>
+__device__ __forceinline__ T surface_cc(const T (&r)[3], T R) {
     T err = T(0);
     const T p0 = r[0] * r[0], p1 = r[1] * r[1], p2 = r[2] * r[2], pR = R * R;
     const T e = (fma_t<T>(r[0], r[0], -p0) + fma_t<T>(r[1], r[1], -p1)) +
@@ -195,12 +213,21 @@ __device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T
     T sum = two_sum<T>(p0, p1, err);
     sum = two_sum<T>(sum, p2, err);
     sum = two_sum<T>(sum, -pR, err);
-    const T cc = sum + (err + e);
-    const T disc = b * b - T(4) * cc2 * cc;
-    if (disc < T(0)) return T(0.5);
-    const T sq = fast_sqrt(disc);
-    const T t = b < T(0) ? fast_div(T(2) * cc, sq - b) : fast_div(-b - sq, T(2) * cc2);
-    return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+    return sum + (err + e);
+}
+
+// the same for r = n + g with integer n and the particle's common fractional
+// offset g: |n|^2 + 2 n.g + (|g|^2 - R^2), the last term precomputed per
+// particle, so no two large float32 terms cancel
+__device__ __forceinline__ float surface_cc_split(const int (&n)[3], const float (&g)[3], float C) {
+    const int nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    const float ng = fmaf((float)n[2], g[2], fmaf((float)n[1], g[1], (float)n[0] * g[0]));
+    return (float)nn + fmaf(2.0f, ng, C);
+}
+
+template <typename T>
+__device__ __forceinline__ T link_fraction(const T (&r)[3], T c0, T c1, T c2_, T cc2, T R) {
+    return link_root<T>(r, surface_cc<T>(r, R), c0, c1, c2_, cc2);
 }
 
 // lattice directions as run-time tables (for link work distributed over lanes)

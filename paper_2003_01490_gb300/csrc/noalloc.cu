@@ -50,7 +50,7 @@ __global__ void noalloc_view_kernel(int n, const double* __restrict__ pos, const
         s->xf[3 * i + d] = (float)x;
     }
     v.R = (float)radius[i];
-    v.pad = 0.f;
+    v.C = 0.f;   // unused by the mapping
     s->view[i] = v;
 }
 

@@ -127,12 +127,20 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
     }
     T r[3], R, u[3], om[3];
     int n[3];
-    PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
+    T cc;   // |r|^2 - R^2
+    if constexpr (sizeof(T) == 4) {
+        float g[3], C;
+        PartOps<T>::load(a, i, x, y, z, r, n, g, C, R, u, om);
+        cc = surface_cc_split(n, g, C);
+    } else {
+        PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
+        cc = surface_cc<T>(r, R);
+    }
     const int cp[3] = {-c[0], -c[1], -c[2]};
     const T cp0 = (T)cp[0], cp1 = (T)cp[1], cp2 = (T)cp[2];
     const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
-    const T delta = link_fraction<T>(r, cp0, cp1, cp2, (T)cc2, R);
+    const T delta = link_root<T>(r, cc, cp0, cp1, cp2, (T)cc2);
     const T dbc = cli ? delta : T(0.5);
     const T inv = fast_div(T(1), T(1) + T(2) * dbc);
     const T kappa = (T(1) - T(2) * dbc) * inv;
