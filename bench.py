@@ -35,7 +35,7 @@ def parse_args():
     ap.add_argument('--steps', type=int, default=1000)
     ap.add_argument('--warmup', type=int, default=20)
     ap.add_argument('--impl', default='ours', choices=('ours', 'reference'))
-    ap.add_argument('--workload', default='suspension', choices=('suspension', 'sphere-wall', 'batched'))
+    ap.add_argument('--workload', default='suspension', choices=('suspension', 'sphere-wall', 'batched', 'served'))
     ap.add_argument('--instances', type=int, default=64, help='batched: number of boxes')
     ap.add_argument('--steps-divisor', type=int, default=20,
                     help='batched: divide each instance step count (2000-10000) by this')
@@ -523,6 +523,38 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, rank, world, local):
+    """A seeded stream of jobs (Poisson arrivals; sphere-wall and suspension
+    cubes of 32^3 to 128^3) served with continuous batching in float16
+    storage, against the plain float32 FIFO loop on the same trace."""
+    import torch
+    from paper_2003_01490_gb300 import serve, workloads
+    jobs = workloads.served(n=args.instances if '--instances' in sys.argv else 48,
+                            seed=20030149 + 1000 * rank, storage=args.storage or 'f16',
+                            steps_divisor=args.steps_divisor if '--steps-divisor' in sys.argv else 50)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    clocks = ClockSampler(local)
+    clocks.start()
+    rec = serve.serve(jobs, budget)
+    clk = clocks.stop()
+    base_jobs = [dict(j, storage='f32') for j in jobs]
+    base = serve.fifo(base_jobs)
+    s_srv, s_fifo = serve.summary(rec), serve.summary(base)
+    line = {
+        'metric': 'MLUPS', 'value': s_srv['mlups'], 'unit': 'MLUPS', 'n_gpus': world,
+        'steps': sum(j['steps'] for j in jobs), 'warmup': 0, 'ms_per_step': None,
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': args.storage or 'f16', 'data': 'synthetic',
+        'config': {'workload': 'served: %d jobs, Poisson arrivals (mean gap 4 ms), sphere-wall and suspension '
+                               'cubes 32^3-128^3, steps 1000-20000 / 50' % len(jobs),
+                   'budget_bytes': budget, 'parallelism': 'replicas' if world > 1 else 'single GPU'},
+        'served': s_srv, 'fifo_f32': s_fifo, 'clocks': clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.cpu_sample:
@@ -538,6 +570,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.workload == 'batched':
         run_batched(args, rank, world, local)
+    elif args.workload == 'served':
+        run_served(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

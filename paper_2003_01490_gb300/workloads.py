@@ -161,3 +161,48 @@ def batched(n=64, seed=20030149, storage='f32', steps_divisor=20):
             dem=dict(e_dry=0.97, Tc=0.0, nu_p=0.23, mu_p=0.15, n_sub=10, gravity=(0.0, 0.0, -g)),
             body_force=(0.0, 0.0, 0.0)))
     return out
+
+
+def served(n=48, seed=20030149, storage='f16', steps_divisor=50, max_side=128, gap=0.004):
+    """A seeded stream of independent jobs for the served mode: Poisson
+    arrivals with mean gap `gap` seconds; half are sphere-wall jobs (one
+    sphere, no-slip walls at the z faces), half periodic suspensions (random
+    sequential addition). Every job is a cube s^3 with s in {32, 48, ...,
+    max_side}; sphere diameters are uniform in [8, 16] (one per job);
+    suspensions hold up to 2000 spheres, capped at 27 % solids; step counts
+    are log-uniform in [1000, 20000], divided by steps_divisor."""
+    rng = SplitMix64(seed)
+    jobs = []
+    t = 0.0
+    sides = list(range(32, max_side + 1, 16))
+    for k in range(n):
+        t += -gap * math.log(1.0 - rng.uniform())
+        s = sides[min(len(sides) - 1, int(rng.uniform() * len(sides)))]
+        D = 8.0 + 8.0 * rng.uniform()
+        steps = int(round(math.exp(math.log(1000.0) + rng.uniform() * (math.log(20000.0) - math.log(1000.0)))))
+        steps = max(1, steps // steps_divisor)
+        tau = 0.6
+        nu = (tau - 0.5) / 3.0
+        if rng.uniform() < 0.5:
+            ratio = 4.0
+            u_s = 0.02
+            Re = u_s * D / nu
+            g = 18.0 * nu * u_s * (1.0 + 0.15 * Re ** 0.687) / ((ratio - 1.0) * D * D)
+            job = dict(name='job %d: sphere-wall %d^3, D=%.1f' % (k, s, D), shape=(s, s, s), periodic=(1, 1, 0),
+                       pos=np.array([[s / 2.0, s / 2.0, 0.75 * s]]), vel=np.zeros((1, 3)), omega=np.zeros((1, 3)),
+                       radius=np.array([D / 2]), density=np.array([ratio]),
+                       dem=dict(e_dry=0.97, Tc=0.0, nu_p=0.23, mu_p=0.15, n_sub=10, gravity=(0.0, 0.0, -g)))
+        else:
+            cap = int(0.27 * s ** 3 / (math.pi * D ** 3 / 6.0))
+            m = min(int(rng.uniform() * 2001), cap)
+            pos = random_sequential_addition((s, s, s), m, D, rng) if m else np.zeros((0, 3))
+            ratio = 2.5
+            g = 0.005 * 18.0 * nu / ((ratio - 1.0) * D * D)
+            job = dict(name='job %d: suspension %d^3, %d spheres D=%.1f' % (k, s, m, D), shape=(s, s, s),
+                       periodic=(1, 1, 1), pos=pos, vel=np.zeros((m, 3)), omega=np.zeros((m, 3)),
+                       radius=np.full(m, D / 2), density=np.full(m, ratio),
+                       dem=dict(e_dry=0.97, Tc=0.0, nu_p=0.23, mu_p=0.15, n_sub=10, gravity=(0.0, 0.0, -g),
+                                fluid_counterforce=1))
+        job.update(tau=tau, storage=storage, steps=steps, arrival=t, body_force=(0.0, 0.0, 0.0))
+        jobs.append(job)
+    return jobs

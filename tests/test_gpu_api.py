@@ -143,3 +143,17 @@ def test_concurrent_contexts_equal_each_run_alone(L):
         s2 = L.lbm_get_particle_state(ctx)
         for k in ('pos', 'vel', 'omega'):
             assert np.array_equal(s2[k], s[k]), k
+
+
+def test_served_jobs_equal_each_run_alone(L):
+    """Continuous batching (jobs admitted over time, advanced in rounds on
+    their own streams) leaves every job's result exactly as if it ran alone."""
+    from paper_2003_01490_gb300 import serve, workloads
+    jobs = workloads.served(n=4, seed=5, storage='f16', steps_divisor=400, max_side=48, gap=0.001)
+    mixed = serve.serve(jobs, budget_bytes=1 << 34, chunk=3, keep_state=True)
+    alone = serve.fifo(jobs, keep_state=True)
+    for a, b in zip(mixed, alone):
+        for k in ('pos', 'vel', 'omega'):
+            assert np.array_equal(a['state'][k], b['state'][k]), (a['name'], k)
+    summ = serve.summary(mixed)
+    assert summ['jobs'] == 4 and summ['p99_latency_s'] >= summ['p50_latency_s'] > 0
