@@ -1,0 +1,80 @@
+"""Precision form over a long run: float64, float32 and shifted float16 /
+bfloat16 PDF storage against the float64 oracle's trajectory of a 32 x 32 x 64
+periodic suspension (19 spheres of D = 12) at steps 100, 250, 500 and 1000,
+stored in tests/golden/suspension_32x32x64_trajectory.txt by
+tests/golden/make_precision_trajectory.py (oracle only). Reported per
+format: RMS particle position error / D, relative L2 error of the particle
+velocities, and the relative errors of the fluid's mean and RMS velocity and
+RMS density deviation. The bounds sit an order of magnitude above the errors
+measured on GB300 when the test was written; the printed values are the
+report."""
+import os
+
+import numpy as np
+import pytest
+
+from cases import build_gpu, spheres
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, 'golden', 'suspension_32x32x64_trajectory.txt')
+
+
+def load_golden():
+    out = {}
+    step = None
+    for line in open(GOLDEN):
+        if line.startswith('#') or not line.strip():
+            continue
+        if line.startswith('step'):
+            step = int(line.split()[1])
+            out[step] = {'rows': [], 'fields': None}
+        elif line.startswith('fields'):
+            out[step]['fields'] = np.array([float(v) for v in line.split()[1:]])
+        else:
+            out[step]['rows'].append([float(v) for v in line.split()])
+    for v in out.values():
+        v['rows'] = np.array(v['rows'])
+    return out
+
+
+def case(storage):
+    from paper_2003_01490_gb300 import workloads
+    w = workloads.suspension(shape=(32, 32, 64), n=19, D=12.0, seed=20030149, storage=storage, steps=1000)
+    return dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage=storage,
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']), dem=w['dem'])
+
+
+# bound on (RMS position error / D, velocity rel L2, field statistics rel error) at step 1000
+BOUNDS = {'f64': (1e-8, 1e-6, 1e-6), 'f32': (1e-4, 1e-2, 1e-2), 'f16': (1e-2, 0.5, 0.2), 'bf16': (5e-2, 1.0, 0.5)}
+
+
+@pytest.mark.parametrize('storage', ['f64', 'f32', 'f16', 'bf16'])
+def test_long_run_error_against_the_oracle(storage):
+    from paper_2003_01490_gb300 import lbmdem as L
+    gold = load_golden()
+    ctx = build_gpu(case(storage))
+    done = 0
+    D = 12.0
+    for step in sorted(gold):
+        L.lbm_step(ctx, step - done)
+        done = step
+        st = L.lbm_get_particle_state(ctx)
+        ref = gold[step]['rows']
+        dx = st['pos'] - ref[:, :3]
+        dx -= np.array([32.0, 32.0, 64.0]) * np.round(dx / np.array([32.0, 32.0, 64.0]))   # periodic images
+        e_x = np.sqrt((dx ** 2).sum(1).mean()) / D
+        e_u = np.linalg.norm(st['vel'] - ref[:, 3:]) / np.linalg.norm(ref[:, 3:])
+        rho, u, flags = L.lbm_get_fields(ctx)
+        fluid = (flags & L.FLAG_SOLID) == 0
+        uf = u[:, fluid]
+        stats = np.array([uf[0].mean(), uf[1].mean(), uf[2].mean(), np.sqrt((uf ** 2).sum(0).mean()),
+                          np.sqrt(((rho[fluid] - 1.0) ** 2).mean())])
+        gs = gold[step]['fields']
+        e_f = np.abs(stats[3:] - gs[3:]) / np.abs(gs[3:])
+        e_mean = np.linalg.norm(stats[:3] - gs[:3]) / np.linalg.norm(gs[:3])
+        print('%s step %4d: position/D %.3e, velocity %.3e, mean u %.3e, rms u %.3e, rms rho-1 %.3e'
+              % (storage, step, e_x, e_u, e_mean, e_f[0], e_f[1]))
+    bx, bu, bf = BOUNDS[storage]
+    assert e_x < bx and e_u < bu and max(e_f.max(), e_mean) < bf
