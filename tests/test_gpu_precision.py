@@ -47,7 +47,7 @@ def case(storage):
 
 
 # bound on (RMS position error / D, velocity rel L2, field statistics rel error) at step 1000
-BOUNDS = {'f64': (1e-8, 1e-6, 1e-6), 'f32': (1e-4, 1e-2, 1e-2), 'f16': (1e-2, 0.5, 0.2), 'bf16': (5e-2, 1.0, 0.5)}
+BOUNDS = {'f64': (1e-10, 1e-9, 1e-7), 'f32': (1e-6, 1e-5, 1e-4), 'f16': (1e-4, 5e-3, 5e-3), 'bf16': (1e-3, 0.1, 0.2)}
 
 
 @pytest.mark.parametrize('storage', ['f64', 'f32', 'f16', 'bf16'])
