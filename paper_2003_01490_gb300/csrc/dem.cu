@@ -147,9 +147,14 @@ void launch_bins(const DemParams& p, cudaStream_t st) {
     bin_fill_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
 }
 
+// one warp per particle: lane k tests entry k of each of the 27 bins around it
+// (a bin holds at most BIN_CAP = 32 particles); hits are appended in bin order
 __global__ void neighbour_kernel(const DemParams p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.P.n) return;
+    static_assert(BIN_CAP == 32, "one lane per bin entry");
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= p.P.n) return;   // warp-uniform
+    const unsigned FULL = 0xffffffffu;
     const float xi[3] = {p.P.xf[3 * i], p.P.xf[3 * i + 1], p.P.xf[3 * i + 2]};
     const float Ri = (float)p.P.R[i];
     const float extra = (float)(p.cut_max + NBR_SKIN) + 0.01f;
@@ -169,31 +174,40 @@ __global__ void neighbour_kernel(const DemParams p) {
                 const int wz = (p.nbins[2] >= 3) ? wrap_idx(bz, p.nbins[2]) : bz;
                 const long long bi = ((long long)wz * p.nbins[1] + wy) * p.nbins[0] + wx;
                 const int nb = min(p.P.bin_count[bi], BIN_CAP);
-                for (int k = 0; k < nb; ++k) {
-                    const int j = p.P.bin_list[bi * BIN_CAP + k];
-                    if (j == i) continue;
-                    float d2 = 0.f;
-                    for (int d = 0; d < 3; ++d) {
-                        const float dd = mimgf(xi[d] - p.P.xf[3 * j + d], p.g.n[d], p.g.per[d]);
-                        d2 += dd * dd;
-                    }
-                    const float reach = Ri + (float)p.P.R[j] + extra;
-                    if (d2 < reach * reach) {
-                        if (cnt < NBR_CAP) p.P.nbr[i * NBR_CAP + cnt] = j;
-                        ++cnt;
+                bool hit = false;
+                int j = -1;
+                if (lane < nb) {
+                    j = p.P.bin_list[bi * BIN_CAP + lane];
+                    if (j != i) {
+                        float d2 = 0.f;
+                        for (int d = 0; d < 3; ++d) {
+                            const float dd = mimgf(xi[d] - p.P.xf[3 * j + d], p.g.n[d], p.g.per[d]);
+                            d2 += dd * dd;
+                        }
+                        const float reach = Ri + (float)p.P.R[j] + extra;
+                        hit = d2 < reach * reach;
                     }
                 }
+                const unsigned m = __ballot_sync(FULL, hit);
+                if (hit) {
+                    const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (slot < NBR_CAP) p.P.nbr[i * NBR_CAP + slot] = j;
+                }
+                cnt += __popc(m);
             }
-    if (cnt > NBR_CAP) {
-        atomicOr(p.status, ST_NBR_OVERFLOW);
-        cnt = NBR_CAP;
+    if (lane == 0) {
+        if (cnt > NBR_CAP) {
+            atomicOr(p.status, ST_NBR_OVERFLOW);
+            cnt = NBR_CAP;
+        }
+        p.P.nbr_count[i] = cnt;
     }
-    p.P.nbr_count[i] = cnt;
 }
 
 void launch_neighbours(const DemParams& p, cudaStream_t st) {
     if (p.P.n == 0) return;
-    neighbour_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
+    const long long threads = 32LL * p.P.n;
+    neighbour_kernel<<<(int)((threads + 127) / 128), 128, 0, st>>>(p);
 }
 
 // ------------------------------------------------------------ Velocity Verlet
@@ -315,172 +329,224 @@ __device__ __forceinline__ double collision_time(double diameter, double Tc) {
     return Tc > 0.0 ? Tc : 2.31 * diameter * 1.7320508075688772;
 }
 
-// One Velocity-Verlet subcycle (Algorithm 1, inner loop), 4 lanes per particle.
-// Reads the state of buffer `cur` (x, u, omega at the subcycle's positions),
-// evaluates lubrication (Eqs. (25)-(33)), contact (Eqs. (39)-(50)), the
-// averaged fluid force and V (rho_p - rho_f) g, then (lane 0 of the group)
-// updates the velocities (Eq. (38)) and, unless it is the last subcycle, the
-// positions of the next subcycle (Eq. (37)) into buffer 1 - cur.
-// init = 1 evaluates the initial force F(t = 0) only (no state or history
-// update). Pair terms are evaluated by both partners with mirrored operands.
-// lanes per particle in the subcycle kernel (a power of two up to 32)
-#ifndef LBM_DEM_GROUP
-#define LBM_DEM_GROUP 4
-#endif
-constexpr int GROUP = LBM_DEM_GROUP;
-
-__global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gid / GROUP;
-    const int sub = gid % GROUP;
-    const bool act = i < p.P.n;
+// Force and torque on particle i from its neighbour j (lubrication,
+// Eqs. (25)-(33), and contact, Eqs. (39)-(50)) at the subcycle's positions;
+// contact = the spring of the pair continues, dnew its new value.
+__device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, int j, V3& F, V3& T, bool& contact,
+                                           V3& dnew) {
     const Particles& P = p.P;
     const double* X = P.xs[cur];
     const double* Uv = P.us[cur];
     const double* Om = P.oms[cur];
+    const V3 xi = ld3(X, i), xj = ld3(X, j);
+    const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
+                    mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
+    const double dist = sqrt(dot(d, d));
+    const double Ri = P.R[i], Rj = P.R[j];
+    const double delta = dist - (Ri + Rj);
+    F = mk(0, 0, 0);
+    T = mk(0, 0, 0);
+    contact = false;
+    dnew = mk(0, 0, 0);
+    if (delta >= p.cut_max && delta >= 0.0) return;
+    const V3 n = (1.0 / dist) * d;
+    const V3 ui = ld3(Uv, i), omi = ld3(Om, i), uj = ld3(Uv, j), omj = ld3(Om, j);
+    const V3 uij = ui - uj;
+    if (p.lubrication) {
+        const double Rm = 0.5 * (Ri + Rj);
+        const double dmin = (p.min_a + p.min_b * Rm) * Rm;
+        lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
+    }
+    if (delta < 0.0) {
+        const V3 ri = (-0.5) * d, rj = 0.5 * d;
+        const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
+        const double mi = P.m[i], mj = P.m[j];
+        const double m_eff = mi * mj / (mi + mj);
+        const double Tc = collision_time(Ri + Rj, p.Tc);
+        V3 old = mk(0, 0, 0);
+        const int nin = P.hist_n[p.hin][i];
+        for (int h = 0; h < nin; ++h)
+            if (P.hist_id[p.hin][i * NBR_CAP + h] == j) {
+                const double* s = P.hist_d[p.hin] + 3 * (i * NBR_CAP + h);
+                old = mk(s[0], s[1], s[2]);
+                break;
+            }
+        V3 Fn, Ft;
+        contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
+        F = F + (Fn + Ft);
+        T = T + cross(ri, Ft);
+        contact = true;
+    }
+}
+
+// One Velocity-Verlet subcycle (Algorithm 1, inner loop) for 32 particles per
+// block of 128 threads. Pass 1, four lanes per particle: a float32 prefilter
+// of the neighbour slots (float positions are within 1e-4 of the float64
+// ones, so a gap above cut_max + 1e-3 there is above cut_max exactly); the
+// surviving (particle, slot) pairs are queued in shared memory in particle
+// and slot order. Pass 2: all 128 threads evaluate the queued pairs in
+// float64 (lubrication, Eqs. (25)-(33); contact, Eqs. (39)-(50)), so the
+// slow float64 units see full warps; each particle then sums its pairs in
+// slot order (the result does not depend on scheduling). Pass 3, one thread
+// per particle: plane walls, the averaged fluid force and V (rho_p - rho_f) g,
+// then the velocities (Eq. (38)) and, unless it is the last subcycle, the
+// positions of the next subcycle (Eq. (37)) into buffer 1 - cur.
+// init = 1 evaluates the initial force F(t = 0) only (no state or history
+// update). Pair terms are evaluated by both partners with mirrored operands.
+constexpr int PPB = 32;          // particles per block
+constexpr int PAIR_CHUNK = 128;  // queued pairs evaluated per pass of the block
+
+__global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
+    const Particles& P = p.P;
+    const int tid = threadIdx.x;
+    const int pl = tid >> 2, sub = tid & 3;   // pass 1: particle of the block, lane of its group
+    const int i = blockIdx.x * PPB + pl;
+    const int hout = p.hout;
+    __shared__ unsigned short s_queue[PPB * NBR_CAP];   // pl << 5 | slot
+    __shared__ int s_off[PPB + 1];
+    __shared__ double s_res[PAIR_CHUNK][6];
+    __shared__ double s_sum[PPB][6];
     const float* Xf = P.xfs[cur];
-    V3 F = mk(0, 0, 0), T = mk(0, 0, 0);
-    const int hin = p.hin, hout = p.hout;
-    if (act) {
-        const V3 xi = ld3(X, i), ui = ld3(Uv, i), omi = ld3(Om, i);
-        const double Ri = P.R[i], mi = P.m[i];
+    const unsigned FULL = 0xffffffffu;
+
+    // pass 1: candidate slots of particle pl (bit k = slot k)
+    unsigned mask = 0;
+    int nn = 0;
+    if (i < P.n) {
+        nn = P.nbr_count[i];
         const float xif[3] = {Xf[3 * i], Xf[3 * i + 1], Xf[3 * i + 2]};
+        const float Rif = (float)P.R[i];
         const float reach_pad = (float)p.cut_max + 1e-3f;
-        const int nn = P.nbr_count[i];
-        const int nin = P.hist_n[hin][i];
-        for (int k = sub; k < nn; k += GROUP) {
+        for (int k = sub; k < nn; k += 4) {
             const int j = P.nbr[i * NBR_CAP + k];
-            bool contact = false;
-            V3 dnew = mk(0, 0, 0);
-            // float32 prefilter: float positions are within 1e-4 of the float64
-            // ones, so a gap above cut_max + 1e-3 here is above cut_max exactly
             float d2f = 0.f;
             for (int d = 0; d < 3; ++d) {
                 const float dd = mimgf(xif[d] - Xf[3 * j + d], p.g.n[d], p.g.per[d]);
                 d2f += dd * dd;
             }
-            const float reach = (float)Ri + (float)P.R[j] + reach_pad;
-            if (d2f < reach * reach) {
-                const V3 xj = ld3(X, j);
-                const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
-                                mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
-                const double dist = sqrt(dot(d, d));
-                const double Rj = P.R[j];
-                const double delta = dist - (Ri + Rj);
-                if (!(delta >= p.cut_max && delta >= 0.0)) {
-                    const V3 n = (1.0 / dist) * d;
-                    const V3 uj = ld3(Uv, j), omj = ld3(Om, j);
-                    const V3 uij = ui - uj;
-                    if (p.lubrication) {
-                        const double Rm = 0.5 * (Ri + Rj);
-                        const double dmin = (p.min_a + p.min_b * Rm) * Rm;
-                        lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
-                    }
-                    if (delta < 0.0) {
-                        const V3 ri = (-0.5) * d, rj = 0.5 * d;
-                        const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
-                        const double mj = P.m[j];
-                        const double m_eff = mi * mj / (mi + mj);
-                        const double Tc = collision_time(Ri + Rj, p.Tc);
-                        V3 old = mk(0, 0, 0);
-                        for (int h = 0; h < nin; ++h)
-                            if (P.hist_id[hin][i * NBR_CAP + h] == j) {
-                                const double* s = P.hist_d[hin] + 3 * (i * NBR_CAP + h);
-                                old = mk(s[0], s[1], s[2]);
-                                break;
-                            }
-                        V3 Fn, Ft;
-                        contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
-                        F = F + (Fn + Ft);
-                        T = T + cross(ri, Ft);
-                        contact = true;
-                    }
-                }
-            }
-            if (!init) {
-                // tangential spring of this neighbour slot for the next subcycle
-                P.hist_id[hout][i * NBR_CAP + k] = contact ? j : -1;
-                if (contact) {
-                    double* s = P.hist_d[hout] + 3 * (i * NBR_CAP + k);
-                    s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
-                }
-            }
-        }
-        if (sub == 0) {
-            // plane walls on the faces of non-periodic axes
-            const double xa[3] = {xi.x, xi.y, xi.z};
-            for (int a = 0; a < 3; ++a) {
-                if (p.g.per[a]) continue;
-                for (int side = 0; side < 2; ++side) {
-                    const int face = 2 * a + side;
-                    V3 nw = mk(0, 0, 0);
-                    const double sgn = side == 0 ? 1.0 : -1.0;
-                    if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
-                    const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
-                    const double delta = (xa[a] - xw) * sgn - Ri;
-                    const double* uwp = p.g.wall_vel[side][a];
-                    const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
-                    const V3 uij = ui - uw;
-                    if (p.lubrication) {
-                        const double dmin = (p.min_a + p.min_b * Ri) * Ri;
-                        lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
-                    }
-                    if (!init) P.wact[hout][6 * i + face] = 0;
-                    if (delta < 0.0) {
-                        const V3 ri = (-(Ri + 0.5 * delta)) * nw;
-                        const V3 ucp = (ui + cross(omi, ri)) - uw;
-                        const double Tc = collision_time(2.0 * Ri, p.Tc);
-                        V3 old = mk(0, 0, 0);
-                        if (P.wact[hin][6 * i + face]) {
-                            const double* s = P.whist[hin] + 3 * (6 * i + face);
-                            old = mk(s[0], s[1], s[2]);
-                        }
-                        V3 Fn, Ft, dnew;
-                        contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
-                        F = F + (Fn + Ft);
-                        T = T + cross(ri, Ft);
-                        if (!init) {
-                            double* s = P.whist[hout] + 3 * (6 * i + face);
-                            s[0] = dnew.x; s[1] = dnew.y; s[2] = dnew.z;
-                            P.wact[hout][6 * i + face] = 1;
-                        }
-                    }
-                }
-            }
+            const float reach = Rif + (float)P.R[j] + reach_pad;
+            if (d2f < reach * reach) mask |= 1u << k;
+            else if (!init) P.hist_id[hout][i * NBR_CAP + k] = -1;   // no spring on this slot
         }
     }
-    // sum the four lanes of a particle, in warps where any lane interacted
-    const unsigned FULL = 0xffffffffu;
-    const bool hit = F.x != 0.0 || F.y != 0.0 || F.z != 0.0 || T.x != 0.0 || T.y != 0.0 || T.z != 0.0;
-    if (__ballot_sync(FULL, hit)) {
+    mask |= __shfl_xor_sync(FULL, mask, 1);
+    mask |= __shfl_xor_sync(FULL, mask, 2);
+    if (sub == 0) s_off[pl] = __popc(mask);
+    if (tid < 6 * PPB) reinterpret_cast<double*>(s_sum)[tid] = 0.0;
+    if (tid + 128 < 6 * PPB) reinterpret_cast<double*>(s_sum)[tid + 128] = 0.0;
+    __syncthreads();
+    if (tid < 32) {   // exclusive prefix over the 32 particles
+        const int c = s_off[tid];
+        int incl = c;
 #pragma unroll
-        for (int o = 1; o < GROUP; o <<= 1) {
-            F.x += __shfl_xor_sync(FULL, F.x, o);
-            F.y += __shfl_xor_sync(FULL, F.y, o);
-            F.z += __shfl_xor_sync(FULL, F.z, o);
-            T.x += __shfl_xor_sync(FULL, T.x, o);
-            T.y += __shfl_xor_sync(FULL, T.y, o);
-            T.z += __shfl_xor_sync(FULL, T.z, o);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (tid >= o) incl += v;
         }
-    }
-    // hand the sums to one lane per particle (warp 0 of the block), so the
-    // float64 integration runs with every lane of the warp busy
-    constexpr int PPB = 128 / GROUP;   // particles per block
-    __shared__ double sFT[PPB][6];
-    const int local = threadIdx.x / GROUP;
-    if (sub == 0) {
-        sFT[local][0] = F.x; sFT[local][1] = F.y; sFT[local][2] = F.z;
-        sFT[local][3] = T.x; sFT[local][4] = T.y; sFT[local][5] = T.z;
+        s_off[tid] = incl - c;
+        if (tid == 31) s_off[PPB] = incl;
     }
     __syncthreads();
-    if (threadIdx.x >= PPB) return;
-    const int ip = blockIdx.x * PPB + threadIdx.x;
+    {
+        // the group's lanes write the queue entries of their particle, in slot order
+        unsigned m = mask;
+        int r = 0;
+        const int base = s_off[pl];
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            if ((r & 3) == sub) s_queue[base + r] = (unsigned short)((pl << 5) | k);
+            ++r;
+        }
+    }
+    __syncthreads();
+    // pass 2: the queued pairs in chunks of 128, one per thread
+    const int total = s_off[PPB];
+    for (int c0 = 0; c0 < total; c0 += PAIR_CHUNK) {
+        const int e = c0 + tid;
+        if (e < total) {
+            const int q = s_queue[e];
+            const int ep = q >> 5, k = q & 31;
+            const int ei = blockIdx.x * PPB + ep;
+            const int j = P.nbr[ei * NBR_CAP + k];
+            V3 F, T, dnew;
+            bool contact;
+            pair_force(p, cur, ei, j, F, T, contact, dnew);
+            s_res[tid][0] = F.x; s_res[tid][1] = F.y; s_res[tid][2] = F.z;
+            s_res[tid][3] = T.x; s_res[tid][4] = T.y; s_res[tid][5] = T.z;
+            if (!init) {
+                // tangential spring of this neighbour slot for the next subcycle
+                P.hist_id[hout][ei * NBR_CAP + k] = contact ? j : -1;
+                if (contact) {
+                    double* sd = P.hist_d[hout] + 3 * (ei * NBR_CAP + k);
+                    sd[0] = dnew.x; sd[1] = dnew.y; sd[2] = dnew.z;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < PPB) {   // particle tid adds its pairs of this chunk in slot order
+            const int lo = max(s_off[tid], c0), hi = min(s_off[tid + 1], c0 + PAIR_CHUNK);
+            for (int e2 = lo; e2 < hi; ++e2)
+                for (int c = 0; c < 6; ++c) s_sum[tid][c] += s_res[e2 - c0][c];
+        }
+        __syncthreads();
+    }
+    // pass 3: one thread per particle
+    if (tid >= PPB) return;
+    const int ip = blockIdx.x * PPB + tid;
     if (ip >= P.n) return;
-    const V3 Fs = mk(sFT[threadIdx.x][0] + P.fbar[6 * ip] + P.ext[3 * ip],
-                     sFT[threadIdx.x][1] + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
-                     sFT[threadIdx.x][2] + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
-    const V3 Ts = mk(sFT[threadIdx.x][3] + P.fbar[6 * ip + 3], sFT[threadIdx.x][4] + P.fbar[6 * ip + 4],
-                     sFT[threadIdx.x][5] + P.fbar[6 * ip + 5]);
+    const double* X = P.xs[cur];
+    const double* Uv = P.us[cur];
+    const double* Om = P.oms[cur];
+    V3 F = mk(s_sum[tid][0], s_sum[tid][1], s_sum[tid][2]);
+    V3 T = mk(s_sum[tid][3], s_sum[tid][4], s_sum[tid][5]);
+    {
+        // plane walls on the faces of non-periodic axes
+        const V3 xi = ld3(X, ip), ui = ld3(Uv, ip), omi = ld3(Om, ip);
+        const double Ri = P.R[ip], mi = P.m[ip];
+        const double xa[3] = {xi.x, xi.y, xi.z};
+        for (int a = 0; a < 3; ++a) {
+            if (p.g.per[a]) continue;
+            for (int side = 0; side < 2; ++side) {
+                const int face = 2 * a + side;
+                V3 nw = mk(0, 0, 0);
+                const double sgn = side == 0 ? 1.0 : -1.0;
+                if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
+                const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
+                const double delta = (xa[a] - xw) * sgn - Ri;
+                const double* uwp = p.g.wall_vel[side][a];
+                const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
+                const V3 uij = ui - uw;
+                if (p.lubrication) {
+                    const double dmin = (p.min_a + p.min_b * Ri) * Ri;
+                    lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
+                }
+                if (!init) P.wact[hout][6 * ip + face] = 0;
+                if (delta < 0.0) {
+                    const V3 ri = (-(Ri + 0.5 * delta)) * nw;
+                    const V3 ucp = (ui + cross(omi, ri)) - uw;
+                    const double Tc = collision_time(2.0 * Ri, p.Tc);
+                    V3 old = mk(0, 0, 0);
+                    if (P.wact[p.hin][6 * ip + face]) {
+                        const double* sd = P.whist[p.hin] + 3 * (6 * ip + face);
+                        old = mk(sd[0], sd[1], sd[2]);
+                    }
+                    V3 Fn, Ft, dnew;
+                    contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
+                    F = F + (Fn + Ft);
+                    T = T + cross(ri, Ft);
+                    if (!init) {
+                        double* sd = P.whist[hout] + 3 * (6 * ip + face);
+                        sd[0] = dnew.x; sd[1] = dnew.y; sd[2] = dnew.z;
+                        P.wact[hout][6 * ip + face] = 1;
+                    }
+                }
+            }
+        }
+    }
+    const V3 Fs = mk(F.x + P.fbar[6 * ip] + P.ext[3 * ip], F.y + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
+                     F.z + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
+    const V3 Ts = mk(T.x + P.fbar[6 * ip + 3], T.y + P.fbar[6 * ip + 4], T.z + P.fbar[6 * ip + 5]);
     if (init) {
         st3(P.F_prev, ip, Fs);
         st3(P.T_prev, ip, Ts);
@@ -528,9 +594,7 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
 
 void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st) {
     if (p.P.n == 0) return;
-    const int threads = 128;
-    const long long total = (long long)p.P.n * GROUP;
-    subcycle_kernel<<<(int)((total + threads - 1) / threads), threads, 0, st>>>(p, cur, init, last);
+    subcycle_kernel<<<(p.P.n + PPB - 1) / PPB, 128, 0, st>>>(p, cur, init, last);
 }
 
 // copy state buffer 1 into buffer 0 (after an odd number of subcycles)
