@@ -42,6 +42,16 @@ __host__ __device__ constexpr T wq(int q) {
     return c2(q) == 0 ? T(1) / T(3) : (c2(q) == 1 ? T(1) / T(18) : T(1) / T(36));
 }
 
+// lattice direction components as 2-bit fields (c + 1) of one word per axis,
+// for directions chosen at run time (one per lane)
+__host__ __device__ constexpr unsigned long long pack_dirs(int axis) {
+    unsigned long long v = 0;
+    for (int q = 0; q < Q; ++q)
+        v |= (unsigned long long)((axis == 0 ? cx(q) : axis == 1 ? cy(q) : cz(q)) + 1) << (2 * q);
+    return v;
+}
+__device__ __forceinline__ int dir_c(unsigned long long packed, int q) { return (int)((packed >> (2 * q)) & 3ull) - 1; }
+
 // flag bits (mirrors LBM_FLAG_* of the public header)
 constexpr uint8_t FL_SOLID = 0x01, FL_SHELL = 0x02, FL_NEAR = 0x04, FL_MISS = 0x08,
                   FL_NEWFLUID = 0x10;

@@ -397,57 +397,74 @@ void launch_solid_markers(const MapParams& p, cudaStream_t st) {
 
 // ------------------------------------------------------------ refill
 
+// One warp per uncovered cell: lane q (1..18) reads the neighbour x + c_q
+// (its 19 PDFs, when it was fluid before and after the update), the warp sums
+// densities and shares the axis neighbours' velocities, and lane q (0..18)
+// writes f_q of Eq. (18).
 template <typename S>
-__global__ void refill_kernel(const RefillParams p) {
+__global__ void __launch_bounds__(128) refill_kernel(const RefillParams p) {
     using T = typename Store<S>::T;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int count = min(*p.count, p.cap);
     const S* f = static_cast<const S*>(p.f);
     S* fw = static_cast<S*>(p.f);
     const long long N = p.g.ncells;
     const int nx = p.g.n[0], ny = p.g.n[1];
     const T ax = (T)p.accel[0], ay = (T)p.accel[1], az = (T)p.accel[2];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    constexpr unsigned long long PX = pack_dirs(0), PY = pack_dirs(1), PZ = pack_dirs(2);
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < count; k += warps) {   // warp-uniform
         const long long idx = p.list[k];
         const int x = (int)(idx % nx);
         const int y = (int)((idx / nx) % ny);
         const int z = (int)(idx / ((long long)nx * ny));
         const int cpos[3] = {x, y, z};
         const int i = p.list_owner[k];
-        T drho_sum = T(0);    // neighbour densities minus rho0 (shifted, no cancellation)
-        int nnb = 0;
-        T uax[6][3];      // velocities of the axis neighbours +x -x +y -y +z -z
-        bool okax[6] = {false, false, false, false, false, false};
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            int nb[3] = {x + cx(q), y + cy(q), z + cz(q)};
+        const int q = lane < Q ? lane : 0;
+        const int c[3] = {dir_c(PX, q), dir_c(PY, q), dir_c(PZ, q)};
+        // lane q: neighbour x + c_q, fluid before and after the update
+        bool ok = false;
+        T dr = T(0), jx = T(0), jy = T(0), jz = T(0);
+        if (q >= 1) {
+            int nb[3] = {x + c[0], y + c[1], z + c[2]};
             bool out = false;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (p.g.per[d]) nb[d] = wrap_idx(nb[d], p.g.n[d]);
                 else if (nb[d] < 0 || nb[d] >= p.g.n[d]) out = true;
             }
-            if (out) continue;
-            const long long j = ((long long)nb[2] * ny + nb[1]) * nx + nb[0];
-            const uint8_t fl = p.flags[j];
-            if (fl & (FL_SOLID | FL_NEWFLUID)) continue;
-            T dr = T(0), jx = T(0), jy = T(0), jz = T(0);
+            if (!out) {
+                const long long j = ((long long)nb[2] * ny + nb[1]) * nx + nb[0];
+                if (!(p.flags[j] & (FL_SOLID | FL_NEWFLUID))) {
+                    ok = true;
 #pragma unroll
-            for (int r = 0; r < Q; ++r) {
-                const T v = Store<S>::load(f + (long long)r * N + j);
-                dr += v;
-                jx += (T)cx(r) * v;
-                jy += (T)cy(r) * v;
-                jz += (T)cz(r) * v;
+                    for (int r = 0; r < Q; ++r) {
+                        const T v = Store<S>::load(f + (long long)r * N + j);
+                        dr += v;
+                        jx += (T)cx(r) * v;
+                        jy += (T)cy(r) * v;
+                        jz += (T)cz(r) * v;
+                    }
+                }
             }
-            drho_sum += dr;
-            ++nnb;
-            const int slot = c2(q) != 1 ? -1 : (cx(q) == 1 ? 0 : cx(q) == -1 ? 1 : cy(q) == 1 ? 2 : cy(q) == -1 ? 3 : cz(q) == 1 ? 4 : 5);
-            if (slot >= 0) {
-                okax[slot] = true;
-                uax[slot][0] = jx - T(0.5) * ax;
-                uax[slot][1] = jy - T(0.5) * ay;
-                uax[slot][2] = jz - T(0.5) * az;
-            }
+        }
+        T drho_sum = dr;   // neighbour densities minus rho0 (shifted, no cancellation)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) drho_sum += __shfl_xor_sync(FULL, drho_sum, o);
+        const unsigned okm = __ballot_sync(FULL, ok);
+        const int nnb = __popc(okm);
+        // velocities of the axis neighbours +x -x +y -y +z -z (lanes 4, 3, 1, 2, 5, 6)
+        const T vx = jx - T(0.5) * ax, vy = jy - T(0.5) * ay, vz = jz - T(0.5) * az;
+        constexpr int SLOT_Q[6] = {4, 3, 1, 2, 5, 6};
+        T uax[6][3];
+        bool okax[6];
+#pragma unroll
+        for (int sl = 0; sl < 6; ++sl) {
+            uax[sl][0] = __shfl_sync(FULL, vx, SLOT_Q[sl]);
+            uax[sl][1] = __shfl_sync(FULL, vy, SLOT_Q[sl]);
+            uax[sl][2] = __shfl_sync(FULL, vz, SLOT_Q[sl]);
+            okax[sl] = (okm >> SLOT_Q[sl]) & 1u;
         }
         const T drb = nnb ? drho_sum / (T)nnb : T(0);
         const T rb = T(1) + drb;
@@ -479,28 +496,29 @@ __global__ void refill_kernel(const RefillParams p) {
                 else g[a][b] = T(0);
             }
         }
-        const T coef = T(1) / (T(3) * (T)p.s_nu);   // c_s^2 / s_nu
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const T c[3] = {(T)cx(q), (T)cy(q), (T)cz(q)};
+        if (lane < Q) {
+            const T coef = T(1) / (T(3) * (T)p.s_nu);   // c_s^2 / s_nu
+            const T cf[3] = {(T)c[0], (T)c[1], (T)c[2]};
             T second = T(0);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
                     const T pab = rb * ut[a] * ut[b] - rb * coef * (g[a][b] + g[b][a]);
-                    second += pab * (c[a] * c[b] - (a == b ? T(1) / T(3) : T(0)));
+                    second += pab * (cf[a] * cf[b] - (a == b ? T(1) / T(3) : T(0)));
                 }
-            const T cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
+            const T cu = cf[0] * ut[0] + cf[1] * ut[1] + cf[2] * ut[2];
+            const int cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+            const T w = cc == 0 ? T(1) / T(3) : (cc == 1 ? T(1) / T(18) : T(1) / T(36));
             // f_q - w_q written without forming f_q: w_q (rho_bar - 1) + ...
-            const T dfq = wq<T>(q) * (drb + T(3) * rb * cu + T(4.5) * second);
+            const T dfq = w * (drb + T(3) * rb * cu + T(4.5) * second);
             Store<S>::store(fw + (long long)q * N + idx, dfq);
         }
     }
 }
 
 void launch_refill(const RefillParams& p, cudaStream_t st) {
-    const int blocks = 152 * 4, threads = 128;
+    const int blocks = 152 * 8, threads = 128;   // 4 warps (cells) per block
     switch (p.storage) {
         case 0: refill_kernel<double><<<blocks, threads, 0, st>>>(p); break;
         case 1: refill_kernel<float><<<blocks, threads, 0, st>>>(p); break;
