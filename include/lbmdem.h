@@ -65,6 +65,7 @@ typedef enum {
 #define LBM_FLAG_NEAR 0x04u      /* fluid cell that may have a particle link              */
 #define LBM_FLAG_MISS 0x08u      /* solid cell that may own a missing link (Sec. 2.2)     */
 #define LBM_FLAG_NEWFLUID 0x10u  /* solid before the last mapping update, fluid after     */
+#define LBM_FLAG_MULTI 0x20u     /* solid cell inside more than one sphere (owner: lowest) */
 
 /* Box: every axis is either periodic or closed by a no-slip wall on both of
  * its faces (halfway bounce-back, Eq. (14) with delta = 1/2). */
@@ -119,7 +120,8 @@ lbm_status lbm_required_bytes(const lbm_grid *grid, lbm_storage storage, int max
  * queued on it. The fluid starts at rest with rho = 1 and no particles.
  * Device memory is allocated by the library and released by lbm_destroy().
  * Errors: LBM_ERR_INVALID (bad sizes, a box of more than 2^31 - 2^24 cells,
- * tau <= 1/2, non-positive max_particles), LBM_ERR_OOM, LBM_ERR_CUDA. */
+ * tau <= 1/2, max_particles outside [0, 4,000,000]), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_grid *grid, const lbm_relax *relax, const double *body_force,
                       const lbm_dem *dem, lbm_storage storage, int max_particles,
                       void *cuda_stream, lbm_ctx **out);
@@ -171,9 +173,10 @@ lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);
 
 /* Copy / replace the post-collision PDFs f_q (unshifted values), 19 x cells
  * doubles, direction-major (q = 0..18 in the order fixed by App. A). Solid
- * cells read as NaN: every PDF slot of a solid cell holds a NaN marker, by
- * which the dense kernel finds particle links; values given for solid cells
- * are replaced by that marker. Synchronises the stream. */
+ * cells read as NaN: every PDF slot of a solid cell holds a NaN marker (with
+ * the owning particle in its payload for f32 and f64 storage), by which the
+ * dense kernel finds particle links; values given for solid cells are
+ * replaced by that marker. Synchronises the stream. */
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *f);
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
 

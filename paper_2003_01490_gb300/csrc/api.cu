@@ -221,7 +221,9 @@ lbm_status validate(const lbm_grid* g, const lbm_relax* r, const lbm_dem* d, lbm
     if (!(r->magic > 0.0) || !(r->lambda_b_shell > 0.0) || !(r->lambda_b_bulk > 0.0) || !(r->shell_width >= 0.0))
         return fail(nullptr, LBM_ERR_INVALID, "magic, lambda_b must be > 0 and shell_width >= 0");
     if (st < LBM_STORE_F64 || st > LBM_STORE_BF16) return fail(nullptr, LBM_ERR_INVALID, "unknown storage format");
-    if (max_particles < 0) return fail(nullptr, LBM_ERR_INVALID, "max_particles must be >= 0");
+    // the NaN marker of a solid cell carries particle + 1 in 22 bits
+    if (max_particles < 0 || max_particles > 4000000)
+        return fail(nullptr, LBM_ERR_INVALID, "max_particles must be in [0, 4,000,000]");
     if (d->n_sub < 1) return fail(nullptr, LBM_ERR_INVALID, "n_sub must be >= 1");
     if (!(d->e_dry > 0.0 && d->e_dry <= 1.0)) return fail(nullptr, LBM_ERR_INVALID, "e_dry must be in (0, 1]");
     if (!(d->nu_p >= 0.0 && d->nu_p < 1.0)) return fail(nullptr, LBM_ERR_INVALID, "nu_p must be in [0, 1)");

@@ -52,9 +52,23 @@ __host__ __device__ constexpr unsigned long long pack_dirs(int axis) {
 }
 __device__ __forceinline__ int dir_c(unsigned long long packed, int q) { return (int)((packed >> (2 * q)) & 3ull) - 1; }
 
+// NaN marker held by every PDF slot of a solid cell: a quiet NaN whose low 22
+// bits carry owner + 1 in the 4- and 8-byte formats (the 16-bit formats keep
+// no payload). Arithmetic NaNs are canonical (all payload bits set), which
+// decodes to an index above every particle count the library accepts.
+constexpr unsigned int MARKER_PAYLOAD = 0x3FFFFFu;
+__device__ __forceinline__ unsigned int marker_bits32(int owner) { return 0x7FC00000u | (unsigned)(owner + 1); }
+__device__ __forceinline__ unsigned long long marker_bits64(int owner) {
+    return 0x7FF8000000000000ull | (unsigned long long)(owner + 1);
+}
+__device__ __forceinline__ int marker_owner(float v) { return (int)(__float_as_uint(v) & MARKER_PAYLOAD) - 1; }
+__device__ __forceinline__ int marker_owner(double v) {
+    return (int)((unsigned long long)__double_as_longlong(v) & MARKER_PAYLOAD) - 1;
+}
+
 // flag bits (mirrors LBM_FLAG_* of the public header)
 constexpr uint8_t FL_SOLID = 0x01, FL_SHELL = 0x02, FL_NEAR = 0x04, FL_MISS = 0x08,
-                  FL_NEWFLUID = 0x10;
+                  FL_NEWFLUID = 0x10, FL_MULTI = 0x20;
 
 // device status bits (sticky, reported to the host by lbm_sync)
 constexpr int ST_UNSTABLE = 1, ST_TILE_OVERFLOW = 2, ST_NBR_OVERFLOW = 4, ST_BIN_OVERFLOW = 8,

@@ -120,16 +120,17 @@ void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
 
 // ------------------------------------------------------------ mapping
 
-// The NaN marker that every PDF slot of a solid cell holds (the dense kernel
-// finds particle links by it): all-ones exponent and mantissa, a NaN in
-// float64, float32, float16 and bfloat16.
-__device__ __forceinline__ void put_markers(void* const (&pdf)[2], int elem, long long ncells, long long idx) {
+// The NaN marker of a solid cell (owner + 1 in the payload of the 4- and
+// 8-byte formats) into all its PDF slots of both buffers; the dense kernel
+// finds particle links and their particle by it.
+__device__ __forceinline__ void put_markers(void* const (&pdf)[2], int elem, long long ncells, long long idx,
+                                            int owner) {
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         for (int q = 0; q < Q; ++q) {
             const long long k = (long long)q * ncells + idx;
-            if (elem == 8) reinterpret_cast<unsigned long long*>(pdf[b])[k] = 0x7fffffffffffffffull;
-            else if (elem == 4) reinterpret_cast<unsigned int*>(pdf[b])[k] = 0x7fffffffu;
+            if (elem == 8) reinterpret_cast<unsigned long long*>(pdf[b])[k] = marker_bits64(owner);
+            else if (elem == 4) reinterpret_cast<unsigned int*>(pdf[b])[k] = marker_bits32(owner);
             else reinterpret_cast<unsigned short*>(pdf[b])[k] = (unsigned short)0x7fff;
         }
     }
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
 
     int own[TILE_Z];
     unsigned shell4 = 0, nnear4 = 0;   // per z: shell bit; near count (saturating at 2) in 2 bits
+    unsigned multi4 = 0;               // per z: inside a second sphere
 #pragma unroll
     for (int j = 0; j < TILE_Z; ++j) own[j] = 0x7fffffff;
 #pragma unroll
@@ -286,7 +288,10 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
                     inside = r & 1;
                     in_shell = (r & 2) != 0;
                 }
-                if (inside) { if (id < own[j]) own[j] = id; }
+                if (inside) {
+                    if (own[j] != 0x7fffffff) multi4 |= 1u << j;
+                    if (id < own[j]) own[j] = id;
+                }
                 else if (in_shell) shell4 |= 1u << j;
             }
         }
@@ -312,8 +317,14 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
                 nf |= FL_MISS;
                 miss_bits |= 1u << j;
             }
+            // new solid cells get markers; the particle of a solid cell can only
+            // change where spheres overlap (now or at the last mapping), so
+            // those cells get them again
+            const bool multi = (multi4 >> j) & 1u;
+            if (multi) nf |= FL_MULTI;
             p.owner[idx] = own[j];
-            if (!(old & FL_SOLID) && p.pdf[0]) put_markers(p.pdf, p.elem, p.g.ncells, idx);
+            if ((!(old & FL_SOLID) || multi || (old & FL_MULTI)) && p.pdf[0])
+                put_markers(p.pdf, p.elem, p.g.ncells, idx, own[j]);
         } else {
             if (shell4 & (1u << j)) nf |= FL_SHELL;
             if (nn >= 1u) nf |= FL_NEAR;
@@ -387,7 +398,7 @@ void launch_map(const MapParams& p, cudaStream_t st) {
 __global__ void solid_markers_kernel(const __grid_constant__ MapParams p) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < p.g.ncells; idx += stride)
-        if (p.flags[idx] & FL_SOLID) put_markers(p.pdf, p.elem, p.g.ncells, idx);
+        if (p.flags[idx] & FL_SOLID) put_markers(p.pdf, p.elem, p.g.ncells, idx, p.owner[idx]);
 }
 
 void launch_solid_markers(const MapParams& p, cudaStream_t st) {

@@ -81,11 +81,15 @@ struct SCArgs {
     long long* acc_k;
 };
 
-// NaN marker held by every PDF slot of a solid cell
+// NaN marker of a solid cell of particle owner, and a plain NaN
 template <typename T>
-__device__ __forceinline__ T solid_marker();
-template <> __device__ __forceinline__ float solid_marker<float>() { return __int_as_float(0x7fffffff); }
-template <> __device__ __forceinline__ double solid_marker<double>() { return __longlong_as_double(0x7fffffffffffffffLL); }
+__device__ __forceinline__ T solid_marker(int owner);
+template <> __device__ __forceinline__ float solid_marker<float>(int owner) { return __uint_as_float(marker_bits32(owner)); }
+template <> __device__ __forceinline__ double solid_marker<double>(int owner) {
+    return __longlong_as_double((long long)marker_bits64(owner));
+}
+template <typename T>
+__device__ __forceinline__ T plain_nan() { return solid_marker<T>(MARKER_PAYLOAD - 1); }
 
 // CLI value f_q(x, t+1) of the link of fluid cell (x, y, z) in pull direction
 // q into the solid cell x - c_q, and its force and torque into acc (float32
@@ -96,8 +100,8 @@ template <> __device__ __forceinline__ double solid_marker<double>() { return __
 __host__ __device__ constexpr int qinfo(int q) { return (cx(q) + 1) | ((cy(q) + 1) << 2) | ((cz(q) + 1) << 4) | (opp(q) << 6); }
 
 template <typename S, typename T>
-__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, int qi, Acc<T>& acc,
-                                        const Sinks& sk) {
+__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, int qi, int key1,
+                                        Acc<T>& acc, const Sinks& sk) {
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int plane = nx * ny;
     const long long N = a.g.ncells;
@@ -116,8 +120,9 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
     const int idx = z * plane + y * nx + x;
     const int up = uv[2] * plane + uv[1] * nx + uv[0];
     const int down = dv[2] * plane + dv[1] * nx + dv[0];
-    const int i = a.owner[up];
-    if (i < 0) return solid_marker<T>();   // a NaN from a fluid cell: left for the stability check
+    // the particle from the marker's payload (the owner array for 16-bit storage)
+    const int i = key1 > 0 ? key1 - 1 : a.owner[up];
+    if (i < 0 || i >= a.np) return plain_nan<T>();   // a NaN from a fluid cell: left for the stability check
     const T fout = Store<S>::load(a.src + p * N + idx);
     const T fin = Store<S>::load(a.src + q * N + idx);
     T fdown = cli ? Store<S>::load(a.src + p * N + down) : T(0);
@@ -276,16 +281,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     // dynamic shared memory (sc_smem_bytes): PDFs of the cells of warps with
     // links [q][thread]; per lane the particle of its open force sums (-1:
     // none), the open float sums (F, T) and the exact integer sums (float32
-    // path); per warp the link entries q | lane << 8
+    // path); per warp the link entries q | lane << 5 | (particle + 1) << 10
     extern __shared__ __align__(16) unsigned char sc_smem[];
     T (*s_f)[256] = reinterpret_cast<T (*)[256]>(sc_smem);
     T (*s_sum)[256] = reinterpret_cast<T (*)[256]>(sc_smem + Q * 256 * sizeof(T));
     int (*s_int)[256] = reinterpret_cast<int (*)[256]>(sc_smem + (Q + 6) * 256 * sizeof(T));
     int* s_key = reinterpret_cast<int*>(sc_smem + (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0));
-    unsigned short (*s_queue)[32 * (Q - 1)] =
-        reinterpret_cast<unsigned short (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
-    constexpr int G = 32 / (int)sizeof(S);
-    const unsigned gmask = (G >= 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
+    unsigned (*s_queue)[32 * (Q - 1)] =
+        reinterpret_cast<unsigned (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
     __shared__ int s_qi[Q];
     if (tid < Q) {
@@ -309,8 +312,6 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
         const int idx = z * plane + y * nx + x;
         const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
         const bool fluid = !(fl & FL_SOLID);
-        // lanes of a 32-byte sector (G cells) that hold fluid cells
-        const unsigned bal = __ballot_sync(FULL, fluid && valid);
         T f[Q];
         unsigned lmask = 0;   // pull directions of this cell that are particle links
         if (fluid) {
@@ -352,20 +353,24 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
             const int cnt = __popc(lmask);
             const int incl = warp_incl_scan(cnt, lane);
             const int total = __shfl_sync(FULL, incl, 31);
-            unsigned short* queue = s_queue[tid >> 5];
+            // the cell's PDFs wait in shared memory (freeing their registers for
+            // the link work); each link's CLI value lands in its cell's slot
+#pragma unroll
+            for (int q = 0; q < Q; ++q) s_f[q][tid] = f[q];
+            // entries q | lane << 5 | (particle + 1) << 10, the particle read
+            // from the marker's payload (0: look it up in the owner array)
+            unsigned* queue = s_queue[tid >> 5];
             {
                 unsigned mm = lmask;
                 int pos = incl - cnt;
                 while (mm) {
                     const int q = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    queue[pos++] = (unsigned short)(q | (lane << 8));
+                    unsigned key1 = 0;
+                    if constexpr (sizeof(S) >= 4) key1 = (unsigned)(marker_owner(s_f[q][tid]) + 1);
+                    queue[pos++] = (unsigned)q | ((unsigned)lane << 5) | (key1 << 10);
                 }
             }
-            // the cell's PDFs wait in shared memory (freeing their registers for
-            // the link work); each link's CLI value lands in its cell's slot
-#pragma unroll
-            for (int q = 0; q < Q; ++q) s_f[q][tid] = f[q];
             __syncwarp();
             Acc<T> acc;
             acc.key = s_key[tid];
@@ -380,8 +385,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
                 const int k = lane * m + j;
                 if (k < total) {
                     const unsigned e = queue[k];
-                    const int q = (int)(e & 31u), src = (int)(e >> 8);
-                    s_f[q][tid - lane + src] = link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], acc, sk);
+                    const int q = (int)(e & 31u), src = (int)((e >> 5) & 31u);
+                    s_f[q][tid - lane + src] =
+                        link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], (int)(e >> 10), acc, sk);
                 }
             }
             s_key[tid] = acc.key;
@@ -395,16 +401,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
 #pragma unroll
             for (int q = 0; q < Q; ++q) f[q] = s_f[q][tid];
         }
-        if (!fluid) {
-            // Solid cells keep the marker in every slot. Those that share a
-            // 32-byte sector with fluid cells write it again, so every written
-            // sector is complete and L2 needs no fill read.
-            if (valid && (bal & gmask)) {
-                const T mk = solid_marker<T>();
-#pragma unroll
-                for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, mk);
-            }
-        } else {
+        // solid cells store nothing: their slots keep the marker of the mapping
+        if (fluid) {
             collide_store<S, T>(a, f, fl, N, idx);
         }
     }
@@ -423,7 +421,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
 // bytes of dynamic shared memory of the kernel (256 threads)
 template <typename T>
 constexpr size_t sc_smem_bytes() {
-    return (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0) + 256 * 4 + 8 * 32 * (Q - 1) * 2;
+    return (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0) + 256 * 4 + 8 * 32 * (Q - 1) * 4;
 }
 
 template <typename S>

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, '_lib', 'liblbmdem.so')
 
 STORAGE = {'f64': 0, 'f32': 1, 'f16': 2, 'bf16': 3}
-FLAG_SOLID, FLAG_SHELL, FLAG_NEAR, FLAG_MISS, FLAG_NEWFLUID = 0x01, 0x02, 0x04, 0x08, 0x10
+FLAG_SOLID, FLAG_SHELL, FLAG_NEAR, FLAG_MISS, FLAG_NEWFLUID, FLAG_MULTI = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20
 STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CUDA',
           -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -7: 'LBM_ERR_STATE'}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
