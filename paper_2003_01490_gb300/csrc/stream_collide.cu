@@ -9,15 +9,16 @@
 // through a rank-2 correction in moment space.
 //
 // PDFs are stored shifted (f_q - w_q) in SoA layout f[q][z][y][x], read from
-// one buffer and written to the other. Every PDF slot of a solid cell holds a
-// NaN marker (written by the mapping when the cell turns solid and kept by
-// this kernel), so the pull of a fluid cell x finds its particle links for
-// free: direction q is a link exactly when the value pulled from
-// y = x - c_q is the marker. The warp then spreads its links evenly over its
-// lanes; each link's CLI value f_q(x, t+1) (link fraction delta_p from the
-// ray-sphere intersection; bounce-back, delta = 1/2 in the coefficients, when
-// x + c_q is not fluid) goes through shared memory to the thread of x, and
-// its force and torque are reduced per warp by particle (lanes with the same
+// one buffer and written to the other (fluid cells only). Every PDF slot of a
+// solid cell holds a NaN marker written by the mapping (with the owning
+// particle in its payload for 4- and 8-byte storage), so the pull of a fluid
+// cell x finds its particle links for free: direction q is a link exactly
+// when the value pulled from y = x - c_q is a marker. The warp then spreads
+// its links evenly over its lanes; each link's CLI value f_q(x, t+1) (link
+// fraction delta_p from the ray-sphere intersection; bounce-back, delta = 1/2
+// in the coefficients, when x + c_q is not fluid) goes through shared memory
+// to the thread of x, and its force and torque are summed per lane while the
+// particle stays the same, then per warp by particle (lanes with the same
 // particle found with match_any) and added atomically.
 //
 // Per-particle sums. Float64 storage: float64 partial sums, float64 atomics.
@@ -261,6 +262,39 @@ __device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], 
     for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
 }
 
+// a lane's open force sums between rows: particle, float sums and the exact
+// integer sums (float32 path) as two 16-bit halves per word; sums that could
+// leave 16 bits are flushed to the particle first
+template <typename T>
+__device__ __forceinline__ void load_sums(Acc<T>& acc, const int* s_key, T (*s_sum)[256], int (*s_int)[256], int tid) {
+    acc.key = s_key[tid];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc.f[c] = s_sum[c][tid];
+    if (sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int v = s_int[c][tid];
+            acc.k[2 * c] = (int)(short)(v & 0xffff);
+            acc.k[2 * c + 1] = v >> 16;
+        }
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store_sums(Acc<T>& acc, int* s_key, T (*s_sum)[256], int (*s_int)[256], int tid,
+                                           const Sinks& sk) {
+    if (sizeof(T) == 4) {
+        bool big = false;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) big |= acc.k[c] > 30000 || acc.k[c] < -30000;
+        if (big && acc.key >= 0) flush<T>(acc, sk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_int[c][tid] = (acc.k[2 * c] & 0xffff) | (acc.k[2 * c + 1] << 16);
+    }
+    s_key[tid] = acc.key;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_sum[c][tid] = acc.f[c];
+}
+
 // One block per (x, y) tile of 256 cells and a chunk of zchunk (<= LBM_SC_ZCHUNK)
 // consecutive z planes, marched in order: the links a warp meets in
 // consecutive rows mostly belong to the same spheres, so a lane's force sums
@@ -281,14 +315,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     // dynamic shared memory (sc_smem_bytes): PDFs of the cells of warps with
     // links [q][thread]; per lane the particle of its open force sums (-1:
     // none), the open float sums (F, T) and the exact integer sums (float32
-    // path); per warp the link entries q | lane << 5 | (particle + 1) << 10
+    // path, two 16-bit halves per word); per warp the link entries q | lane << 8
     extern __shared__ __align__(16) unsigned char sc_smem[];
     T (*s_f)[256] = reinterpret_cast<T (*)[256]>(sc_smem);
     T (*s_sum)[256] = reinterpret_cast<T (*)[256]>(sc_smem + Q * 256 * sizeof(T));
     int (*s_int)[256] = reinterpret_cast<int (*)[256]>(sc_smem + (Q + 6) * 256 * sizeof(T));
-    int* s_key = reinterpret_cast<int*>(sc_smem + (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0));
-    unsigned (*s_queue)[32 * (Q - 1)] =
-        reinterpret_cast<unsigned (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
+    int* s_key = reinterpret_cast<int*>(sc_smem + (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 3 * 256 * 4 : 0));
+    unsigned short (*s_queue)[32 * (Q - 1)] =
+        reinterpret_cast<unsigned short (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
     __shared__ int s_qi[Q];
     if (tid < Q) {
@@ -302,7 +336,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         s_sum[c][tid] = T(0);
-        if (sizeof(T) == 4) s_int[c][tid] = 0;
+        if (sizeof(T) == 4 && c < 3) s_int[c][tid] = 0;
     }
     bool open = false;   // warp-uniform: some lane of the warp holds sums
 
@@ -357,45 +391,36 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
             // the link work); each link's CLI value lands in its cell's slot
 #pragma unroll
             for (int q = 0; q < Q; ++q) s_f[q][tid] = f[q];
-            // entries q | lane << 5 | (particle + 1) << 10, the particle read
-            // from the marker's payload (0: look it up in the owner array)
-            unsigned* queue = s_queue[tid >> 5];
+            // entries q | lane << 8
+            unsigned short* queue = s_queue[tid >> 5];
             {
                 unsigned mm = lmask;
                 int pos = incl - cnt;
                 while (mm) {
                     const int q = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    unsigned key1 = 0;
-                    if constexpr (sizeof(S) >= 4) key1 = (unsigned)(marker_owner(s_f[q][tid]) + 1);
-                    queue[pos++] = (unsigned)q | ((unsigned)lane << 5) | (key1 << 10);
+                    queue[pos++] = (unsigned short)(q | (lane << 8));
                 }
             }
             __syncwarp();
             Acc<T> acc;
-            acc.key = s_key[tid];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                acc.f[c] = s_sum[c][tid];
-                if (sizeof(T) == 4) acc.k[c] = s_int[c][tid];
-            }
+            load_sums<T>(acc, s_key, s_sum, s_int, tid);
             // lane l takes the m consecutive entries l m .. l m + m - 1
             const int m = (total + 31) >> 5;
             for (int j = 0; j < m; ++j) {
                 const int k = lane * m + j;
                 if (k < total) {
                     const unsigned e = queue[k];
-                    const int q = (int)(e & 31u), src = (int)((e >> 5) & 31u);
-                    s_f[q][tid - lane + src] =
-                        link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], (int)(e >> 10), acc, sk);
+                    const int q = (int)(e & 31u), src = (int)(e >> 8);
+                    const int st = tid - lane + src;
+                    // the particle from the marker's payload, still in the slot
+                    // (0: look it up in the owner array)
+                    int key1 = 0;
+                    if constexpr (sizeof(S) >= 4) key1 = marker_owner(s_f[q][st]) + 1;
+                    s_f[q][st] = link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], key1, acc, sk);
                 }
             }
-            s_key[tid] = acc.key;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                s_sum[c][tid] = acc.f[c];
-                if (sizeof(T) == 4) s_int[c][tid] = acc.k[c];
-            }
+            store_sums<T>(acc, s_key, s_sum, s_int, tid, sk);
             open = true;
             __syncwarp();
 #pragma unroll
@@ -408,12 +433,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     }
     if (open) {   // warp-uniform
         Acc<T> acc;
-        acc.key = s_key[tid];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            acc.f[c] = s_sum[c][tid];
-            if (sizeof(T) == 4) acc.k[c] = s_int[c][tid];
-        }
+        load_sums<T>(acc, s_key, s_sum, s_int, tid);
         commit<T>(acc, sk);
     }
 }
@@ -421,7 +441,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
 // bytes of dynamic shared memory of the kernel (256 threads)
 template <typename T>
 constexpr size_t sc_smem_bytes() {
-    return (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 6 * 256 * 4 : 0) + 256 * 4 + 8 * 32 * (Q - 1) * 4;
+    return (Q + 6) * 256 * sizeof(T) + (sizeof(T) == 4 ? 3 * 256 * 4 : 0) + 256 * 4 + 8 * 32 * (Q - 1) * 2;
 }
 
 template <typename S>
