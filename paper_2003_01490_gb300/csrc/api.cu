@@ -58,6 +58,9 @@ struct lbm_ctx {
     long long launches = 0;
     // captured steady-state steps, one per (PDF buffer, history buffer) parity
     cudaStream_t capture_stream = nullptr;
+    // second stream for work beside the dense kernel, with its fork/join events
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t step_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};   // kernel launches in each graph
     int graph_hcur[2][2] = {{0, 0}, {0, 0}};            // history parity after each graph
@@ -73,6 +76,27 @@ struct lbm_ctx {
     size_t ev_used = 0;
     long long prof_steps = 0;
 };
+
+// streams, events and graphs a context holds (device memory is separate)
+void destroy_handles(lbm_ctx* ctx) {
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    ctx->events.clear();
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ctx->step_graph[a][b]) {
+                cudaGraphExecDestroy(ctx->step_graph[a][b]);
+                ctx->step_graph[a][b] = nullptr;
+            }
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->side_stream) {
+        cudaStreamSynchronize(ctx->side_stream);
+        cudaStreamDestroy(ctx->side_stream);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    ctx->capture_stream = ctx->side_stream = nullptr;
+    ctx->ev_fork = ctx->ev_join = nullptr;
+}
 
 namespace {
 
@@ -253,7 +277,11 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
             ctx->num_sms = sms;
         cudaError_t pe = prepare_stream_collide((int)st);
+        if (pe == cudaSuccess) pe = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+        if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+        if (pe == cudaSuccess) pe = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
         if (pe != cudaSuccess) {
+            destroy_handles(ctx);
             delete ctx;
             return fail(nullptr, LBM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(pe));
         }
@@ -274,10 +302,12 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->bytes = L.total;
     if (arena) {
         if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) {
+            destroy_handles(ctx);
             delete ctx;
             return fail(nullptr, LBM_ERR_INVALID, "arena must be 256-byte aligned");
         }
         if (arena_bytes < L.total) {
+            destroy_handles(ctx);
             delete ctx;
             return fail(nullptr, LBM_ERR_OOM, "arena smaller than lbm_required_bytes()");
         }
@@ -287,6 +317,7 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
         void* p = nullptr;
         cudaError_t e = cudaMalloc(&p, L.total);
         if (e != cudaSuccess) {
+            destroy_handles(ctx);
             delete ctx;
             return fail(nullptr, LBM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
@@ -361,6 +392,7 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
     if (e != cudaSuccess) {
         if (ctx->own_memory) cudaFree(ctx->base);
+        destroy_handles(ctx);
         delete ctx;
         return fail(nullptr, LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
     }
@@ -381,6 +413,7 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
     if (e != cudaSuccess) {
         if (ctx->own_memory) cudaFree(ctx->base);
+        destroy_handles(ctx);
         delete ctx;
         return fail(nullptr, LBM_ERR_CUDA, std::string("initial mapping: ") + cudaGetErrorString(e));
     }
@@ -747,10 +780,20 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     lp.num_sms = ctx->num_sms;
     lp.accel_d = ctx->accel;
     lp.accel_f = ctx->accel_f;
-    launch_boundary(lp, sm);
+    launch_boundary(lp, sm, BC_ACCEL);
+    if (lp.missing_links) {
+        // the missing links run beside the dense kernel on the side stream
+        // (their sums commute with the dense kernel's); finalize waits for both
+        CK(cudaEventRecord(ctx->ev_fork, sm));
+        CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
+        launch_boundary(lp, ctx->side_stream, BC_LINKS);
+        CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
+        ctx->launches += 1;
+    }
     CK(prof_mark(ctx));
     launch_stream_collide(lp, sm);
     CK(prof_mark(ctx));
+    if (lp.missing_links) CK(cudaStreamWaitEvent(sm, ctx->ev_join, 0));
     FinalizeParams fpp{};
     fpp.P = ctx->P;
     fpp.use_fixed = ctx->storage != LBM_STORE_F64;
@@ -1037,11 +1080,7 @@ void lbm_destroy(lbm_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            if (ctx->step_graph[a][b]) cudaGraphExecDestroy(ctx->step_graph[a][b]);
-    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    destroy_handles(ctx);
     if (ctx->own_memory && ctx->base) cudaFree(ctx->base);
     delete ctx;
 }

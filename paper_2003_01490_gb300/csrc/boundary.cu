@@ -4,7 +4,8 @@
 //
 // Thread 0 of block 0 forms the fluid body force a_user - ext_total / N_fluid
 // (the counter force of a periodic suspension, N_fluid from the last mapping)
-// that the dense kernel and the refill use. The other work walks the
+// that the dense kernel and the refill use (mode BC_ACCEL). The other work
+// (mode BC_LINKS, launched beside the dense kernel on a second stream) walks the
 // missing-link list of the mapping (solid cells next to another body): a link
 // x -> s into a solid cell s of particle i is missing when x belongs to
 // another body (or lies behind a wall) and its centre is not inside sphere i;
@@ -118,9 +119,9 @@ __device__ __forceinline__ void missing_links(const BcArgs<S>& a, long long idx,
 }
 
 template <typename S>
-__global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a) {
+__global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mode) {
     using T = typename Store<S>::T;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if ((mode & BC_ACCEL) && blockIdx.x == 0 && threadIdx.x == 0) {
         double acc3[3] = {a.a_user[0], a.a_user[1], a.a_user[2]};
         if (a.counterforce) {
             const double nf = (double)(a.g.ncells - (long long)(*a.n_solid));
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a) {
             a.accel_f[d] = (float)acc3[d];
         }
     }
-    if (!a.missing_links) return;
+    if (!(mode & BC_LINKS) || !a.missing_links) return;
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
     const int mcount = min(*a.miss_count, a.miss_cap);
     const int stride = (int)(gridDim.x * blockDim.x);
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a) {
 }
 
 template <typename S>
-void launch_boundary_t(const LbmStepParams& p, cudaStream_t st) {
+void launch_boundary_t(const LbmStepParams& p, cudaStream_t st, int mode) {
     BcArgs<S> b;
     b.flags = p.flags;
     b.owner = p.owner;
@@ -170,16 +171,16 @@ void launch_boundary_t(const LbmStepParams& p, cudaStream_t st) {
     b.n_solid = p.n_solid;
     b.accel_d = p.accel_d;
     b.accel_f = p.accel_f;
-    const int blocks = p.missing_links ? 8 * (p.num_sms > 0 ? p.num_sms : 1) : 1;
-    boundary_kernel<S><<<blocks, 128, 0, st>>>(b);
+    const int blocks = (mode & BC_LINKS) && p.missing_links ? 8 * (p.num_sms > 0 ? p.num_sms : 1) : 1;
+    boundary_kernel<S><<<blocks, 128, 0, st>>>(b, mode);
 }
 
-void launch_boundary(const LbmStepParams& p, cudaStream_t st) {
+void launch_boundary(const LbmStepParams& p, cudaStream_t st, int mode) {
     switch (p.storage) {
-        case 0: launch_boundary_t<double>(p, st); break;
-        case 1: launch_boundary_t<float>(p, st); break;
-        case 2: launch_boundary_t<__half>(p, st); break;
-        default: launch_boundary_t<__nv_bfloat16>(p, st); break;
+        case 0: launch_boundary_t<double>(p, st, mode); break;
+        case 1: launch_boundary_t<float>(p, st, mode); break;
+        case 2: launch_boundary_t<__half>(p, st, mode); break;
+        default: launch_boundary_t<__nv_bfloat16>(p, st, mode); break;
     }
 }
 

@@ -30,7 +30,9 @@ struct LbmStepParams {
     double* accel_d;                 // out: fluid body force of the step [3]
     float* accel_f;
 };
-void launch_boundary(const LbmStepParams& p, cudaStream_t st);
+// BC_ACCEL: the fluid body force of the step; BC_LINKS: the missing links
+constexpr int BC_ACCEL = 1, BC_LINKS = 2;
+void launch_boundary(const LbmStepParams& p, cudaStream_t st, int mode);
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st);
 // kernel attributes on the current device (before any launch or capture)
 cudaError_t prepare_stream_collide(int storage);
