@@ -102,35 +102,29 @@ __host__ __device__ constexpr int qinfo(int q) { return (cx(q) + 1) | ((cy(q) + 
 
 template <typename S, typename T>
 __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, int qi, int key1,
-                                        Acc<T>& acc, const Sinks& sk) {
+                                        unsigned lm_src, T fdown_raw, Acc<T>& acc, const Sinks& sk) {
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int plane = nx * ny;
     const long long N = a.g.ncells;
     const int c[3] = {(qi & 3) - 1, ((qi >> 2) & 3) - 1, ((qi >> 4) & 3) - 1};
     const int p = (qi >> 6) & 31;
-    const int cpos[3] = {x, y, z};
-    int uv[3], dv[3];
-    bool cli = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        uv[d] = wrap_idx(cpos[d] - c[d], a.g.n[d]);
-        dv[d] = cpos[d] + c[d];
-        if (!a.g.per[d] && (dv[d] < 0 || dv[d] >= a.g.n[d])) cli = false;
-        dv[d] = wrap_idx(dv[d], a.g.n[d]);
-    }
     const int idx = z * plane + y * nx + x;
-    const int up = uv[2] * plane + uv[1] * nx + uv[0];
-    const int down = dv[2] * plane + dv[1] * nx + dv[0];
     // the particle from the marker's payload (the owner array for 16-bit storage)
-    const int i = key1 > 0 ? key1 - 1 : a.owner[up];
+    int i = key1 - 1;
+    if (key1 <= 0) {
+        const int uv[3] = {wrap_idx(x - c[0], nx), wrap_idx(y - c[1], ny), wrap_idx(z - c[2], a.g.n[2])};
+        i = a.owner[uv[2] * plane + uv[1] * nx + uv[0]];
+    }
     if (i < 0 || i >= a.np) return plain_nan<T>();   // a NaN from a fluid cell: left for the stability check
     const T fout = Store<S>::load(a.src + p * N + idx);
     const T fin = Store<S>::load(a.src + q * N + idx);
-    T fdown = cli ? Store<S>::load(a.src + p * N + down) : T(0);
-    if (fdown != fdown) {   // x + c_q is solid: bounce-back coefficients
-        cli = false;
-        fdown = T(0);
-    }
+    // CLI needs x + c_q fluid and inside the box; its post-collision f_p is the
+    // cell's own pull in direction p (marker there: bounce-back coefficients)
+    bool cli = !((lm_src >> p) & 1u);
+    if (!a.g.per[0] && (x + c[0] < 0 || x + c[0] >= nx)) cli = false;
+    if (!a.g.per[1] && (y + c[1] < 0 || y + c[1] >= ny)) cli = false;
+    if (!a.g.per[2] && (z + c[2] < 0 || z + c[2] >= a.g.n[2])) cli = false;
+    const T fdown = cli ? fdown_raw : T(0);
     T r[3], R, u[3], om[3];
     int n[3];
     T cc;   // |r|^2 - R^2
@@ -409,15 +403,21 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
             const int m = (total + 31) >> 5;
             for (int j = 0; j < m; ++j) {
                 const int k = lane * m + j;
+                const unsigned e = k < total ? queue[k] : 0u;
+                const int q = (int)(e & 31u), src = (int)(e >> 8);
+                const unsigned lm_src = __shfl_sync(FULL, lmask, src);
                 if (k < total) {
-                    const unsigned e = queue[k];
-                    const int q = (int)(e & 31u), src = (int)(e >> 8);
                     const int st = tid - lane + src;
+                    const int qi = s_qi[q];
                     // the particle from the marker's payload, still in the slot
                     // (0: look it up in the owner array)
                     int key1 = 0;
                     if constexpr (sizeof(S) >= 4) key1 = marker_owner(s_f[q][st]) + 1;
-                    s_f[q][st] = link_value<S, T>(a, x - lane + src, y, z, q, s_qi[q], key1, acc, sk);
+                    // f_p pulled by the same cell: f~_p(x + c_q) (read before any
+                    // link of direction p could overwrite it; such a link makes
+                    // x + c_q solid and its value unused)
+                    const T fdown_raw = s_f[(qi >> 6) & 31][st];
+                    s_f[q][st] = link_value<S, T>(a, x - lane + src, y, z, q, qi, key1, lm_src, fdown_raw, acc, sk);
                 }
             }
             store_sums<T>(acc, s_key, s_sum, s_int, tid, sk);
