@@ -229,6 +229,10 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     L.add(8 * n);                                // 55 hI
     L.add(8 * 3 * n);                            // 56 ext
     L.add(4 * (size_t)s.refill_cap);             // 57 refill_owner
+    for (int h = 0; h < 2; ++h) {
+        L.add(4 * 3 * n);                        // 58/60 float32 u
+        L.add(4 * 3 * n);                        // 59/61 float32 omega
+    }
     (void)g;
 }
 
@@ -355,6 +359,10 @@ lbm_status create_impl(const lbm_grid* g, const lbm_relax* r, const double* bf, 
     ctx->P.hm = (double*)at(54);
     ctx->P.hI = (double*)at(55);
     ctx->P.ext = (double*)at(56);
+    for (int h = 0; h < 2; ++h) {
+        ctx->P.ufs[h] = (float*)at(58 + 2 * h);
+        ctx->P.omfs[h] = (float*)at(59 + 2 * h);
+    }
     ctx->scratch = (double*)at(11);
     ctx->scratch_cells = s.scratch_cells;
     ctx->bin_cap = s.bin_cap;
@@ -453,6 +461,15 @@ lbm_status remap(lbm_ctx* ctx, cudaStream_t sm) {
     return LBM_OK;
 }
 
+template <typename T>
+void fill_consts(const DemParams& dp, DemConsts<T>& k) {
+    k.mu_f = (T)dp.mu_f; k.cut_n = (T)dp.cut_n; k.cut_tt = (T)dp.cut_tt; k.cut_tr = (T)dp.cut_tr;
+    k.cut_max = (T)dp.cut_max; k.inv_cut_n = (T)dp.inv_cut_n; k.inv_cut_tt = (T)dp.inv_cut_tt;
+    k.inv_cut_tr = (T)dp.inv_cut_tr; k.min_a = (T)dp.min_a; k.min_b = (T)dp.min_b; k.log_e = (T)dp.log_e;
+    k.pi2_log_e2 = (T)dp.pi2_log_e2; k.kappa = (T)dp.kappa; k.sqrt_kappa = (T)dp.sqrt_kappa;
+    k.mu_p = (T)dp.mu_p; k.Tc = (T)dp.Tc; k.dt = (T)dp.dt;
+}
+
 DemParams dem_params(lbm_ctx* ctx) {
     DemParams dp{};
     dp.g = ctx->g;
@@ -492,6 +509,9 @@ DemParams dem_params(lbm_ctx* ctx) {
     dp.tangential = d.tangential_lubrication;
     dp.dt = 1.0 / d.n_sub;
     dp.status = ctx->status;
+    dp.pair_f32 = ctx->storage != LBM_STORE_F64;
+    fill_consts(dp, dp.kd);
+    fill_consts(dp, dp.kf);
     return dp;
 }
 

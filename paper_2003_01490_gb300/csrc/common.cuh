@@ -158,6 +158,8 @@ struct Particles {
     double* us[2];
     double* oms[2];
     float* xfs[2];
+    float* ufs[2];         // float32 copies of us, oms for the float32 pair laws
+    float* omfs[2];
     // DEM neighbour structure and contact history
     int* bin_count;        // [nbins]
     int* bin_list;         // [nbins * BIN_CAP]

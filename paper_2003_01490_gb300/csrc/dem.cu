@@ -14,24 +14,46 @@
 
 namespace lbmdem {
 
-struct V3 {
-    double x, y, z;
+template <typename T>
+struct Vec3 {
+    T x, y, z;
 };
+using V3 = Vec3<double>;
 __device__ __forceinline__ V3 mk(double x, double y, double z) { return {x, y, z}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
-__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+template <typename T>
+__device__ __forceinline__ Vec3<T> zero3() { return {T(0), T(0), T(0)}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator+(Vec3<T> a, Vec3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator-(Vec3<T> a, Vec3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator-(Vec3<T> a) { return {-a.x, -a.y, -a.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator*(T s, Vec3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T>
+__device__ __forceinline__ T dot(Vec3<T> a, Vec3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> cross(Vec3<T> a, Vec3<T> b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 __device__ __forceinline__ V3 ld3(const double* p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
+__device__ __forceinline__ Vec3<float> ld3(const float* p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
 __device__ __forceinline__ void st3(double* p, int i, V3 v) {
     p[3 * i] = v.x;
     p[3 * i + 1] = v.y;
     p[3 * i + 2] = v.z;
 }
+template <typename T, typename U>
+__device__ __forceinline__ Vec3<T> cvt3(Vec3<U> v) { return {(T)v.x, (T)v.y, (T)v.z}; }
+__device__ __forceinline__ float tlog(float x) { return logf(x); }
+__device__ __forceinline__ double tlog(double x) { return log(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+// the interaction constants in the pair arithmetic's precision
+template <typename T>
+__device__ __forceinline__ const DemConsts<T>& consts(const DemParams& p);
+template <> __device__ __forceinline__ const DemConsts<double>& consts<double>(const DemParams& p) { return p.kd; }
+template <> __device__ __forceinline__ const DemConsts<float>& consts<float>(const DemParams& p) { return p.kf; }
 __device__ __forceinline__ float mimgf(float d, int n, int per) {
     if (per) {
         const float half = 0.5f * (float)n;
@@ -137,6 +159,12 @@ __global__ void bin_fill_kernel(const DemParams p) {
     int b[3];
     for (int d = 0; d < 3; ++d) b[d] = bin_coord(p.P.xf[3 * i + d], (float)p.binsize[d], p.nbins[d]);
     const long long bi = ((long long)b[2] * p.nbins[1] + b[1]) * p.nbins[0] + b[0];
+    if (p.pair_f32) {   // float32 copies of the subcycle state read by the float32 pair laws
+        for (int d = 0; d < 3; ++d) {
+            p.P.ufs[0][3 * i + d] = (float)p.P.us[0][3 * i + d];
+            p.P.omfs[0][3 * i + d] = (float)p.P.oms[0][3 * i + d];
+        }
+    }
     const int slot = atomicAdd(p.P.bin_count + bi, 1);
     if (slot < BIN_CAP) p.P.bin_list[bi * BIN_CAP + slot] = i;
     else atomicOr(p.status, ST_BIN_OVERFLOW);
@@ -247,134 +275,174 @@ void launch_dem_position(const DemParams& p, cudaStream_t st) {
 // ------------------------------------------------------------ interaction laws
 
 // lubrication force and torque on i due to j (Rj <= 0: plane wall), Eqs. (27)-(33)
-__device__ void lubrication_on_i(const DemParams& p, double Ri, double Rj, double delta, V3 n, V3 uij,
-                                 V3 omi, V3 omj, double dmin, V3& F, V3& T) {
-    const double pi = 3.14159265358979323846;
-    const double mu = p.mu_f;
-    const double dl = delta > dmin ? delta : dmin;
-    const V3 un = dot(uij, n) * n;
-    const V3 ut = uij - un;
-    double c_n, c_ftt, c_ttt, c_ftr, c_ttr;
-    V3 om_ftr, om_ttr;
-    if (Rj <= 0.0) {
-        c_n = 1.0; c_ftt = 8.0 / 15.0; c_ttt = 1.0 / 10.0; c_ftr = 2.0 / 15.0; c_ttr = 2.0 / 5.0;
+template <typename T>
+__device__ void lubrication_on_i(const DemConsts<T>& k, int tangential, T Ri, T Rj, T delta, Vec3<T> n,
+                                 Vec3<T> uij, Vec3<T> omi, Vec3<T> omj, T dmin, Vec3<T>& F, Vec3<T>& Tq) {
+    const T pi = T(3.14159265358979323846);
+    const T mu = k.mu_f;
+    const T dl = delta > dmin ? delta : dmin;
+    const Vec3<T> un = dot(uij, n) * n;
+    const Vec3<T> ut = uij - un;
+    T c_n, c_ftt, c_ttt, c_ftr, c_ttr;
+    Vec3<T> om_ftr, om_ttr;
+    if (Rj <= T(0)) {
+        c_n = T(1); c_ftt = T(8.0 / 15.0); c_ttt = T(1.0 / 10.0); c_ftr = T(2.0 / 15.0); c_ttr = T(2.0 / 5.0);
         om_ftr = omi;
         om_ttr = omi;
     } else if (Rj == Ri) {
         // k = 1: the coefficients below are exact binary fractions or the
         // correctly rounded quotients the general formulas give
-        c_n = 0.25; c_ftt = 1.0 / 6.0; c_ttt = 0.125; c_ftr = 1.0 / 30.0; c_ttr = 0.2;
-        const V3 oms = omi + omj;
-        om_ftr = oms + 4.0 * omi + 4.0 * omj;
-        om_ttr = omi + 0.25 * omj;
+        c_n = T(0.25); c_ftt = T(1.0 / 6.0); c_ttt = T(0.125); c_ftr = T(1.0 / 30.0); c_ttr = T(0.2);
+        const Vec3<T> oms = omi + omj;
+        om_ftr = oms + T(4) * omi + T(4) * omj;
+        om_ttr = omi + T(0.25) * omj;
     } else {
-        const double k = Rj / Ri;
-        const double k1 = 1.0 + k;
-        const double i1 = 1.0 / k1;
-        const double i2 = i1 * i1;
-        c_n = k * k * i2;
-        c_ftt = 4.0 * k * (2.0 + k + 2.0 * k * k) * (i2 * i1) * (1.0 / 15.0);
-        c_ttt = k * (4.0 + k) * i2 * 0.1;
-        c_ftr = 2.0 * k * k * i2 * (1.0 / 15.0);
-        c_ttr = 2.0 * k * i1 * 0.2;
-        const V3 oms = omi + omj;
-        om_ftr = oms + (4.0 * Ri / Rj) * omi + (4.0 * k) * omj;
-        om_ttr = omi + (k * 0.25) * omj;
+        const T kr = Rj / Ri;
+        const T k1 = T(1) + kr;
+        const T i1 = T(1) / k1;
+        const T i2 = i1 * i1;
+        c_n = kr * kr * i2;
+        c_ftt = T(4) * kr * (T(2) + kr + T(2) * kr * kr) * (i2 * i1) * T(1.0 / 15.0);
+        c_ttt = kr * (T(4) + kr) * i2 * T(0.1);
+        c_ftr = T(2) * kr * kr * i2 * T(1.0 / 15.0);
+        c_ttr = T(2) * kr * i1 * T(0.2);
+        const Vec3<T> oms = omi + omj;
+        om_ftr = oms + (T(4) * Ri / Rj) * omi + (T(4) * kr) * omj;
+        om_ttr = omi + (kr * T(0.25)) * omj;
     }
-    if (delta > 0.0 && delta < p.cut_n)
-        F = F + (-6.0 * pi * mu * Ri * Ri * c_n * (1.0 / dl - p.inv_cut_n)) * un;
-    const bool tt = p.tangential && delta > 0.0 && delta < p.cut_tt;
-    const bool tr = p.tangential && delta > 0.0 && delta < p.cut_tr;
+    if (delta > T(0) && delta < k.cut_n)
+        F = F + (T(-6) * pi * mu * Ri * Ri * c_n * (T(1) / dl - k.inv_cut_n)) * un;
+    const bool tt = tangential && delta > T(0) && delta < k.cut_tt;
+    const bool tr = tangential && delta > T(0) && delta < k.cut_tr;
     if (tt || tr) {
-        const double lg_tt = log(dl * p.inv_cut_tt);
-        const double lg_tr = p.cut_tr == p.cut_tt ? lg_tt : log(dl * p.inv_cut_tr);
+        const T lg_tt = tlog(dl * k.inv_cut_tt);
+        const T lg_tr = k.cut_tr == k.cut_tt ? lg_tt : tlog(dl * k.inv_cut_tr);
         if (tt) {
-            F = F + (6.0 * pi * mu * Ri * c_ftt * lg_tt) * ut;
-            T = T + (8.0 * pi * mu * Ri * Ri * c_ttt * lg_tt) * cross(uij, n);
+            F = F + (T(6) * pi * mu * Ri * c_ftt * lg_tt) * ut;
+            Tq = Tq + (T(8) * pi * mu * Ri * Ri * c_ttt * lg_tt) * cross(uij, n);
         }
         if (tr) {
-            F = F + (-6.0 * pi * mu * Ri * Ri * c_ftr * lg_tr) * cross(om_ftr, n);
-            T = T + (8.0 * pi * mu * Ri * Ri * Ri * c_ttr * lg_tr) * (om_ttr - dot(om_ttr, n) * n);
+            F = F + (T(-6) * pi * mu * Ri * Ri * c_ftr * lg_tr) * cross(om_ftr, n);
+            Tq = Tq + (T(8) * pi * mu * Ri * Ri * Ri * c_ttr * lg_tr) * (om_ttr - dot(om_ttr, n) * n);
         }
     }
 }
 
 // normal + Coulomb-limited tangential contact force on i, Eqs. (41)-(50)
-__device__ void contact_force(const DemParams& p, V3 n, double delta, V3 ucp, V3 uij, double m_eff,
-                              double Tc, V3 dt_old, V3& Fn, V3& Ft, V3& dt_new) {
-    const double iT = 1.0 / Tc;
-    const double kn = m_eff * p.pi2_log_e2 * (iT * iT);
-    const double dn = -2.0 * m_eff * p.log_e * iT;
-    const double kt = p.kappa * kn, dtg = p.sqrt_kappa * dn;
-    const V3 un = dot(uij, n) * n;
-    const V3 ut = ucp - un;
+template <typename T>
+__device__ void contact_force(const DemConsts<T>& k, Vec3<T> n, T delta, Vec3<T> ucp, Vec3<T> uij, T m_eff,
+                              T Tc, Vec3<T> dt_old, Vec3<T>& Fn, Vec3<T>& Ft, Vec3<T>& dt_new) {
+    const T iT = T(1) / Tc;
+    const T kn = m_eff * k.pi2_log_e2 * (iT * iT);
+    const T dn = T(-2) * m_eff * k.log_e * iT;
+    const T kt = k.kappa * kn, dtg = k.sqrt_kappa * dn;
+    const Vec3<T> un = dot(uij, n) * n;
+    const Vec3<T> ut = ucp - un;
     Fn = (-kn * delta) * n - dn * un;
-    const V3 proj = dt_old - dot(dt_old, n) * n;
-    const double lp = sqrt(dot(proj, proj));
-    const V3 rot = lp > 0.0 ? (sqrt(dot(dt_old, dt_old)) / lp) * proj : mk(0, 0, 0);
-    const V3 Fsd = (-kt) * rot - dtg * ut;
-    const double fc = p.mu_p * sqrt(dot(Fn, Fn));
-    const double lsd = sqrt(dot(Fsd, Fsd));
+    const Vec3<T> proj = dt_old - dot(dt_old, n) * n;
+    const T lp = tsqrt(dot(proj, proj));
+    const Vec3<T> rot = lp > T(0) ? (tsqrt(dot(dt_old, dt_old)) / lp) * proj : zero3<T>();
+    const Vec3<T> Fsd = (-kt) * rot - dtg * ut;
+    const T fc = k.mu_p * tsqrt(dot(Fn, Fn));
+    const T lsd = tsqrt(dot(Fsd, Fsd));
     if (lsd < fc) {
         Ft = Fsd;
-        dt_new = rot + p.dt * ut;
+        dt_new = rot + k.dt * ut;
     } else {
-        const V3 t = lsd > 0.0 ? (1.0 / lsd) * Fsd : mk(0, 0, 0);
+        const Vec3<T> t = lsd > T(0) ? (T(1) / lsd) * Fsd : zero3<T>();
         Ft = fc * t;
-        dt_new = (-1.0 / kt) * (fc * t + dtg * ut);
+        dt_new = (T(-1) / kt) * (fc * t + dtg * ut);
     }
 }
 
-__device__ __forceinline__ double collision_time(double diameter, double Tc) {
-    return Tc > 0.0 ? Tc : 2.31 * diameter * 1.7320508075688772;
+template <typename T>
+__device__ __forceinline__ T collision_time(T diameter, T Tc) {
+    return Tc > T(0) ? Tc : T(2.31) * diameter * T(1.7320508075688772);
+}
+
+// periodic shift (0 or -+n) that takes the separation of a close pair to its
+// minimum image, decided on the float32 copy of the separation
+__device__ __forceinline__ double image_shift(float d, int n, int per) {
+    if (per) {
+        const float half = 0.5f * (float)n;
+        if (d > half) return -(double)n;
+        if (d < -half) return (double)n;
+    }
+    return 0.0;
 }
 
 // Force and torque on particle i from its neighbour j (lubrication,
 // Eqs. (25)-(33), and contact, Eqs. (39)-(50)) at the subcycle's positions;
-// contact = the spring of the pair continues, dnew its new value.
-__device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, int j, V3& F, V3& T, bool& contact,
-                                           V3& dnew) {
+// contact = the spring of the pair continues, dnew its new value. T = double:
+// all in float64. T = float: the separation and |d|^2 - (Ri + Rj)^2 in
+// float64 (the overlap delta = that / (|d| + Ri + Rj) keeps float32 relative
+// accuracy), the interaction laws in float32.
+template <typename T>
+__device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, int j, Vec3<T>& F, Vec3<T>& Tq,
+                                           bool& contact, Vec3<T>& dnew) {
     const Particles& P = p.P;
+    const DemConsts<T>& k = consts<T>(p);
     const double* X = P.xs[cur];
-    const double* Uv = P.us[cur];
-    const double* Om = P.oms[cur];
     const V3 xi = ld3(X, i), xj = ld3(X, j);
-    const V3 d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
-                    mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
-    const double dist = sqrt(dot(d, d));
-    const double Ri = P.R[i], Rj = P.R[j];
-    const double delta = dist - (Ri + Rj);
-    F = mk(0, 0, 0);
-    T = mk(0, 0, 0);
-    contact = false;
-    dnew = mk(0, 0, 0);
-    if (delta >= p.cut_max && delta >= 0.0) return;
-    const V3 n = (1.0 / dist) * d;
-    const V3 ui = ld3(Uv, i), omi = ld3(Om, i), uj = ld3(Uv, j), omj = ld3(Om, j);
-    const V3 uij = ui - uj;
-    if (p.lubrication) {
-        const double Rm = 0.5 * (Ri + Rj);
-        const double dmin = (p.min_a + p.min_b * Rm) * Rm;
-        lubrication_on_i(p, Ri, Rj, delta, n, uij, omi, omj, dmin, F, T);
+    Vec3<T> d;
+    T dist, delta, Ri, Rj;
+    if constexpr (sizeof(T) == 8) {
+        d = mk(mimg(xi.x - xj.x, p.g.n[0], p.g.per[0]), mimg(xi.y - xj.y, p.g.n[1], p.g.per[1]),
+               mimg(xi.z - xj.z, p.g.n[2], p.g.per[2]));
+        dist = sqrt(dot(d, d));
+        Ri = P.R[i];
+        Rj = P.R[j];
+        delta = dist - (Ri + Rj);
+    } else {
+        const float* Xf = P.xfs[cur];
+        V3 dd = xi - xj;
+        dd.x += image_shift(Xf[3 * i] - Xf[3 * j], p.g.n[0], p.g.per[0]);
+        dd.y += image_shift(Xf[3 * i + 1] - Xf[3 * j + 1], p.g.n[1], p.g.per[1]);
+        dd.z += image_shift(Xf[3 * i + 2] - Xf[3 * j + 2], p.g.n[2], p.g.per[2]);
+        const double S = P.R[i] + P.R[j];
+        const double e = fma(-S, S, dot(dd, dd));
+        d = cvt3<float>(dd);
+        dist = sqrtf(dot(d, d));
+        Ri = P.view[i].R;
+        Rj = P.view[j].R;
+        delta = (float)e / (dist + (float)S);
     }
-    if (delta < 0.0) {
-        const V3 ri = (-0.5) * d, rj = 0.5 * d;
-        const V3 ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
-        const double mi = P.m[i], mj = P.m[j];
-        const double m_eff = mi * mj / (mi + mj);
-        const double Tc = collision_time(Ri + Rj, p.Tc);
-        V3 old = mk(0, 0, 0);
+    F = zero3<T>();
+    Tq = zero3<T>();
+    contact = false;
+    dnew = zero3<T>();
+    if (delta >= k.cut_max && delta >= T(0)) return;
+    const Vec3<T> n = (T(1) / dist) * d;
+    Vec3<T> ui, omi, uj, omj;
+    if constexpr (sizeof(T) == 8) {
+        ui = ld3(P.us[cur], i); omi = ld3(P.oms[cur], i); uj = ld3(P.us[cur], j); omj = ld3(P.oms[cur], j);
+    } else {
+        ui = ld3(P.ufs[cur], i); omi = ld3(P.omfs[cur], i); uj = ld3(P.ufs[cur], j); omj = ld3(P.omfs[cur], j);
+    }
+    const Vec3<T> uij = ui - uj;
+    if (p.lubrication) {
+        const T Rm = T(0.5) * (Ri + Rj);
+        const T dmin = (k.min_a + k.min_b * Rm) * Rm;
+        lubrication_on_i<T>(k, p.tangential, Ri, Rj, delta, n, uij, omi, omj, dmin, F, Tq);
+    }
+    if (delta < T(0)) {
+        const Vec3<T> ri = T(-0.5) * d, rj = T(0.5) * d;
+        const Vec3<T> ucp = (ui + cross(omi, ri)) - (uj + cross(omj, rj));
+        const T mi = (T)P.m[i], mj = (T)P.m[j];
+        const T m_eff = mi * mj / (mi + mj);
+        const T Tc = collision_time<T>(Ri + Rj, k.Tc);
+        Vec3<T> old = zero3<T>();
         const int nin = P.hist_n[p.hin][i];
         for (int h = 0; h < nin; ++h)
             if (P.hist_id[p.hin][i * NBR_CAP + h] == j) {
                 const double* s = P.hist_d[p.hin] + 3 * (i * NBR_CAP + h);
-                old = mk(s[0], s[1], s[2]);
+                old = Vec3<T>{(T)s[0], (T)s[1], (T)s[2]};
                 break;
             }
-        V3 Fn, Ft;
-        contact_force(p, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
+        Vec3<T> Fn, Ft;
+        contact_force<T>(k, n, delta, ucp, uij, m_eff, Tc, old, Fn, Ft, dnew);
         F = F + (Fn + Ft);
-        T = T + cross(ri, Ft);
+        Tq = Tq + cross(ri, Ft);
         contact = true;
     }
 }
@@ -396,6 +464,7 @@ __device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, i
 constexpr int PPB = 32;          // particles per block
 constexpr int PAIR_CHUNK = 128;  // queued pairs evaluated per pass of the block
 
+template <typename T>
 __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
     const Particles& P = p.P;
     const int tid = threadIdx.x;
@@ -404,8 +473,8 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     const int hout = p.hout;
     __shared__ unsigned short s_queue[PPB * NBR_CAP];   // pl << 5 | slot
     __shared__ int s_off[PPB + 1];
-    __shared__ double s_res[PAIR_CHUNK][6];
-    __shared__ double s_sum[PPB][6];
+    __shared__ T s_res[PAIR_CHUNK][6];
+    __shared__ T s_sum[PPB][6];
     const float* Xf = P.xfs[cur];
     const unsigned FULL = 0xffffffffu;
 
@@ -432,8 +501,8 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     mask |= __shfl_xor_sync(FULL, mask, 1);
     mask |= __shfl_xor_sync(FULL, mask, 2);
     if (sub == 0) s_off[pl] = __popc(mask);
-    if (tid < 6 * PPB) reinterpret_cast<double*>(s_sum)[tid] = 0.0;
-    if (tid + 128 < 6 * PPB) reinterpret_cast<double*>(s_sum)[tid + 128] = 0.0;
+    if (tid < 6 * PPB) reinterpret_cast<T*>(s_sum)[tid] = T(0);
+    if (tid + 128 < 6 * PPB) reinterpret_cast<T*>(s_sum)[tid + 128] = T(0);
     __syncthreads();
     if (tid < 32) {   // exclusive prefix over the 32 particles
         const int c = s_off[tid];
@@ -469,17 +538,17 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
             const int ep = q >> 5, k = q & 31;
             const int ei = blockIdx.x * PPB + ep;
             const int j = P.nbr[ei * NBR_CAP + k];
-            V3 F, T, dnew;
+            Vec3<T> F, Tq, dnew;
             bool contact;
-            pair_force(p, cur, ei, j, F, T, contact, dnew);
+            pair_force<T>(p, cur, ei, j, F, Tq, contact, dnew);
             s_res[tid][0] = F.x; s_res[tid][1] = F.y; s_res[tid][2] = F.z;
-            s_res[tid][3] = T.x; s_res[tid][4] = T.y; s_res[tid][5] = T.z;
+            s_res[tid][3] = Tq.x; s_res[tid][4] = Tq.y; s_res[tid][5] = Tq.z;
             if (!init) {
                 // tangential spring of this neighbour slot for the next subcycle
                 P.hist_id[hout][ei * NBR_CAP + k] = contact ? j : -1;
                 if (contact) {
                     double* sd = P.hist_d[hout] + 3 * (ei * NBR_CAP + k);
-                    sd[0] = dnew.x; sd[1] = dnew.y; sd[2] = dnew.z;
+                    sd[0] = (double)dnew.x; sd[1] = (double)dnew.y; sd[2] = (double)dnew.z;
                 }
             }
         }
@@ -498,55 +567,66 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     const double* X = P.xs[cur];
     const double* Uv = P.us[cur];
     const double* Om = P.oms[cur];
-    V3 F = mk(s_sum[tid][0], s_sum[tid][1], s_sum[tid][2]);
-    V3 T = mk(s_sum[tid][3], s_sum[tid][4], s_sum[tid][5]);
+    Vec3<T> F = {s_sum[tid][0], s_sum[tid][1], s_sum[tid][2]};
+    Vec3<T> Tq = {s_sum[tid][3], s_sum[tid][4], s_sum[tid][5]};
     {
         // plane walls on the faces of non-periodic axes
-        const V3 xi = ld3(X, ip), ui = ld3(Uv, ip), omi = ld3(Om, ip);
-        const double Ri = P.R[ip], mi = P.m[ip];
-        const double xa[3] = {xi.x, xi.y, xi.z};
+        const DemConsts<T>& k = consts<T>(p);
+        const V3 xd = ld3(X, ip);
+        Vec3<T> ui, omi;
+        if constexpr (sizeof(T) == 8) {
+            ui = ld3(Uv, ip);
+            omi = ld3(Om, ip);
+        } else {
+            ui = ld3(P.ufs[cur], ip);
+            omi = ld3(P.omfs[cur], ip);
+        }
+        const double Rid = P.R[ip];
+        const T Ri = (T)Rid, mi = (T)P.m[ip];
+        const double xa[3] = {xd.x, xd.y, xd.z};
         for (int a = 0; a < 3; ++a) {
             if (p.g.per[a]) continue;
             for (int side = 0; side < 2; ++side) {
                 const int face = 2 * a + side;
-                V3 nw = mk(0, 0, 0);
-                const double sgn = side == 0 ? 1.0 : -1.0;
+                Vec3<T> nw = zero3<T>();
+                const T sgn = side == 0 ? T(1) : T(-1);
                 if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
                 const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
-                const double delta = (xa[a] - xw) * sgn - Ri;
+                const T delta = (T)((xa[a] - xw) * (side == 0 ? 1.0 : -1.0) - Rid);
                 const double* uwp = p.g.wall_vel[side][a];
-                const V3 uw = mk(uwp[0], uwp[1], uwp[2]);
-                const V3 uij = ui - uw;
+                const Vec3<T> uw = {(T)uwp[0], (T)uwp[1], (T)uwp[2]};
+                const Vec3<T> uij = ui - uw;
                 if (p.lubrication) {
-                    const double dmin = (p.min_a + p.min_b * Ri) * Ri;
-                    lubrication_on_i(p, Ri, -1.0, delta, nw, uij, omi, mk(0, 0, 0), dmin, F, T);
+                    const T dmin = (k.min_a + k.min_b * Ri) * Ri;
+                    lubrication_on_i<T>(k, p.tangential, Ri, T(-1), delta, nw, uij, omi, zero3<T>(), dmin, F, Tq);
                 }
                 if (!init) P.wact[hout][6 * ip + face] = 0;
-                if (delta < 0.0) {
-                    const V3 ri = (-(Ri + 0.5 * delta)) * nw;
-                    const V3 ucp = (ui + cross(omi, ri)) - uw;
-                    const double Tc = collision_time(2.0 * Ri, p.Tc);
-                    V3 old = mk(0, 0, 0);
+                if (delta < T(0)) {
+                    const Vec3<T> ri = (-(Ri + T(0.5) * delta)) * nw;
+                    const Vec3<T> ucp = (ui + cross(omi, ri)) - uw;
+                    const T Tc = collision_time<T>(T(2) * Ri, k.Tc);
+                    Vec3<T> old = zero3<T>();
                     if (P.wact[p.hin][6 * ip + face]) {
                         const double* sd = P.whist[p.hin] + 3 * (6 * ip + face);
-                        old = mk(sd[0], sd[1], sd[2]);
+                        old = Vec3<T>{(T)sd[0], (T)sd[1], (T)sd[2]};
                     }
-                    V3 Fn, Ft, dnew;
-                    contact_force(p, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
+                    Vec3<T> Fn, Ft, dnew;
+                    contact_force<T>(k, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
                     F = F + (Fn + Ft);
-                    T = T + cross(ri, Ft);
+                    Tq = Tq + cross(ri, Ft);
                     if (!init) {
                         double* sd = P.whist[hout] + 3 * (6 * ip + face);
-                        sd[0] = dnew.x; sd[1] = dnew.y; sd[2] = dnew.z;
+                        sd[0] = (double)dnew.x; sd[1] = (double)dnew.y; sd[2] = (double)dnew.z;
                         P.wact[hout][6 * ip + face] = 1;
                     }
                 }
             }
         }
     }
-    const V3 Fs = mk(F.x + P.fbar[6 * ip] + P.ext[3 * ip], F.y + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
-                     F.z + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
-    const V3 Ts = mk(T.x + P.fbar[6 * ip + 3], T.y + P.fbar[6 * ip + 4], T.z + P.fbar[6 * ip + 5]);
+    const V3 Fd = cvt3<double>(F), Td = cvt3<double>(Tq);
+    const V3 Fs = mk(Fd.x + P.fbar[6 * ip] + P.ext[3 * ip], Fd.y + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
+                     Fd.z + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
+    const V3 Ts = mk(Td.x + P.fbar[6 * ip + 3], Td.y + P.fbar[6 * ip + 4], Td.z + P.fbar[6 * ip + 5]);
     if (init) {
         st3(P.F_prev, ip, Fs);
         st3(P.T_prev, ip, Ts);
@@ -564,6 +644,12 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     const int nxt = 1 - cur;
     st3(P.us[nxt], ip, u);
     st3(P.oms[nxt], ip, om);
+    if constexpr (sizeof(T) == 4) {
+        for (int d = 0; d < 3; ++d) {
+            P.ufs[nxt][3 * ip + d] = (float)(d == 0 ? u.x : d == 1 ? u.y : u.z);
+            P.omfs[nxt][3 * ip + d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
+        }
+    }
     const double ua[3] = {u.x, u.y, u.z};
     const double Fa[3] = {Fs.x, Fs.y, Fs.z};
     const double c = p.dt * cu;
@@ -594,7 +680,8 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
 
 void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st) {
     if (p.P.n == 0) return;
-    subcycle_kernel<<<(p.P.n + PPB - 1) / PPB, 128, 0, st>>>(p, cur, init, last);
+    if (p.pair_f32) subcycle_kernel<float><<<(p.P.n + PPB - 1) / PPB, 128, 0, st>>>(p, cur, init, last);
+    else subcycle_kernel<double><<<(p.P.n + PPB - 1) / PPB, 128, 0, st>>>(p, cur, init, last);
 }
 
 // copy state buffer 1 into buffer 0 (after an odd number of subcycles)

@@ -99,6 +99,13 @@ struct FinalizeParams {
 };
 void launch_finalize(const FinalizeParams& p, cudaStream_t st);
 
+// interaction constants of the DEM in the precision of its pair arithmetic
+template <typename T>
+struct DemConsts {
+    T mu_f, cut_n, cut_tt, cut_tr, cut_max, inv_cut_n, inv_cut_tt, inv_cut_tr, min_a, min_b;
+    T log_e, pi2_log_e2, kappa, sqrt_kappa, mu_p, Tc, dt;
+};
+
 struct DemParams {
     Geom g;
     Particles P;
@@ -115,6 +122,11 @@ struct DemParams {
     int lubrication, tangential;
     double dt;              // subcycle time step 1/n_sub
     int hin, hout;          // history buffers to read and write
+    // 1: pair and wall laws in float32 (separations and overlaps from the
+    // float64 positions), 0: all in float64
+    int pair_f32;
+    DemConsts<double> kd;
+    DemConsts<float> kf;
     int* status;
 };
 void launch_bins(const DemParams& p, cudaStream_t st);
