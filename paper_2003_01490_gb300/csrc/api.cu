@@ -801,19 +801,32 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     lp.accel_d = ctx->accel;
     lp.accel_f = ctx->accel_f;
     launch_boundary(lp, sm, BC_ACCEL);
-    if (lp.missing_links) {
-        // the missing links run beside the dense kernel on the side stream
-        // (their sums commute with the dense kernel's); finalize waits for both
+    // beside the dense kernel, on the side stream: the missing links (their
+    // sums commute with the dense kernel's) and the DEM's neighbour lists,
+    // which read only the positions the dense kernel reads too; finalize
+    // waits for both streams
+    const bool side = lp.missing_links || move;
+    if (side) {
         CK(cudaEventRecord(ctx->ev_fork, sm));
         CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
-        launch_boundary(lp, ctx->side_stream, BC_LINKS);
+        if (lp.missing_links) {
+            launch_boundary(lp, ctx->side_stream, BC_LINKS);
+            ctx->launches += 1;
+        }
+        if (move) {
+            dp.P = ctx->P;
+            CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2],
+                               ctx->side_stream));
+            launch_bins(dp, ctx->side_stream);
+            launch_neighbours(dp, ctx->side_stream);
+            ctx->launches += 2;
+        }
         CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
-        ctx->launches += 1;
     }
     CK(prof_mark(ctx));
     launch_stream_collide(lp, sm);
     CK(prof_mark(ctx));
-    if (lp.missing_links) CK(cudaStreamWaitEvent(sm, ctx->ev_join, 0));
+    if (side) CK(cudaStreamWaitEvent(sm, ctx->ev_join, 0));
     FinalizeParams fpp{};
     fpp.P = ctx->P;
     fpp.use_fixed = ctx->storage != LBM_STORE_F64;
@@ -824,12 +837,8 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     CK(prof_mark(ctx));
     if (move) {
         // Algorithm 1, lines 4-10: DEM subcycles
-        dp.P = ctx->P;
-        CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
-        launch_bins(dp, sm);
-        launch_neighbours(dp, sm);
         launch_dem_position(dp, sm);
-        ctx->launches += 3;
+        ctx->launches += 1;
         int cur = 0;
         for (int s = 0; s < d.n_sub; ++s) {
             dp.hin = ctx->hcur;

@@ -560,15 +560,17 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
         }
         __syncthreads();
     }
-    // pass 3: one thread per particle
-    if (tid >= PPB) return;
-    const int ip = blockIdx.x * PPB + tid;
+    // pass 3: one thread per particle, lanes 0-7 of each warp (the float64
+    // work of the block spread over the four schedulers)
+    if ((tid & 31) >= PPB / 4) return;
+    const int pl3 = (tid >> 5) * (PPB / 4) + (tid & 31);
+    const int ip = blockIdx.x * PPB + pl3;
     if (ip >= P.n) return;
     const double* X = P.xs[cur];
     const double* Uv = P.us[cur];
     const double* Om = P.oms[cur];
-    Vec3<T> F = {s_sum[tid][0], s_sum[tid][1], s_sum[tid][2]};
-    Vec3<T> Tq = {s_sum[tid][3], s_sum[tid][4], s_sum[tid][5]};
+    Vec3<T> F = {s_sum[pl3][0], s_sum[pl3][1], s_sum[pl3][2]};
+    Vec3<T> Tq = {s_sum[pl3][3], s_sum[pl3][4], s_sum[pl3][5]};
     {
         // plane walls on the faces of non-periodic axes
         const DemConsts<T>& k = consts<T>(p);
