@@ -160,16 +160,19 @@ __device__ __forceinline__ float short_axis_image(float n, float g, int L) {
     return tw > fl ? n - fl : (tw < -fl ? n + fl : n);
 }
 
-// One block per 32x4x4 tile, 128 threads; thread (x, y) handles the column
-// of the tile's four z cells. Per candidate the shared arrays hold the
-// integer offset n0 of the tile's first cell from the particle's base cell
-// (as an exact float; on long periodic axes already moved to the image
-// nearest to the tile), the common fractional offset g = 1/2 - frac, R^2 and
-// the thresholds of the shell and near tests with their float32 tolerances.
-// A cell's offset is (n0 + l) + g with the integer part formed first, so no
-// float32 intermediate is larger than the offset itself. Each warp first
-// drops the candidates that cannot reach its 32 x 1 x 4 cells.
+// One block per 32x4x4 tile, 128 threads; warp w takes the 8x4x4 brick of
+// x in [8w, 8w + 8) (a compact brick meets fewer spheres than a 32-cell row),
+// lane l the column x = 8w + (l & 7), y = l >> 3 of its four z cells. Per
+// candidate the shared arrays hold the integer offset n0 of the tile's first
+// cell from the particle's base cell (as an exact float; on long periodic
+// axes already moved to the image nearest to the tile), the common fractional
+// offset g = 1/2 - frac, R^2 and the thresholds of the shell and near tests
+// with their float32 tolerances. A cell's offset is (n0 + l) + g with the
+// integer part formed first, so no float32 intermediate is larger than the
+// offset itself. Each warp first drops the candidates that cannot reach its
+// brick.
 __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __grid_constant__ MapParams p) {
+    static_assert(TILE_X == 32 && TILE_Y == 4, "four 8x4 column bricks per tile");
     __shared__ float4 cn[TILE_CAP];
     __shared__ float4 ca[TILE_CAP];
     __shared__ float4 cb[TILE_CAP];
@@ -177,8 +180,8 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     __shared__ unsigned int s_solid[4];
     __shared__ unsigned int s_base;
     const long long t = ((long long)blockIdx.z * p.ntile[1] + blockIdx.y) * p.ntile[0] + blockIdx.x;
-    const int lx = threadIdx.x, ly = threadIdx.y;
-    const int tid = lx + TILE_X * ly, warp = ly;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lx = 8 * warp + (lane & 7), ly = lane >> 3;
     const int org[3] = {(int)blockIdx.x * TILE_X, (int)blockIdx.y * TILE_Y, (int)blockIdx.z * TILE_Z};
     const int x = org[0] + lx, y = org[1] + ly;
     const int nx = p.g.n[0], ny = p.g.n[1], nz = p.g.n[2];
@@ -224,22 +227,24 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
 
     const bool any_small = p.small[0] | p.small[1] | p.small[2];
     const float flx = (float)lx, fly = (float)ly;
-    // candidates that may reach this warp's cells (conservative float bound)
+    const float bx0 = (float)(8 * warp);
+    // candidates that may reach this warp's brick (conservative float bound)
     unsigned relm[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int k = (threadIdx.x & 31) + 32 * h;
+        const int k = lane + 32 * h;
         bool rel = false;
         if (k < ncand) {
             if (any_small) {
                 rel = true;
             } else {
                 const float4 Nn = cn[k], A = ca[k], B = cb[k];
-                const float xlo = Nn.x + A.x, xhi = (Nn.x + (float)(TILE_X - 1)) + A.x;
+                const float xlo = (Nn.x + bx0) + A.x, xhi = (Nn.x + (bx0 + 7.0f)) + A.x;
+                const float ylo = Nn.y + A.y, yhi = (Nn.y + (float)(TILE_Y - 1)) + A.y;
                 const float zlo = Nn.z + A.z, zhi = (Nn.z + (float)(TILE_Z - 1)) + A.z;
                 const float dx = xlo > 0.f ? xlo : (xhi < 0.f ? -xhi : 0.f);
+                const float dy = ylo > 0.f ? ylo : (yhi < 0.f ? -yhi : 0.f);
                 const float dz = zlo > 0.f ? zlo : (zhi < 0.f ? -zhi : 0.f);
-                const float dy = (Nn.y + fly) + A.y;
                 const float reach = fmaxf(B.y, B.x + B.w) * 1.0001f + 0.01f;
                 rel = dx * dx + dy * dy + dz * dz <= reach;
             }
@@ -248,7 +253,8 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     }
 
     int own[TILE_Z];
-    unsigned shell4 = 0, nnear4 = 0;   // per z: shell bit; near count (saturating at 2) in 2 bits
+    unsigned shell4 = 0;               // per z: shell bit
+    unsigned near1 = 0, near2 = 0;     // per z: near one / two particles
     unsigned multi4 = 0;               // per z: inside a second sphere
 #pragma unroll
     for (int j = 0; j < TILE_Z; ++j) own[j] = 0x7fffffff;
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
             }
             const float dx = fx + A.x, dy = fy + A.y;
             const float sxy = dx * dx + dy * dy;
+            const float far2 = B.x + B.w;
 #pragma unroll
             for (int j = 0; j < TILE_Z; ++j) {
                 float fz = Nn.z + (float)j;
@@ -274,10 +281,10 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
                 const float dz = fz + A.z;
                 const float d2f = sxy + dz * dz;
                 if (d2f <= B.y) {
-                    const unsigned cur = (nnear4 >> (2 * j)) & 3u;
-                    if (cur < 2u) nnear4 += 1u << (2 * j);
+                    near2 |= near1 & (1u << j);
+                    near1 |= 1u << j;
                 }
-                if (d2f > B.x + B.w) continue;
+                if (d2f > far2) continue;
                 const bool exact_needed = fabsf(d2f - A.w) <= B.z || fabsf(d2f - B.x) <= B.w;
                 bool inside, in_shell;
                 if (!exact_needed) {
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
         if (!valid_xy || z >= nz) continue;
         const long long idx = idx0 + j * plane;
         const bool wall_adj = wall_xy || (!p.g.per[2] && (z == 0 || z == nz - 1));
-        const unsigned nn = (nnear4 >> (2 * j)) & 3u;
+        const unsigned nn = ((near1 >> j) & 1u) + ((near2 >> j) & 1u);
         const uint8_t old = (uint8_t)(old4 >> (8 * j));
         uint8_t nf = 0;
         if (own[j] != 0x7fffffff) {
@@ -347,7 +354,6 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
 
     // block-aggregated append to the missing-link list and solid count
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned mb[TILE_Z];
     unsigned wm = 0, ws = 0;
@@ -390,9 +396,8 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
 }
 
 void launch_map(const MapParams& p, cudaStream_t st) {
-    dim3 block(TILE_X, TILE_Y, 1);
     dim3 grid(p.ntile[0], p.ntile[1], p.ntile[2]);
-    map_kernel<<<grid, block, 0, st>>>(p);
+    map_kernel<<<grid, TILE_X * TILE_Y, 0, st>>>(p);
 }
 
 __global__ void solid_markers_kernel(const __grid_constant__ MapParams p) {
