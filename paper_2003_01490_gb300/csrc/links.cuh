@@ -7,21 +7,14 @@
 
 namespace lbmdem {
 
-// float -> fixed point with scale 2^32 using float32 and int32 operations only;
-// exact up to the final rounding at 2^-32. |v| must stay below 2^31.
+// float -> fixed point with scale 2^32: v 2^32 is exact in float32 and
+// rounds to the nearest 64-bit integer. |v| must stay below 2^31.
 __device__ __forceinline__ long long to_fixed(float v, int* status) {
-    float hi = truncf(v);
-    float r1 = (v - hi) * 65536.0f;
-    float mid = truncf(r1);
-    float r2 = (r1 - mid) * 65536.0f;
-    if (!(fabsf(hi) < 2147483520.0f)) {
+    if (!(fabsf(v) < 2147483520.0f)) {
         atomicOr(status, ST_FIXED_OVERFLOW);
         return 0;
     }
-    unsigned long long h = (unsigned long long)(long long)__float2int_rz(hi);
-    long long m = (long long)__float2int_rz(mid);
-    long long l = (long long)__float2int_rn(r2);
-    return (long long)(h << 32) + m * 65536LL + l;
+    return __float2ll_rn(v * 4294967296.0f);
 }
 
 // per-lane partial sums of one particle's link forces and torques
