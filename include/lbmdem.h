@@ -137,7 +137,7 @@ lbm_status lbm_create_in_arena(const lbm_grid *grid, const lbm_relax *relax,
 /* Add n spheres (Sec. 2.2 mapping is applied at once). pos, vel, omega: n x 3
  * doubles; radius, density: n doubles, density = rho_p / rho_f. Allowed only
  * before the first lbm_step(). Errors: LBM_ERR_INVALID if a centre lies
- * outside the box, a radius is < 1 cell, a density is <= 0, two spheres
+ * outside the box, a radius is outside [1, 100] cells, a density is <= 0, two spheres
  * overlap (centre distance < R_i + R_j), a sphere crosses a wall or a
  * periodic side is not longer than 2 R + 4 cells (a sphere and its own
  * periodic image would share boundary cells);

@@ -613,7 +613,7 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     double rmax = ctx->r_max;
     for (int k = 0; k < n; ++k) {
         const double R = radius[k], rho = density[k];
-        if (!(R >= 1.0)) return fail(ctx, LBM_ERR_INVALID, "radius must be >= 1 cell");
+        if (!(R >= 1.0 && R <= 100.0)) return fail(ctx, LBM_ERR_INVALID, "radius must be in [1, 100] cells");
         if (!(rho > 0.0)) return fail(ctx, LBM_ERR_INVALID, "density ratio must be > 0");
         for (int a = 0; a < 3; ++a) {
             const double x = pos[3 * k + a];

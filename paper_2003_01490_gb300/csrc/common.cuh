@@ -147,7 +147,7 @@ struct Particles {
     double* T_new;         // [3n]
     double* acc_d;         // [6n] float64 link-force accumulators (F, T)
     long long* acc_i;      // [6n] fixed-point link-force accumulators (float32 kernels)
-    long long* acc_k;      // [6n] exact 36 x (constant link force, its torque about the base cell)
+    long long* acc_k;      // [3n] exact 36 x (constant link force, its torque about the base cell), two per word
     double* fp;            // [6n] F^fp, T^fp of the last step
     double* fp_old;        // [6n] F^fp, T^fp of the step before
     double* fbar;          // [6n] averaged F^fp, T^fp used by the DEM

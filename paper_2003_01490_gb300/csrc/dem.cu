@@ -109,10 +109,15 @@ __global__ void finalize_kernel(const FinalizeParams p) {
         // constant link parts summed exactly by the float32 boundary kernel:
         // K = 36 sum 2 w c and 36 sum 2 w (n x c); torque adds g x (K / 36)
         // with g = 1/2 - (x - floor(x)) the common fractional cell offset
+        // (two components per word: lo + hi 2^32)
         double k[6], g[3];
-        for (int c = 0; c < 6; ++c) {
-            k[c] = (double)p.P.acc_k[6 * i + c] * (1.0 / 36.0);
-            p.P.acc_k[6 * i + c] = 0;
+        for (int c2 = 0; c2 < 3; ++c2) {
+            const unsigned long long w = (unsigned long long)p.P.acc_k[3 * i + c2];
+            const long long lo = (long long)(int)(unsigned)(w & 0xffffffffull);
+            const long long hi = (long long)(w - (unsigned long long)lo) >> 32;
+            k[2 * c2] = (double)lo * (1.0 / 36.0);
+            k[2 * c2 + 1] = (double)hi * (1.0 / 36.0);
+            p.P.acc_k[3 * i + c2] = 0;
         }
         for (int d = 0; d < 3; ++d) {
             const double x = p.P.x[3 * i + d];

@@ -36,8 +36,13 @@ __device__ __forceinline__ void add_float(const Sinks& s, int i, int c, double v
 __device__ __forceinline__ void add_float(const Sinks& s, int i, int c, float v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_i + 6 * i + c), (unsigned long long)to_fixed(v, s.status));
 }
-__device__ __forceinline__ void add_int(const Sinks& s, int i, int c, int v) {
-    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_k + 6 * i + c), (unsigned long long)(long long)v);
+// two exact integer sums (components 2 c2 and 2 c2 + 1) in one 64-bit word,
+// lo + hi 2^32: a particle's totals stay inside 32 bits (radius <= 100), so
+// the halves separate exactly however the adds wrap
+__device__ __forceinline__ void add_int2(const Sinks& s, int i, int c2, int lo, int hi) {
+    if (lo | hi)
+        atomicAdd(reinterpret_cast<unsigned long long*>(s.acc_k + 3 * i + c2),
+                  ((unsigned long long)(long long)hi << 32) + (unsigned long long)(long long)lo);
 }
 
 template <typename T>
@@ -45,7 +50,10 @@ __device__ __forceinline__ void flush(Acc<T>& a, const Sinks& s) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         add_float(s, a.key, c, a.f[c]);
-        if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+        if (sizeof(T) == 4 && (c & 1)) add_int2(s, a.key, c >> 1, a.k[c - 1], a.k[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
         a.f[c] = T(0);
         a.k[c] = 0;
     }
@@ -82,7 +90,7 @@ __device__ __forceinline__ void commit(Acc<T>& a, const Sinks& s) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             add_float(s, a.key, c, a.f[c]);
-            if (sizeof(T) == 4) add_int(s, a.key, c, a.k[c]);
+            if (sizeof(T) == 4 && (c & 1)) add_int2(s, a.key, c >> 1, a.k[c - 1], a.k[c]);
         }
     }
 }
