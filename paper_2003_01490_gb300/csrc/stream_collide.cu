@@ -39,11 +39,10 @@
 #ifndef LBM_SC_MIN_BLOCKS
 #define LBM_SC_MIN_BLOCKS 4
 #endif
-// consecutive z planes marched by one block
 // longest chunk of consecutive z planes marched by one block (shorter when
-// the box is too small to give every SM several blocks)
+// the box is too small to give every SM several blocks); tuned on GB300
 #ifndef LBM_SC_ZCHUNK
-#define LBM_SC_ZCHUNK 16
+#define LBM_SC_ZCHUNK 24
 #endif
 // the same for float64 storage
 #ifndef LBM_SC_MIN_BLOCKS_F64
