@@ -61,13 +61,14 @@ def workload(name, storage=None, seed_offset=0, shape=None, particles=None):
     if name == 'suspension' and shape:
         sh = tuple(int(v) for v in shape.split('x'))
         n = particles or max(1, int(round(0.2696 * sh[0] * sh[1] * sh[2] / (math.pi * 12.0 ** 3 / 6.0))))
-        w = workloads.suspension(shape=sh, n=n, seed=20030149 + seed_offset)
+        w = workloads.suspension(shape=sh, n=n, seed=20030149 + seed_offset, storage=storage or 'f32')
     elif name == 'suspension':
-        w = workloads.suspension(seed=20030149 + seed_offset)
+        w = workloads.suspension(seed=20030149 + seed_offset, storage=storage or 'f32')
     else:
         w = workloads.sphere_wall()
-    if storage:
-        w['storage'] = storage
+        if storage:
+            w['storage'] = storage
+            w['name'] = w['name'].rsplit(', ', 1)[0] + ', ' + storage
     return w
 
 
