@@ -144,7 +144,10 @@ template <> struct PartOps<float> {
         float g[3], C;
         load(a, i, x, y, z, r, n, g, C, R, u, om);
     }
-    // also the fractional offset g and C = |g|^2 - R^2 of the particle
+    // also the fractional offset g and C = |g|^2 - R^2 of the particle. The
+    // image is chosen on the integer offset: a link cell lies within R + 2
+    // cells of the centre on every axis and a periodic side is longer than
+    // 2 R + 4, so exactly one image has |n_d| <= floor(n / 2)
     template <typename A>
     __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float (&g)[3],
                                 float& C, float& R, float (&u)[3], float (&om)[3]) {
@@ -155,10 +158,9 @@ template <> struct PartOps<float> {
             int nd = c[d] - v.base[d];
             g[d] = 0.5f - v.frac[d];
             if (a.g.per[d]) {
-                const float half = 0.5f * (float)a.g.n[d];
-                const float rd = (float)nd + g[d];
-                if (rd > half) nd -= a.g.n[d];
-                else if (rd < -half) nd += a.g.n[d];
+                const int L = a.g.n[d], half = L >> 1;
+                if (nd > half) nd -= L;
+                else if (nd < -half) nd += L;
             }
             n[d] = nd;
             r[d] = (float)nd + g[d];
@@ -200,7 +202,8 @@ __device__ __forceinline__ T link_root(const T (&r)[3], T cc, T c0, T c1, T c2_,
     const T disc = b * b - T(4) * cc2 * cc;
     if (disc < T(0)) return T(0.5);
     const T sq = fast_sqrt(disc);
-    const T t = b < T(0) ? fast_div(T(2) * cc, sq - b) : fast_div(-b - sq, T(2) * cc2);
+    const bool neg = b < T(0);
+    const T t = fast_div(neg ? T(2) * cc : -b - sq, neg ? sq - b : T(2) * cc2);
     return t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
 }
 
