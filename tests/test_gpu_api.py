@@ -55,6 +55,16 @@ def test_wall_crossing_short_periodic_side_and_capacity(L):
     assert e.value.status == L.STATUS_CODES['LBM_ERR_CAPACITY']
 
 
+def test_radius_outside_one_to_hundred_cells_is_rejected(L):
+    # the exact integer link sums of a particle stay inside 32 bits up to R = 100
+    ctx = fresh(L, shape=(208, 208, 208), periodic=(1, 1, 1), max_particles=2)
+    for R in (0.5, 100.5):
+        with pytest.raises(L.LbmError) as e:
+            add(L, ctx, [[104.0, 104.0, 104.0]], [R])
+        assert e.value.status == L.STATUS_CODES['LBM_ERR_INVALID']
+    add(L, ctx, [[104.0, 104.0, 104.0]], [100.0])
+
+
 def test_spheres_only_before_the_first_step(L):
     ctx = fresh(L)
     add(L, ctx, [[10.0, 10.0, 10.0]], [3.0])
