@@ -102,7 +102,12 @@ typedef struct {
     int tangential_lubrication; /* 1 = include Eqs. (30)-(33)                             */
     int force_averaging;   /* 1 = average F^fp, T^fp over two steps (Sec. 4.2)            */
     int fluid_counterforce;/* 1 = fluid body force -sum V (rho_p - 1) g / N_fluid         */
-    int fixed_particles;   /* 1 = particles keep position and velocity (no DEM)           */
+    int fixed_particles;   /* 0 = DEM (Algorithm 1); 1 = particles keep position and
+                              velocity (no DEM); 2 = prescribed motion: each step moves
+                              every particle by its velocity, x += u (Eq. (37) with no
+                              force, one time step), with the velocities the caller set
+                              (lbm_add_spheres, lbm_set_particle_velocity); no DEM
+                              forces; mapping and refill as in Algorithm 1             */
     int missing_links;     /* 1 = missing-link correction F_q = 2 w_q c_q (Sec. 2.2)       */
 } lbm_dem;
 
@@ -159,6 +164,14 @@ lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
 lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *vel,
                                   double *omega, double *force_hyd, double *torque_hyd,
                                   int *n_out);
+
+/* Replace the translational and angular velocities of particles 0 .. n-1
+ * (vel, omega: n x 3 doubles each, either may be NULL), e.g. to prescribe a
+ * particle's motion step by step (Sec. 2.3.3 prescribes the settling velocity
+ * of a sphere this way). The new velocities enter the next step's boundary
+ * condition, position update and refill. Errors: LBM_ERR_INVALID if n is
+ * negative or above the particle count. Synchronises the stream. */
+lbm_status lbm_set_particle_velocity(lbm_ctx *ctx, int n, const double *vel, const double *omega);
 
 /* Copy rho (cells doubles), u (3 x cells doubles, component-major: u_x block,
  * then u_y, then u_z) and flags (cells bytes, LBM_FLAG_* bits) to host

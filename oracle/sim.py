@@ -67,7 +67,7 @@ class Params:
                  mu_p=0.15, n_sub=10, lub_cut_n=2.0 / 3.0, lub_cut_tt=0.5, lub_cut_tr=0.5,
                  lub_min_a=0.001, lub_min_b=0.00007, gravity=(0.0, 0.0, 0.0), lubrication=True,
                  tangential_lubrication=True, force_averaging=True, fluid_counterforce=False,
-                 fixed_particles=False, missing_links=True):
+                 fixed_particles=False, missing_links=True, prescribed_motion=False):
         self.tau = tau
         self.magic = magic
         self.lambda_b_shell = lambda_b_shell
@@ -84,6 +84,9 @@ class Params:
         self.fluid_counterforce = fluid_counterforce
         self.fixed_particles = fixed_particles
         self.missing_links = missing_links
+        # prescribed motion (Sec. 2.3.3 prescribes a sphere's velocity per
+        # step): positions advance by the velocities the caller sets, no DEM
+        self.prescribed_motion = prescribed_motion
 
     def rates(self):
         """Relaxation rates (bulk cells, shell cells) as two S diagonals (Eq. (12))."""
@@ -296,7 +299,7 @@ class Simulation:
     def _step(self):
         p, dom = self.p, self.dom
         N = len(self.R)
-        if self.F_prev is None and N and not p.fixed_particles:
+        if self.F_prev is None and N and not p.fixed_particles and not p.prescribed_motion:
             self.F_prev, self.T_prev = self.dem_forces(np.zeros((N, 3)), np.zeros((N, 3)), 0.0,
                                                        update_history=False)
         self.accel = self.fluid_accel()
@@ -320,8 +323,12 @@ class Simulation:
         ft = self.ft.copy()
         ft[:, fluid] = collide(f[:, fluid], self.accel, s_bulk, s_shell, self.shell[fluid])
         self.ft = ft
-        # Algorithm 1, lines 4-10: DEM subcycles
-        if N and not p.fixed_particles:
+        # Algorithm 1, lines 4-10: DEM subcycles; prescribed motion instead
+        # moves each particle by its velocity over the step (Eq. (37), no force)
+        if N and p.prescribed_motion:
+            self.X = self.X + self.U
+            self.wrap_positions()
+        elif N and not p.fixed_particles:
             self.dem_subcycles(Fbar, Tbar)
         # Algorithm 1, line 11: mapping update and refill
         self.refilled = []

@@ -258,6 +258,8 @@ lbm_status validate(const lbm_grid* g, const lbm_relax* r, const lbm_dem* d, lbm
     if (!(d->mu_p >= 0.0)) return fail(nullptr, LBM_ERR_INVALID, "mu_p must be >= 0");
     if (!(d->lub_cut_n > 0 && d->lub_cut_tt > 0 && d->lub_cut_tr > 0))
         return fail(nullptr, LBM_ERR_INVALID, "lubrication cut-offs must be > 0");
+    if (d->fixed_particles < 0 || d->fixed_particles > 2)
+        return fail(nullptr, LBM_ERR_INVALID, "fixed_particles must be 0 (DEM), 1 (fixed) or 2 (prescribed motion)");
     return LBM_OK;
 }
 
@@ -754,11 +756,14 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     const lbm_relax& r = ctx->relax;
     const lbm_dem& d = ctx->dem;
     const double s_nu = 1.0 / r.tau;
-    const bool move = ctx->P.n > 0 && !d.fixed_particles;
+    // particles move by the DEM (fixed_particles 0) or by their prescribed
+    // velocities (2); both remap and refill
+    const bool move = ctx->P.n > 0 && d.fixed_particles != 1;
+    const bool dem = move && d.fixed_particles == 0;
     const bool first = !ctx->stepped;
     if (first) {
         ctx->stepped = true;
-        if (move) {
+        if (dem) {
             // F(t = 0) for the first Velocity-Verlet position update needs the
             // neighbour lists of the initial positions
             dp.hin = ctx->hcur;
@@ -805,7 +810,7 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     // sums commute with the dense kernel's) and the DEM's neighbour lists,
     // which read only the positions the dense kernel reads too; finalize
     // waits for both streams
-    const bool side = lp.missing_links || move;
+    const bool side = lp.missing_links || dem;
     if (side) {
         CK(cudaEventRecord(ctx->ev_fork, sm));
         CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
@@ -813,7 +818,7 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
             launch_boundary(lp, ctx->side_stream, BC_LINKS);
             ctx->launches += 1;
         }
-        if (move) {
+        if (dem) {
             dp.P = ctx->P;
             CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2],
                                ctx->side_stream));
@@ -836,20 +841,26 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     ctx->launches += 2 + (ctx->P.n > 0 ? 1 : 0);
     CK(prof_mark(ctx));
     if (move) {
-        // Algorithm 1, lines 4-10: DEM subcycles
-        launch_dem_position(dp, sm);
-        ctx->launches += 1;
-        int cur = 0;
-        for (int s = 0; s < d.n_sub; ++s) {
-            dp.hin = ctx->hcur;
-            dp.hout = 1 - ctx->hcur;
-            launch_dem_subcycle(dp, cur, 0, s == d.n_sub - 1, sm);
-            ctx->hcur = 1 - ctx->hcur;
-            cur = 1 - cur;
+        if (dem) {
+            // Algorithm 1, lines 4-10: DEM subcycles
+            launch_dem_position(dp, sm);
             ctx->launches += 1;
-        }
-        if (cur == 1) {
-            launch_state_copy(ctx->P, sm);
+            int cur = 0;
+            for (int s = 0; s < d.n_sub; ++s) {
+                dp.hin = ctx->hcur;
+                dp.hout = 1 - ctx->hcur;
+                launch_dem_subcycle(dp, cur, 0, s == d.n_sub - 1, sm);
+                ctx->hcur = 1 - ctx->hcur;
+                cur = 1 - cur;
+                ctx->launches += 1;
+            }
+            if (cur == 1) {
+                launch_state_copy(ctx->P, sm);
+                ctx->launches += 1;
+            }
+        } else {
+            // prescribed motion: x += u over the step
+            launch_prescribed_move(ctx->P, ctx->g, sm);
             ctx->launches += 1;
         }
         CK(prof_mark(ctx));
@@ -979,6 +990,21 @@ lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* 
             if (force_hyd) force_hyd[3 * i + a] = fp[6 * i + a];
             if (torque_hyd) torque_hyd[3 * i + a] = fp[6 * i + 3 + a];
         }
+    return check_status(ctx);
+}
+
+lbm_status lbm_set_particle_velocity(lbm_ctx* ctx, int n, const double* vel, const double* omega) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (n < 0 || n > ctx->P.n) return fail(ctx, LBM_ERR_INVALID, "n outside [0, particle count]");
+    if (n == 0) return LBM_OK;
+    cudaStream_t sm = ctx->stream;
+    if (vel) CK(cudaMemcpyAsync(ctx->P.u, vel, 24 * (size_t)n, cudaMemcpyHostToDevice, sm));
+    if (omega) CK(cudaMemcpyAsync(ctx->P.om, omega, 24 * (size_t)n, cudaMemcpyHostToDevice, sm));
+    // the float32 view carries the velocities into the link arithmetic
+    launch_view_update(ctx->P, sm);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(sm));
     return check_status(ctx);
 }
 

@@ -73,9 +73,7 @@ __device__ __forceinline__ double mimg(double d, int n, int per) {
 
 // ------------------------------------------------------------ particle view
 
-__global__ void view_kernel(const Particles P) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+__device__ __forceinline__ void write_view(const Particles& P, int i) {
     PartView v;
     double gg = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -92,6 +90,12 @@ __global__ void view_kernel(const Particles P) {
     v.R = (float)P.R[i];
     v.C = (float)(gg - P.R[i] * P.R[i]);
     P.view[i] = v;
+}
+
+__global__ void view_kernel(const Particles P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    write_view(P, i);
 }
 
 void launch_view_update(const Particles& P, cudaStream_t st) {
@@ -276,6 +280,21 @@ void launch_dem_position(const DemParams& p, cudaStream_t st) {
     if (p.P.n == 0) return;
     position_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
 }
+
+// prescribed motion: every particle moves by its velocity over one time step
+// (Eq. (37) with no force and dt = 1), then its view is rebuilt
+__global__ void prescribed_move_kernel(const Particles P, const Geom g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    for (int d = 0; d < 3; ++d) P.x[3 * i + d] = wrap_pos(P.x[3 * i + d] + P.u[3 * i + d], g.n[d], g.per[d]);
+    write_view(P, i);
+}
+
+void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st) {
+    if (P.n == 0) return;
+    prescribed_move_kernel<<<(P.n + 127) / 128, 128, 0, st>>>(P, g);
+}
+
 
 // ------------------------------------------------------------ interaction laws
 

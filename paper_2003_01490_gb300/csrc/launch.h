@@ -135,6 +135,7 @@ void launch_dem_position(const DemParams& p, cudaStream_t st);
 void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st);
 void launch_state_copy(const Particles& P, cudaStream_t st);
 void launch_view_update(const Particles& P, cudaStream_t st);
+void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st);
 
 // message returned by lbm_last_error(NULL)
 void set_global_error(const std::string& msg);

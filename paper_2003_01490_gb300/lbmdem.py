@@ -18,12 +18,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, '_lib', 'liblbmdem.so')
 
 STORAGE = {'f64': 0, 'f32': 1, 'f16': 2, 'bf16': 3}
+# lbm_dem.fixed_particles: particles moved by the DEM, held fixed, or moved by prescribed velocities
+MOTION_DEM, MOTION_FIXED, MOTION_PRESCRIBED = 0, 1, 2
 FLAG_SOLID, FLAG_SHELL, FLAG_NEAR, FLAG_MISS, FLAG_NEWFLUID, FLAG_MULTI = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20
 STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CUDA',
           -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -7: 'LBM_ERR_STATE'}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
-           'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_get_fields',
+           'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
+           'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
            'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
            'lbm_destroy')
@@ -80,6 +83,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_add_spheres.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_step.argtypes = [c_void_p, c_int]
     lib.lbm_get_particle_state.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
+    lib.lbm_set_particle_velocity.argtypes = [c_void_p, c_int, dp, dp]
     lib.lbm_get_fields.argtypes = [c_void_p, dp, dp, P(ctypes.c_ubyte)]
     lib.lbm_get_owner.argtypes = [c_void_p, P(c_int)]
     lib.lbm_get_pdfs.argtypes = [c_void_p, dp]
@@ -194,6 +198,17 @@ def lbm_add_spheres(ctx, pos, vel, omega, radius, density):
                                           _dptr(radius), _dptr(density), ctypes.byref(first)),
            ctx.handle)
     return first.value
+
+
+def lbm_set_particle_velocity(ctx, vel=None, omega=None):
+    """Replace the velocities of particles 0 .. n-1 ((n, 3) float64 each, either None)."""
+    arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1, 3))
+            for a in (vel, omega)]
+    n = max([len(a) for a in arrs if a is not None] or [0])
+    for a in arrs:
+        if a is not None and len(a) != n:
+            raise ValueError('vel and omega need the same number of rows')
+    _check(load_library().lbm_set_particle_velocity(ctx.handle, n, _dptr(arrs[0]), _dptr(arrs[1])), ctx.handle)
 
 
 def lbm_step(ctx, n_steps=1):

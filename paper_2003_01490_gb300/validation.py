@@ -1,0 +1,194 @@
+"""Full-size validation runs on the GPU, against the values the paper prints.
+
+These cases are too large for the float64 oracle; they check the CUDA path
+against the paper's own simulation results instead.
+
+* :func:`shear_drag_lift` -- Sec. 2.5: a fixed sphere (D = 20) at height
+  L D above the resting bottom wall of a [48 x 16 x 8] D box, periodic in x
+  and y, with the top wall moving at u_w = 0.1. The flow starts from the
+  linear shear profile and runs until the drag and lift coefficients
+  C_D = F_x / (pi/8 rho G^2 L^2 D^4) and C_L (F_z alike), G = u_w / H, settle.
+  The paper prints them for L = 0.505, 1 and Re_s = G D^2 / nu = 1, 25
+  (TRT+aB column of its drag/lift tables), next to the correlation of its
+  reference.
+* :func:`artificial_acceleration` -- Sec. 2.3.3: a sphere whose settling
+  velocity is prescribed every step, u_p(t) = -u_s (1 - exp(-c_acc t / t_St)),
+  with a density probe moving along at x_p + (D, 0, 0) (trilinear
+  interpolation); the paper shows the probe's spectrum as a figure only, so
+  the run reports the probe series.
+
+Command line: ``python -m paper_2003_01490_gb300.validation shear --re 1``
+prints one JSON line per case.
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import lbmdem as L
+
+# lattice directions and weights in the order of App. A (cx, cy, cz)
+_C = np.array([[0, 0, 0], [0, 1, 0], [0, -1, 0], [-1, 0, 0], [1, 0, 0], [0, 0, 1], [0, 0, -1],
+               [-1, 1, 0], [1, 1, 0], [-1, -1, 0], [1, -1, 0], [0, 1, 1], [0, -1, 1], [-1, 0, 1],
+               [1, 0, 1], [0, 1, -1], [0, -1, -1], [-1, 0, -1], [1, 0, -1]], dtype=np.float64)
+_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+# the paper's drag/lift tables (Sec. 2.5): (Re_s, L) -> (C_D, C_L) of its
+# TRT+aB simulation and of the reference correlation
+PAPER_SHEAR = {
+    (1, 0.505): dict(sim=(44.00, 3.43), ref=(44.88, 3.54)),
+    (1, 1.0): dict(sim=(34.44, 2.30), ref=(35.77, 2.32)),
+    (25, 0.505): dict(sim=(3.70, 0.92), ref=(3.53, 0.88)),
+    (25, 1.0): dict(sim=(2.78, 0.41), ref=(2.81, 0.45)),
+}
+
+
+def equilibrium_planes(ux_of_z):
+    """Equilibrium PDFs (rho = 1, u = (u_x(z), 0, 0)) per z plane: (19, nz)."""
+    ux = np.asarray(ux_of_z, dtype=np.float64)
+    cu = _C[:, 0][:, None] * ux[None, :]
+    return _W[:, None] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux)[None, :])
+
+
+def shear_drag_lift(L_dist, re, D=20.0, storage='f32', box=(48, 16, 8), u_w=0.1, block=1000,
+                    window=5, rtol=1e-3, max_steps=200000, re_def='particle', log=None):
+    """Drag and lift coefficients of the fixed sphere near the bottom wall.
+
+    re_def 'shear': re = G D^2 / nu; 'particle': re = G L D^2 / nu, the
+    Reynolds number of the undisturbed velocity G L D at the sphere centre
+    (the two agree at L = 1). Runs blocks of `block` steps until C_D and C_L
+    each changed by less than `rtol` (relative) over the last `window`
+    blocks, or max_steps."""
+    nx, ny, nz = int(box[0] * D), int(box[1] * D), int(box[2] * D)
+    H = float(nz)
+    G = u_w / H
+    nu = G * D * D * (L_dist if re_def == 'particle' else 1.0) / re
+    tau = 3.0 * nu + 0.5
+    r, d = L.lbm_default_params()
+    r.tau = tau
+    d.fixed_particles = L.MOTION_FIXED
+    wall_hi = [[0.0] * 3 for _ in range(3)]
+    wall_hi[2] = [u_w, 0.0, 0.0]
+    grid = L.make_grid((nx, ny, nz), (1, 1, 0), wall_vel_hi=wall_hi)
+    ctx = L.lbm_create(grid, r, (0.0, 0.0, 0.0), d, storage, max_particles=1)
+    # linear shear profile at the cell centres (halfway walls at z = 0 and H)
+    z = np.arange(nz) + 0.5
+    feq = equilibrium_planes(u_w * z / H)
+    f = np.empty((19, nz, ny, nx))
+    for q in range(19):
+        f[q] = feq[q][:, None, None]
+    L.lbm_set_pdfs(ctx, f.reshape(19, -1))
+    del f
+    pos = np.array([[box[0] / 2.0 * D, box[1] / 2.0 * D, L_dist * D]])
+    L.lbm_add_spheres(ctx, pos, np.zeros((1, 3)), np.zeros((1, 3)), np.array([D / 2.0]), np.array([1.0]))
+    norm = math.pi / 8.0 * G * G * L_dist * L_dist * D ** 4
+    hist = []
+    steps = 0
+    t0 = time.time()
+    while steps < max_steps:
+        L.lbm_step(ctx, block)
+        steps += block
+        F = L.lbm_get_particle_state(ctx)['force_hyd'][0]
+        hist.append((F[0] / norm, F[2] / norm))
+        if log:
+            log('step %d: C_D %.4f C_L %.4f' % (steps, hist[-1][0], hist[-1][1]))
+        if len(hist) > window:
+            a, b = np.array(hist[-window - 1]), np.array(hist[-1])
+            if np.all(np.abs(b - a) <= rtol * np.abs(b)):
+                break
+    wall = time.time() - t0
+    cells = nx * ny * nz
+    del ctx
+    cd, cl = hist[-1]
+    paper = PAPER_SHEAR.get((int(re), float(L_dist)))
+    out = dict(case='shear drag/lift', Re=re, re_def=re_def, Re_s=round(G * D * D / nu, 4), L=L_dist, D=D,
+               shape=[nx, ny, nz], tau=tau, storage=storage,
+               steps=steps, converged=steps < max_steps, C_D=round(cd, 4), C_L=round(cl, 4),
+               mlups=round(cells * steps / wall / 1e6, 1))
+    if paper:
+        out['paper_sim'] = dict(C_D=paper['sim'][0], C_L=paper['sim'][1])
+        out['paper_ref'] = dict(C_D=paper['ref'][0], C_L=paper['ref'][1])
+        out['rel_dev_from_paper_sim'] = dict(C_D=round(cd / paper['sim'][0] - 1, 4),
+                                             C_L=round(cl / paper['sim'][1] - 1, 4))
+    return out
+
+
+def trilinear(field, p):
+    """Trilinear interpolation of a cell-centred field [z][y][x] at point p."""
+    nz, ny, nx = field.shape
+    g = np.asarray(p, dtype=np.float64) - 0.5
+    i0 = np.floor(g).astype(int)
+    t = g - i0
+    v = 0.0
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                wgt = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                v += wgt * field[(i0[2] + dz) % nz, (i0[1] + dy) % ny, (i0[0] + dx) % nx]
+    return v
+
+
+def artificial_acceleration(D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.34, c_acc=10.0,
+                            storage='f32', t_ref_units=24.0, probe_every=50, max_steps=None):
+    """Sphere with prescribed settling velocity and a density probe moving with it."""
+    nx, ny, nz = int(box[0] * D), int(box[1] * D), int(box[2] * D)
+    nu = u_s * D / re
+    r, d = L.lbm_default_params()
+    r.tau = 3.0 * nu + 0.5
+    d.fixed_particles = L.MOTION_PRESCRIBED
+    grid = L.make_grid((nx, ny, nz), (0, 0, 1))
+    ctx = L.lbm_create(grid, r, (0.0, 0.0, 0.0), d, storage, max_particles=1)
+    L.lbm_add_spheres(ctx, [[nx / 2.0, ny / 2.0, nz / 2.0]], np.zeros((1, 3)), np.zeros((1, 3)),
+                      np.array([D / 2.0]), np.array([ratio]))
+    t_st = ratio * D * D / (18.0 * nu)
+    steps = int(t_ref_units * D / u_s) if max_steps is None else max_steps
+    series = []
+    t0 = time.time()
+    for t in range(1, steps + 1):
+        u = -u_s * (1.0 - math.exp(-c_acc * t / t_st))
+        L.lbm_set_particle_velocity(ctx, np.array([[0.0, 0.0, u]]))
+        L.lbm_step(ctx, 1)
+        if t % probe_every == 0:
+            x = L.lbm_get_particle_state(ctx)['pos'][0]
+            rho, _, _ = L.lbm_get_fields(ctx)
+            series.append((t, trilinear(rho, x + np.array([D, 0.0, 0.0]))))
+    wall = time.time() - t0
+    del ctx
+    s = np.array(series)
+    late = s[len(s) // 2:, 1] if len(s) else np.zeros(1)
+    return dict(case='artificial acceleration', D=D, shape=[nx, ny, nz], tau=r.tau, storage=storage, steps=steps,
+                probe_samples=len(s), probe_rho_mean=float(late.mean()), probe_rho_std=float(late.std()),
+                wall_s=round(wall, 1))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split('\n')[0])
+    sub = ap.add_subparsers(dest='case', required=True)
+    a = sub.add_parser('shear')
+    a.add_argument('--re', type=float, nargs='+', default=[1.0])
+    a.add_argument('--L', type=float, nargs='+', default=[0.505, 1.0])
+    a.add_argument('--D', type=float, default=20.0)
+    a.add_argument('--storage', default='f32')
+    a.add_argument('--max-steps', type=int, default=200000)
+    a.add_argument('--block', type=int, default=1000)
+    a.add_argument('--re-def', choices=('particle', 'shear'), default='particle')
+    a.add_argument('--verbose', action='store_true')
+    b = sub.add_parser('acceleration')
+    b.add_argument('--D', type=float, default=20.0)
+    b.add_argument('--storage', default='f32')
+    b.add_argument('--max-steps', type=int, default=None)
+    args = ap.parse_args(argv)
+    if args.case == 'shear':
+        for re in args.re:
+            for Ld in args.L:
+                res = shear_drag_lift(Ld, re, D=args.D, storage=args.storage, max_steps=args.max_steps,
+                                      block=args.block, re_def=args.re_def, log=print if args.verbose else None)
+                print(json.dumps(res), flush=True)
+    else:
+        print(json.dumps(artificial_acceleration(D=args.D, storage=args.storage, max_steps=args.max_steps)))
+
+
+if __name__ == '__main__':
+    main()

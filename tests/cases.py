@@ -39,7 +39,8 @@ def build_oracle(case):
                tangential_lubrication=bool(dem['tangential_lubrication']),
                force_averaging=bool(dem['force_averaging']),
                fluid_counterforce=bool(dem['fluid_counterforce']),
-               fixed_particles=bool(dem['fixed_particles']),
+               fixed_particles=int(dem['fixed_particles']) == 1,
+               prescribed_motion=int(dem['fixed_particles']) == 2,
                missing_links=bool(dem['missing_links']))
     sim = Simulation(dom, p)
     if 'init_pdfs' in case:

@@ -216,6 +216,43 @@ def test_moving_particles_collisions_f32(L):
     assert rel_l2(u, u_o, both) < 1e-6 and rel_l2(rho, r_o, both) < 1e-6
 
 
+def prescribed_case(storage):
+    # a sphere accelerated towards -z by a prescribed velocity (the artificial
+    # acceleration of Sec. 2.3.3, scaled to a small box: u_s = 0.05, fast ramp),
+    # spinning, between no-slip walls in x and y, periodic in z
+    return dict(shape=(24, 24, 40), periodic=(0, 0, 1), tau=0.6, storage=storage,
+                spheres=spheres([[12.0, 12.0, 20.0]], [4.5]), dem=dict(fixed_particles=2))
+
+
+def prescribed_velocity(t, u_s=0.05, t_acc=8.0):
+    return np.array([[0.0, 0.0, -u_s * (1.0 - np.exp(-t / t_acc))]])
+
+
+@pytest.mark.parametrize('storage,tol', [('f64', F64_TOL), ('f32', 1e-6)])
+def test_prescribed_motion(L, storage, tol):
+    case = prescribed_case(storage)
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    om = np.array([[0.0, 0.002, 0.0]])
+    refills = 0
+    for t in range(1, 41):
+        u = prescribed_velocity(t)
+        ora.U, ora.Om = u.copy(), om.copy()
+        L.lbm_set_particle_velocity(ctx, u, om)
+        ora.step(1)
+        L.lbm_step(ctx, 1)
+        refills += len(ora.refilled)
+    st = L.lbm_get_particle_state(ctx)
+    assert np.abs(st['pos'] - ora.X).max() < 1e-12
+    assert np.array_equal(st['vel'], ora.U) and np.array_equal(st['omega'], ora.Om)
+    rho, u, flags = L.lbm_get_fields(ctx)
+    assert np.array_equal((flags & L.FLAG_SOLID) != 0, ora.owner >= 0)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < tol and rel_l2(rho, r_o) < tol
+    assert rel_l2(st['force_hyd'], ora.Ffp) < 100 * tol
+    assert refills > 0
+
+
 def test_sphere_wall_workload_first_300_steps_f64(L):
     from paper_2003_01490_gb300 import workloads
     w = workloads.sphere_wall()

@@ -214,3 +214,48 @@ def test_refill_linear_field_uses_exact_strain():
         expect[q] = W[q] * (1 - 1.5 / s_nu * (cq @ S @ cq - np.trace(S) / 3))
     # rho_bar of the linear equilibrium neighbours is exactly 1
     assert np.abs(ft[:, 4, 4, 4] - expect).max() < 1e-15
+
+
+def brute_force_solid_count(dom, X, R):
+    """Cells whose centre lies within R of X (minimum image), by plain loops."""
+    n = 0
+    for k, j, i in itertools.product(range(dom.shape[2]), range(dom.shape[1]), range(dom.shape[0])):
+        d = np.array([i + 0.5, j + 0.5, k + 0.5]) - X
+        d -= np.array(dom.shape) * np.round(d / np.array(dom.shape))
+        n += d @ d <= R * R
+    return n
+
+
+def test_prescribed_motion_moves_by_the_set_velocity():
+    # prescribed motion (Sec. 2.3.3 sets a sphere's velocity every step):
+    # x advances by u per step, the mapping follows, uncovered cells refill
+    dom = Domain(12, 12, 12)
+    sim = Simulation(dom, Params(tau=0.8, prescribed_motion=True))
+    X0 = np.array([[6.25, 6.0, 5.9]])
+    R = 2.6
+    sim.add_spheres(X0, [[0, 0, 0]], [[0, 0, 0]], [R], [1.0])
+    refills = 0
+    U = np.array([[0.35, -0.2, 0.1]])
+    for k in range(1, 9):
+        sim.U = U.copy()
+        sim.step(1)
+        refills += len(sim.refilled)
+    X = (X0 + 8 * U) % 12.0
+    assert np.abs(sim.X - X).max() < 1e-12
+    assert int((sim.owner >= 0).sum()) == brute_force_solid_count(dom, X[0], R)
+    assert refills > 0
+    # the stored velocity is the one set: no DEM forces act on it
+    assert np.array_equal(sim.U, U)
+
+
+def test_prescribed_motion_at_rest_equals_fixed_particles():
+    runs = []
+    for mode in ('prescribed', 'fixed'):
+        dom = Domain(12, 12, 12)
+        sim = Simulation(dom, Params(tau=0.8, body_force=(1e-5, 0, 0),
+                                     prescribed_motion=mode == 'prescribed', fixed_particles=mode == 'fixed'))
+        sim.add_spheres([[6.25, 6.0, 5.9]], [[0, 0, 0]], [[0, 0, 0]], [2.6], [1.0])
+        sim.step(5)
+        runs.append(sim)
+    assert np.array_equal(runs[0].ft, runs[1].ft)
+    assert np.array_equal(runs[0].Ffp, runs[1].Ffp)
