@@ -51,7 +51,9 @@ typedef enum {
 } lbm_status;
 
 /* PDF storage format. Every format stores the shifted value f_q - w_q; the
- * collision runs in float64 for LBM_STORE_F64 and in float32 otherwise. */
+ * collision and the DEM's pair and wall laws run in float64 for
+ * LBM_STORE_F64 and in float32 otherwise (particle state, integration and
+ * sphere overlaps stay float64). */
 typedef enum {
     LBM_STORE_F64 = 0,
     LBM_STORE_F32 = 1,

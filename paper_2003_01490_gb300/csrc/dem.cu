@@ -1,8 +1,11 @@
-// dem.cu -- particle side of Algorithm 1 in float64: force finalisation and
-// two-step averaging of the momentum-exchange force (Sec. 4.2), neighbour
-// search, lubrication correction (Eqs. (25)-(33)), linear spring-dashpot
-// contact with Coulomb-limited tangential spring (Eqs. (39)-(52)) and the
-// Velocity-Verlet subcycles (Eqs. (37)-(38)).
+// dem.cu -- particle side of Algorithm 1: force finalisation and two-step
+// averaging of the momentum-exchange force (Sec. 4.2), neighbour search,
+// lubrication correction (Eqs. (25)-(33)), linear spring-dashpot contact with
+// Coulomb-limited tangential spring (Eqs. (39)-(52)) and the Velocity-Verlet
+// subcycles (Eqs. (37)-(38)); the prescribed-motion update. Particle state
+// and integration are float64; the pair and wall laws run in float64 for
+// float64 PDF storage and in float32 (separations and overlaps from float64
+// positions) for the other formats.
 //
 // One thread per particle gathers every interaction of its particle, so no
 // force atomics are needed; a pair is evaluated by both partners with exactly
