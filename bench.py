@@ -91,6 +91,15 @@ def add_spheres(ctx, w):
     L.lbm_add_spheres(ctx, w['pos'], w['vel'], w['omega'], w['radius'], w['density'])
 
 
+# float64 roofline of the dense kernel: algorithmic FLOPs per fluid cell
+# (population-form TRT + Guo forcing + rank-2 bulk correction, ~200-260) and
+# per particle link (link fraction root, CLI value, momentum-exchange force
+# and torque), and the float64 peak from the unit counts and clocks
+FLOP_PER_FLUID_CELL = 230
+FLOP_PER_LINK = 75
+FP64_PEAK_TFLOPS = round(152 * 2.07e9 * 2 * 2 / 1e12, 3)
+
+
 def bytes_per_cell(storage):
     es = {'f64': 8, 'f32': 4, 'f16': 2, 'bf16': 2}[storage]
     return 2 * 19 * es + 1, 1          # fluid cell, solid cell (flag byte only)
@@ -334,10 +343,10 @@ def run_ours(args, rank, world, local):
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     bf, bs = bytes_per_cell(storage)
-    # per link the kernel also reads f~_p(x), which no pull reads, and the
-    # owner of the solid cell
+    # per link the kernel also reads f~_p(x) and f~_q(x) at the cell itself
+    # (CLI, Eq. (14)), values no pull reads
     es = {'f64': 8, 'f32': 4}.get(storage, 2)
-    alg_bytes = (cells - n_solid) * bf + n_solid * bs + n_links * (es + 4)
+    alg_bytes = (cells - n_solid) * bf + n_solid * bs + n_links * 2 * es
     k_ms = phases['stream_collide'] / max(nsteps, 1)
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
@@ -351,6 +360,17 @@ def run_ours(args, rank, world, local):
                 'links_per_launch': int(n_links),
                 'peak_source': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
                 else 'fallback 6.8 TB/s', 'phase_share': share}
+    if storage == 'f64':
+        # float64: GB300's float64 units (1.26 TFLOP/s) bind before HBM
+        # (305 B and ~230 FLOP per fluid cell)
+        flops = (cells - n_solid) * FLOP_PER_FLUID_CELL + n_links * FLOP_PER_LINK
+        achieved_tf = flops / (k_ms * 1e-3) / 1e12
+        roofline.update({'bound': 'alu', 'achieved': round(achieved_tf, 4), 'peak': FP64_PEAK_TFLOPS,
+                         'unit': 'TFLOP/s', 'frac': round(achieved_tf / FP64_PEAK_TFLOPS, 4),
+                         'alg_flops_per_launch': int(flops),
+                         'peak_source': 'derived: 152 SMs x 2.07 GHz x 2 float64 FMA per clock x 2 FLOP',
+                         'hbm': {'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
+                                 'frac': round(achieved / peak, 4)}})
 
     e2e = None
     if not args.no_e2e:
