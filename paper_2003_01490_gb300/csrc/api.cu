@@ -841,7 +841,12 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     ctx->launches += 2 + (ctx->P.n > 0 ? 1 : 0);
     CK(prof_mark(ctx));
     if (move) {
-        if (dem) {
+        if (dem && ctx->P.n <= DEM_ONE_BLOCK_MAX) {
+            // Algorithm 1, lines 4-10, in one block: few particles
+            launch_dem_step_one_block(dp, ctx->hcur, d.n_sub, sm);
+            if (d.n_sub & 1) ctx->hcur = 1 - ctx->hcur;
+            ctx->launches += 1;
+        } else if (dem) {
             // Algorithm 1, lines 4-10: DEM subcycles
             launch_dem_position(dp, sm);
             ctx->launches += 1;

@@ -405,8 +405,8 @@ __device__ __forceinline__ double image_shift(float d, int n, int per) {
 // float64 (the overlap delta = that / (|d| + Ri + Rj) keeps float32 relative
 // accuracy), the interaction laws in float32.
 template <typename T>
-__device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, int j, Vec3<T>& F, Vec3<T>& Tq,
-                                           bool& contact, Vec3<T>& dnew) {
+__device__ __forceinline__ void pair_force(const DemParams& p, int cur, int hin, int i, int j, Vec3<T>& F,
+                                           Vec3<T>& Tq, bool& contact, Vec3<T>& dnew) {
     const Particles& P = p.P;
     const DemConsts<T>& k = consts<T>(p);
     const double* X = P.xs[cur];
@@ -459,10 +459,10 @@ __device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, i
         const T m_eff = mi * mj / (mi + mj);
         const T Tc = collision_time<T>(Ri + Rj, k.Tc);
         Vec3<T> old = zero3<T>();
-        const int nin = P.hist_n[p.hin][i];
+        const int nin = P.hist_n[hin][i];
         for (int h = 0; h < nin; ++h)
-            if (P.hist_id[p.hin][i * NBR_CAP + h] == j) {
-                const double* s = P.hist_d[p.hin] + 3 * (i * NBR_CAP + h);
+            if (P.hist_id[hin][i * NBR_CAP + h] == j) {
+                const double* s = P.hist_d[hin] + 3 * (i * NBR_CAP + h);
                 old = Vec3<T>{(T)s[0], (T)s[1], (T)s[2]};
                 break;
             }
@@ -488,16 +488,138 @@ __device__ __forceinline__ void pair_force(const DemParams& p, int cur, int i, i
 // positions of the next subcycle (Eq. (37)) into buffer 1 - cur.
 // init = 1 evaluates the initial force F(t = 0) only (no state or history
 // update). Pair terms are evaluated by both partners with mirrored operands.
-constexpr int PPB = 32;          // particles per block
+constexpr int PPB = DEM_ONE_BLOCK_MAX;   // particles per block
 constexpr int PAIR_CHUNK = 128;  // queued pairs evaluated per pass of the block
 
+// pass 3 of a subcycle for particle ip: plane walls, the averaged fluid force
+// and V (rho_p - rho_f) g, the velocities (Eq. (38)) and, unless it is the
+// last subcycle, the positions of the next subcycle (Eq. (37)) into buffer
+// 1 - cur; sum holds the particle's pair forces and torques
 template <typename T>
-__global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
+__device__ void integrate_particle(const DemParams& p, int ip, const T (&sum)[6], int cur, int hin, int hout, int init,
+                                   int last) {
+    const Particles& P = p.P;
+    const double* X = P.xs[cur];
+    const double* Uv = P.us[cur];
+    const double* Om = P.oms[cur];
+    Vec3<T> F = {sum[0], sum[1], sum[2]};
+    Vec3<T> Tq = {sum[3], sum[4], sum[5]};
+    {
+        // plane walls on the faces of non-periodic axes
+        const DemConsts<T>& k = consts<T>(p);
+        const V3 xd = ld3(X, ip);
+        Vec3<T> ui, omi;
+        if constexpr (sizeof(T) == 8) {
+            ui = ld3(Uv, ip);
+            omi = ld3(Om, ip);
+        } else {
+            ui = ld3(P.ufs[cur], ip);
+            omi = ld3(P.omfs[cur], ip);
+        }
+        const double Rid = P.R[ip];
+        const T Ri = (T)Rid, mi = (T)P.m[ip];
+        const double xa[3] = {xd.x, xd.y, xd.z};
+        for (int a = 0; a < 3; ++a) {
+            if (p.g.per[a]) continue;
+            for (int side = 0; side < 2; ++side) {
+                const int face = 2 * a + side;
+                Vec3<T> nw = zero3<T>();
+                const T sgn = side == 0 ? T(1) : T(-1);
+                if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
+                const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
+                const T delta = (T)((xa[a] - xw) * (side == 0 ? 1.0 : -1.0) - Rid);
+                const double* uwp = p.g.wall_vel[side][a];
+                const Vec3<T> uw = {(T)uwp[0], (T)uwp[1], (T)uwp[2]};
+                const Vec3<T> uij = ui - uw;
+                if (p.lubrication) {
+                    const T dmin = (k.min_a + k.min_b * Ri) * Ri;
+                    lubrication_on_i<T>(k, p.tangential, Ri, T(-1), delta, nw, uij, omi, zero3<T>(), dmin, F, Tq);
+                }
+                if (!init) P.wact[hout][6 * ip + face] = 0;
+                if (delta < T(0)) {
+                    const Vec3<T> ri = (-(Ri + T(0.5) * delta)) * nw;
+                    const Vec3<T> ucp = (ui + cross(omi, ri)) - uw;
+                    const T Tc = collision_time<T>(T(2) * Ri, k.Tc);
+                    Vec3<T> old = zero3<T>();
+                    if (P.wact[hin][6 * ip + face]) {
+                        const double* sd = P.whist[hin] + 3 * (6 * ip + face);
+                        old = Vec3<T>{(T)sd[0], (T)sd[1], (T)sd[2]};
+                    }
+                    Vec3<T> Fn, Ft, dnew;
+                    contact_force<T>(k, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
+                    F = F + (Fn + Ft);
+                    Tq = Tq + cross(ri, Ft);
+                    if (!init) {
+                        double* sd = P.whist[hout] + 3 * (6 * ip + face);
+                        sd[0] = (double)dnew.x; sd[1] = (double)dnew.y; sd[2] = (double)dnew.z;
+                        P.wact[hout][6 * ip + face] = 1;
+                    }
+                }
+            }
+        }
+    }
+    const V3 Fd = cvt3<double>(F), Td = cvt3<double>(Tq);
+    const V3 Fs = mk(Fd.x + P.fbar[6 * ip] + P.ext[3 * ip], Fd.y + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
+                     Fd.z + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
+    const V3 Ts = mk(Td.x + P.fbar[6 * ip + 3], Td.y + P.fbar[6 * ip + 4], Td.z + P.fbar[6 * ip + 5]);
+    if (init) {
+        st3(P.F_prev, ip, Fs);
+        st3(P.T_prev, ip, Ts);
+        return;
+    }
+    P.hist_n[hout][ip] = P.nbr_count[ip];
+    // Eq. (38) for u and its rotational analogue for omega (hm = 1/(2m), hI = 1/(2I))
+    const double cu = p.dt * P.hm[ip], co = p.dt * P.hI[ip];
+    const V3 Fp = ld3(P.F_prev, ip), Tp = ld3(P.T_prev, ip);
+    const V3 u = ld3(Uv, ip) + cu * (Fp + Fs);
+    const V3 om = ld3(Om, ip) + co * (Tp + Ts);
+    st3(P.F_prev, ip, Fs);
+    st3(P.T_prev, ip, Ts);
+    if (!(dot(u, u) < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
+    const int nxt = 1 - cur;
+    st3(P.us[nxt], ip, u);
+    st3(P.oms[nxt], ip, om);
+    if constexpr (sizeof(T) == 4) {
+        for (int d = 0; d < 3; ++d) {
+            P.ufs[nxt][3 * ip + d] = (float)(d == 0 ? u.x : d == 1 ? u.y : u.z);
+            P.omfs[nxt][3 * ip + d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
+        }
+    }
+    const double ua[3] = {u.x, u.y, u.z};
+    const double Fa[3] = {Fs.x, Fs.y, Fs.z};
+    const double c = p.dt * cu;
+    PartView v;
+    double gg = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        // Eq. (37) for the next subcycle; the last subcycle keeps its positions
+        double x = X[3 * ip + d];
+        if (!last) x = wrap_pos(x + p.dt * ua[d] + c * Fa[d], p.g.n[d], p.g.per[d]);
+        P.xs[nxt][3 * ip + d] = x;
+        P.xfs[nxt][3 * ip + d] = (float)x;
+        if (last) {
+            const double b = floor(x);
+            v.base[d] = (int)b;
+            v.frac[d] = (float)(x - b);
+            const double g = 0.5 - (x - b);
+            gg += g * g;
+            v.u[d] = (float)ua[d];
+            v.om[d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
+        }
+    }
+    if (last) {
+        v.R = (float)P.R[ip];
+        v.C = (float)(gg - P.R[ip] * P.R[ip]);
+        P.view[ip] = v;
+    }
+}
+
+
+template <typename T>
+__device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int hin, int hout, int init, int last) {
     const Particles& P = p.P;
     const int tid = threadIdx.x;
     const int pl = tid >> 2, sub = tid & 3;   // pass 1: particle of the block, lane of its group
     const int i = blockIdx.x * PPB + pl;
-    const int hout = p.hout;
     __shared__ unsigned short s_queue[PPB * NBR_CAP];   // pl << 5 | slot
     __shared__ int s_off[PPB + 1];
     __shared__ T s_res[PAIR_CHUNK][6];
@@ -567,7 +689,7 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
             const int j = P.nbr[ei * NBR_CAP + k];
             Vec3<T> F, Tq, dnew;
             bool contact;
-            pair_force<T>(p, cur, ei, j, F, Tq, contact, dnew);
+            pair_force<T>(p, cur, hin, ei, j, F, Tq, contact, dnew);
             s_res[tid][0] = F.x; s_res[tid][1] = F.y; s_res[tid][2] = F.z;
             s_res[tid][3] = Tq.x; s_res[tid][4] = Tq.y; s_res[tid][5] = Tq.z;
             if (!init) {
@@ -589,122 +711,57 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
     }
     // pass 3: one thread per particle, lanes 0-7 of each warp (the float64
     // work of the block spread over the four schedulers)
-    if ((tid & 31) >= PPB / 4) return;
-    const int pl3 = (tid >> 5) * (PPB / 4) + (tid & 31);
-    const int ip = blockIdx.x * PPB + pl3;
-    if (ip >= P.n) return;
-    const double* X = P.xs[cur];
-    const double* Uv = P.us[cur];
-    const double* Om = P.oms[cur];
-    Vec3<T> F = {s_sum[pl3][0], s_sum[pl3][1], s_sum[pl3][2]};
-    Vec3<T> Tq = {s_sum[pl3][3], s_sum[pl3][4], s_sum[pl3][5]};
-    {
-        // plane walls on the faces of non-periodic axes
-        const DemConsts<T>& k = consts<T>(p);
-        const V3 xd = ld3(X, ip);
-        Vec3<T> ui, omi;
-        if constexpr (sizeof(T) == 8) {
-            ui = ld3(Uv, ip);
-            omi = ld3(Om, ip);
-        } else {
-            ui = ld3(P.ufs[cur], ip);
-            omi = ld3(P.omfs[cur], ip);
-        }
-        const double Rid = P.R[ip];
-        const T Ri = (T)Rid, mi = (T)P.m[ip];
-        const double xa[3] = {xd.x, xd.y, xd.z};
-        for (int a = 0; a < 3; ++a) {
-            if (p.g.per[a]) continue;
-            for (int side = 0; side < 2; ++side) {
-                const int face = 2 * a + side;
-                Vec3<T> nw = zero3<T>();
-                const T sgn = side == 0 ? T(1) : T(-1);
-                if (a == 0) nw.x = sgn; else if (a == 1) nw.y = sgn; else nw.z = sgn;
-                const double xw = side == 0 ? 0.0 : (double)p.g.n[a];
-                const T delta = (T)((xa[a] - xw) * (side == 0 ? 1.0 : -1.0) - Rid);
-                const double* uwp = p.g.wall_vel[side][a];
-                const Vec3<T> uw = {(T)uwp[0], (T)uwp[1], (T)uwp[2]};
-                const Vec3<T> uij = ui - uw;
-                if (p.lubrication) {
-                    const T dmin = (k.min_a + k.min_b * Ri) * Ri;
-                    lubrication_on_i<T>(k, p.tangential, Ri, T(-1), delta, nw, uij, omi, zero3<T>(), dmin, F, Tq);
-                }
-                if (!init) P.wact[hout][6 * ip + face] = 0;
-                if (delta < T(0)) {
-                    const Vec3<T> ri = (-(Ri + T(0.5) * delta)) * nw;
-                    const Vec3<T> ucp = (ui + cross(omi, ri)) - uw;
-                    const T Tc = collision_time<T>(T(2) * Ri, k.Tc);
-                    Vec3<T> old = zero3<T>();
-                    if (P.wact[p.hin][6 * ip + face]) {
-                        const double* sd = P.whist[p.hin] + 3 * (6 * ip + face);
-                        old = Vec3<T>{(T)sd[0], (T)sd[1], (T)sd[2]};
-                    }
-                    Vec3<T> Fn, Ft, dnew;
-                    contact_force<T>(k, nw, delta, ucp, uij, mi, Tc, old, Fn, Ft, dnew);
-                    F = F + (Fn + Ft);
-                    Tq = Tq + cross(ri, Ft);
-                    if (!init) {
-                        double* sd = P.whist[hout] + 3 * (6 * ip + face);
-                        sd[0] = (double)dnew.x; sd[1] = (double)dnew.y; sd[2] = (double)dnew.z;
-                        P.wact[hout][6 * ip + face] = 1;
-                    }
-                }
-            }
+    if ((tid & 31) < PPB / 4) {
+        const int pl3 = (tid >> 5) * (PPB / 4) + (tid & 31);
+        const int ip = blockIdx.x * PPB + pl3;
+        if (ip < P.n) {
+            T sum[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sum[c] = s_sum[pl3][c];
+            integrate_particle<T>(p, ip, sum, cur, hin, hout, init, last);
         }
     }
-    const V3 Fd = cvt3<double>(F), Td = cvt3<double>(Tq);
-    const V3 Fs = mk(Fd.x + P.fbar[6 * ip] + P.ext[3 * ip], Fd.y + P.fbar[6 * ip + 1] + P.ext[3 * ip + 1],
-                     Fd.z + P.fbar[6 * ip + 2] + P.ext[3 * ip + 2]);
-    const V3 Ts = mk(Td.x + P.fbar[6 * ip + 3], Td.y + P.fbar[6 * ip + 4], Td.z + P.fbar[6 * ip + 5]);
-    if (init) {
-        st3(P.F_prev, ip, Fs);
-        st3(P.T_prev, ip, Ts);
-        return;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
+    subcycle_body<T>(p, cur, p.hin, p.hout, init, last);
+}
+
+// All subcycles of a step in one block when the particles fit in it (at most
+// PPB): the first position update, n_sub subcycles separated by block
+// barriers (each reads the positions and velocities the previous one wrote),
+// and the copy back into buffer 0 after an odd count. Launch latency, not
+// arithmetic, sets the time of a few-particle DEM step.
+template <typename T>
+__global__ void __launch_bounds__(128) dem_step_one_block_kernel(const DemParams p, int hcur, int n_sub) {
+    const int tid = threadIdx.x;
+    if (tid < p.P.n) position_update(p, tid);
+    __syncthreads();
+    int cur = 0;
+    for (int s = 0; s < n_sub; ++s) {
+        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == n_sub - 1);
+        __syncthreads();
+        hcur = 1 - hcur;
+        cur = 1 - cur;
     }
-    P.hist_n[hout][ip] = P.nbr_count[ip];
-    // Eq. (38) for u and its rotational analogue for omega (hm = 1/(2m), hI = 1/(2I))
-    const double cu = p.dt * P.hm[ip], co = p.dt * P.hI[ip];
-    const V3 Fp = ld3(P.F_prev, ip), Tp = ld3(P.T_prev, ip);
-    const V3 u = ld3(Uv, ip) + cu * (Fp + Fs);
-    const V3 om = ld3(Om, ip) + co * (Tp + Ts);
-    st3(P.F_prev, ip, Fs);
-    st3(P.T_prev, ip, Ts);
-    if (!(dot(u, u) < 0.25)) atomicOr(p.status, ST_FAST_PARTICLE);
-    const int nxt = 1 - cur;
-    st3(P.us[nxt], ip, u);
-    st3(P.oms[nxt], ip, om);
-    if constexpr (sizeof(T) == 4) {
-        for (int d = 0; d < 3; ++d) {
-            P.ufs[nxt][3 * ip + d] = (float)(d == 0 ? u.x : d == 1 ? u.y : u.z);
-            P.omfs[nxt][3 * ip + d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
+    if (cur == 1) {
+        const Particles& P = p.P;
+        for (int k = tid; k < 3 * P.n; k += blockDim.x) {
+            P.xs[0][k] = P.xs[1][k];
+            P.us[0][k] = P.us[1][k];
+            P.oms[0][k] = P.oms[1][k];
+            P.xfs[0][k] = P.xfs[1][k];
+            P.ufs[0][k] = P.ufs[1][k];
+            P.omfs[0][k] = P.omfs[1][k];
         }
     }
-    const double ua[3] = {u.x, u.y, u.z};
-    const double Fa[3] = {Fs.x, Fs.y, Fs.z};
-    const double c = p.dt * cu;
-    PartView v;
-    double gg = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        // Eq. (37) for the next subcycle; the last subcycle keeps its positions
-        double x = X[3 * ip + d];
-        if (!last) x = wrap_pos(x + p.dt * ua[d] + c * Fa[d], p.g.n[d], p.g.per[d]);
-        P.xs[nxt][3 * ip + d] = x;
-        P.xfs[nxt][3 * ip + d] = (float)x;
-        if (last) {
-            const double b = floor(x);
-            v.base[d] = (int)b;
-            v.frac[d] = (float)(x - b);
-            const double g = 0.5 - (x - b);
-            gg += g * g;
-            v.u[d] = (float)ua[d];
-            v.om[d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
-        }
-    }
-    if (last) {
-        v.R = (float)P.R[ip];
-        v.C = (float)(gg - P.R[ip] * P.R[ip]);
-        P.view[ip] = v;
-    }
+}
+
+void launch_dem_step_one_block(const DemParams& p, int hcur, int n_sub, cudaStream_t st) {
+    if (p.P.n == 0) return;
+    if (p.pair_f32) dem_step_one_block_kernel<float><<<1, 128, 0, st>>>(p, hcur, n_sub);
+    else dem_step_one_block_kernel<double><<<1, 128, 0, st>>>(p, hcur, n_sub);
 }
 
 void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st) {

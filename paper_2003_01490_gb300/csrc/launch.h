@@ -133,6 +133,10 @@ void launch_bins(const DemParams& p, cudaStream_t st);
 void launch_neighbours(const DemParams& p, cudaStream_t st);
 void launch_dem_position(const DemParams& p, cudaStream_t st);
 void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaStream_t st);
+// at most this many particles: the position update, all subcycles and the
+// state copy of a step in one single-block launch
+constexpr int DEM_ONE_BLOCK_MAX = 32;
+void launch_dem_step_one_block(const DemParams& p, int hcur, int n_sub, cudaStream_t st);
 void launch_state_copy(const Particles& P, cudaStream_t st);
 void launch_view_update(const Particles& P, cudaStream_t st);
 void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st);
