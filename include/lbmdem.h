@@ -167,6 +167,16 @@ lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *
                                   double *omega, double *force_hyd, double *torque_hyd,
                                   int *n_out);
 
+/* Switch how particles move from the next step on (mode as lbm_dem.fixed_particles:
+ * 0 DEM, 1 fixed, 2 prescribed motion), e.g. to release a sphere whose
+ * approach velocity was prescribed (Sec. 4.4 turns the prescribed settling
+ * velocity off once the gap to the wall is below one diameter). Switching to
+ * the DEM after the first step evaluates the force of the first
+ * Velocity-Verlet position update at the current state, including the
+ * current averaged fluid force. Errors: LBM_ERR_INVALID for another mode.
+ * Synchronises the stream. */
+lbm_status lbm_set_motion(lbm_ctx *ctx, int mode);
+
 /* Replace the translational and angular velocities of particles 0 .. n-1
  * (vel, omega: n x 3 doubles each, either may be NULL), e.g. to prescribe a
  * particle's motion step by step (Sec. 2.3.3 prescribes the settling velocity

@@ -292,6 +292,15 @@ class Simulation:
             a = a - self.external_force().sum(axis=0) / (RHO0 * n_fluid)
         return a
 
+    def set_motion(self, dem=False, fixed=False, prescribed=False):
+        """Switch how particles move from the next step on. Switching to the
+        DEM after the first step evaluates the force of the first Velocity-
+        Verlet position update at the current state, with the current
+        averaged fluid force (at t = 0 that force is zero)."""
+        if dem and (self.p.fixed_particles or self.p.prescribed_motion) and self.t > 0:
+            self.F_prev = None
+        self.p.fixed_particles, self.p.prescribed_motion = fixed, prescribed
+
     def step(self, n=1):
         for _ in range(n):
             self._step()
@@ -300,8 +309,9 @@ class Simulation:
         p, dom = self.p, self.dom
         N = len(self.R)
         if self.F_prev is None and N and not p.fixed_particles and not p.prescribed_motion:
-            self.F_prev, self.T_prev = self.dem_forces(np.zeros((N, 3)), np.zeros((N, 3)), 0.0,
-                                                       update_history=False)
+            Fb = self.Fbar if self.t > 0 else np.zeros((N, 3))
+            Tb = self.Tbar if self.t > 0 else np.zeros((N, 3))
+            self.F_prev, self.T_prev = self.dem_forces(Fb, Tb, 0.0, update_history=False)
         self.accel = self.fluid_accel()
         # Algorithm 1, lines 1-2: boundary conditions, interaction force
         f, Ffp, Tfp = stream_and_couple(self.ft, dom, self.owner, self.X, self.U, self.Om, self.R)

@@ -65,6 +65,7 @@ struct lbm_ctx {
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};   // kernel launches in each graph
     int graph_hcur[2][2] = {{0, 0}, {0, 0}};            // history parity after each graph
     bool graphs_off = false;
+    bool dem_restart = false;   // DEM switched on after the first step: initial force pending
     int num_sms = 152;             // multiprocessors of the device (grid sizing)
     double ext_total[3] = {0, 0, 0};
     double r_max = 0.0;
@@ -761,20 +762,21 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     const bool move = ctx->P.n > 0 && d.fixed_particles != 1;
     const bool dem = move && d.fixed_particles == 0;
     const bool first = !ctx->stepped;
-    if (first) {
-        ctx->stepped = true;
-        if (dem) {
-            // F(t = 0) for the first Velocity-Verlet position update needs the
-            // neighbour lists of the initial positions
-            dp.hin = ctx->hcur;
-            dp.hout = 1 - ctx->hcur;
-            dp.P = ctx->P;
-            CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
-            launch_bins(dp, sm);
-            launch_neighbours(dp, sm);
-            launch_dem_subcycle(dp, 0, 1, 0, sm);
-            ctx->launches += 3;
-        }
+    const bool init_dem = dem && (first || ctx->dem_restart);
+    ctx->dem_restart = false;
+    if (first) ctx->stepped = true;
+    if (init_dem) {
+        // the force of the first Velocity-Verlet position update at the current
+        // state (F(t = 0) on the first step, where the averaged fluid force is
+        // still zero) needs the neighbour lists of the current positions
+        dp.hin = ctx->hcur;
+        dp.hout = 1 - ctx->hcur;
+        dp.P = ctx->P;
+        CK(cudaMemsetAsync(ctx->P.bin_count, 0, sizeof(int) * dp.nbins[0] * dp.nbins[1] * dp.nbins[2], sm));
+        launch_bins(dp, sm);
+        launch_neighbours(dp, sm);
+        launch_dem_subcycle(dp, 0, 1, 0, sm);
+        ctx->launches += 3;
     }
     // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
     CK(prof_mark(ctx));
@@ -952,7 +954,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
     if (n_steps < 0) return fail(ctx, LBM_ERR_INVALID, "n_steps must be >= 0");
     DemParams dp = dem_params(ctx);
     for (int step = 0; step < n_steps; ++step) {
-        if (ctx->stepped && !ctx->profiling) {
+        if (ctx->stepped && !ctx->profiling && !ctx->dem_restart) {
             bool done = false;
             lbm_status st = graph_step(ctx, dp, done);
             if (st != LBM_OK) return st;
@@ -996,6 +998,25 @@ lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* 
             if (torque_hyd) torque_hyd[3 * i + a] = fp[6 * i + 3 + a];
         }
     return check_status(ctx);
+}
+
+lbm_status lbm_set_motion(lbm_ctx* ctx, int mode) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (mode < 0 || mode > 2) return fail(ctx, LBM_ERR_INVALID, "mode must be 0 (DEM), 1 (fixed) or 2 (prescribed motion)");
+    if (mode == ctx->dem.fixed_particles) return LBM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // captured steps hold the old step structure
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ctx->step_graph[a][b]) {
+                cudaGraphExecDestroy(ctx->step_graph[a][b]);
+                ctx->step_graph[a][b] = nullptr;
+                ctx->graph_launches[a][b] = 0;
+            }
+    // the DEM's first Velocity-Verlet update needs F at the current state
+    if (mode == 0 && ctx->stepped) ctx->dem_restart = true;
+    ctx->dem.fixed_particles = mode;
+    return LBM_OK;
 }
 
 lbm_status lbm_set_particle_velocity(lbm_ctx* ctx, int n, const double* vel, const double* omega) {

@@ -26,6 +26,7 @@ STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CU
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
+           'lbm_set_motion',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
            'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
@@ -84,6 +85,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_step.argtypes = [c_void_p, c_int]
     lib.lbm_get_particle_state.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_set_particle_velocity.argtypes = [c_void_p, c_int, dp, dp]
+    lib.lbm_set_motion.argtypes = [c_void_p, c_int]
     lib.lbm_get_fields.argtypes = [c_void_p, dp, dp, P(ctypes.c_ubyte)]
     lib.lbm_get_owner.argtypes = [c_void_p, P(c_int)]
     lib.lbm_get_pdfs.argtypes = [c_void_p, dp]
@@ -209,6 +211,12 @@ def lbm_set_particle_velocity(ctx, vel=None, omega=None):
         if a is not None and len(a) != n:
             raise ValueError('vel and omega need the same number of rows')
     _check(load_library().lbm_set_particle_velocity(ctx.handle, n, _dptr(arrs[0]), _dptr(arrs[1])), ctx.handle)
+
+
+def lbm_set_motion(ctx, mode):
+    """Move particles by the DEM (MOTION_DEM), hold them (MOTION_FIXED) or move them by their set
+    velocities (MOTION_PRESCRIBED) from the next step on."""
+    _check(load_library().lbm_set_motion(ctx.handle, int(mode)), ctx.handle)
 
 
 def lbm_step(ctx, n_steps=1):

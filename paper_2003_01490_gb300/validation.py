@@ -11,6 +11,11 @@ against the paper's own simulation results instead.
   The paper prints them for L = 0.505, 1 and Re_s = G D^2 / nu = 1, 25
   (TRT+aB column of its drag/lift tables), next to the correlation of its
   reference.
+* :func:`sphere_wall_rebound` -- Sec. 4.4: a sphere (St = 27) driven towards
+  the bottom wall of a closed box with the prescribed approach velocity, then
+  released (DEM with gravity) when the gap is below one diameter; reports the
+  rebound height H_r = max gap / D after the first contact, which the paper
+  tabulates against n_sub (mean 0.3274 at n_sub = 10).
 * :func:`artificial_acceleration` -- Sec. 2.3.3: a sphere whose settling
   velocity is prescribed every step, u_p(t) = -u_s (1 - exp(-c_acc t / t_St)),
   with a density probe moving along at x_p + (D, 0, 0) (trilinear
@@ -163,6 +168,74 @@ def artificial_acceleration(D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.3
                 wall_s=round(wall, 1))
 
 
+# Sec. 4.4, St = 27 (the experiments' fluid and sphere): Re, rho_f, mu_f, D_p, rho_p, box / D_p
+SPHERE_WALL_ST27 = dict(Re=30.0, rho_f=965.0, mu_f=0.1, D_p=0.006, rho_p=7800.0, box=(12, 12, 48), e_dry=0.97)
+# the paper's rebound heights for n_sub = 10 (ten runs, start perturbed by up to a cell): min, max, mean
+PAPER_REBOUND_NSUB10 = (0.3269, 0.3276, 0.3274)
+
+
+def sphere_wall_rebound(n_sub=10, D=20.0, dz=0.0, u_s=0.02, c_acc=10.0, storage='f32', setup=SPHERE_WALL_ST27,
+                        max_steps=200000, log=None):
+    """Rebound height H_r = max gap / D after the first contact of a sphere
+    hitting the bottom wall of a closed box (Sec. 4.4): its settling velocity
+    is prescribed by the artificial acceleration until the gap is below one
+    diameter, then it moves freely under gravity and buoyancy (DEM). Lattice
+    units from D cells per diameter and u_s; gravity from 9.81 m/s^2 with the
+    time step that matches the fluid's viscosity."""
+    nx, ny, nz = (int(b * D) for b in setup['box'])
+    nu = u_s * D / setup['Re']
+    dx = setup['D_p'] / D
+    dt = nu * dx * dx / (setup['mu_f'] / setup['rho_f'])
+    g = 9.81 * dt * dt / dx
+    ratio = setup['rho_p'] / setup['rho_f']
+    r, d = L.lbm_default_params()
+    r.tau = 3.0 * nu + 0.5
+    d.fixed_particles = L.MOTION_PRESCRIBED
+    d.n_sub = int(n_sub)
+    d.e_dry = setup['e_dry']
+    d.gravity[2] = -g
+    grid = L.make_grid((nx, ny, nz), (0, 0, 0))
+    ctx = L.lbm_create(grid, r, (0.0, 0.0, 0.0), d, storage, max_particles=1)
+    R = D / 2.0
+    z0 = nz - 1.5 * D + dz
+    L.lbm_add_spheres(ctx, [[nx / 2.0, ny / 2.0, z0]], np.zeros((1, 3)), np.zeros((1, 3)), np.array([R]),
+                      np.array([ratio]))
+    t_st = ratio * D * D / (18.0 * nu)
+    t0 = time.time()
+    step, z = 0, z0
+    while z - R >= D and step < max_steps:   # prescribed approach until the gap is below D
+        step += 1
+        L.lbm_set_particle_velocity(ctx, np.array([[0.0, 0.0, -u_s * (1.0 - math.exp(-c_acc * step / t_st))]]))
+        L.lbm_step(ctx, 1)
+        z = L.lbm_get_particle_state(ctx)['pos'][0, 2]
+    release = step
+    L.lbm_set_motion(ctx, L.MOTION_DEM)
+    contact, h_max, falling = None, -1.0, 0
+    while step < max_steps:
+        L.lbm_step(ctx, 1)
+        step += 1
+        gap = (L.lbm_get_particle_state(ctx)['pos'][0, 2] - R) / D
+        if contact is None:
+            if gap <= 0.0:
+                contact = step
+            continue
+        if gap > h_max:
+            h_max, falling = gap, 0
+        elif h_max > 0.0:
+            falling += 1
+            if falling > 200:   # well past the apex of the rebound
+                break
+        if log and step % 1000 == 0:
+            log('step %d: gap/D %.4f, H_r so far %.4f' % (step, gap, h_max))
+    wall = time.time() - t0
+    del ctx
+    mn, mx, mean = PAPER_REBOUND_NSUB10
+    return dict(case='sphere-wall rebound', St=round(ratio * setup['Re'] / 9.0, 1), n_sub=n_sub, D=D, dz=dz,
+                shape=[nx, ny, nz], tau=r.tau, g=g, storage=storage, release_step=release, contact_step=contact,
+                steps=step, H_r=round(h_max, 4),
+                paper_n_sub10=dict(min=mn, max=mx, mean=mean), wall_s=round(wall, 1))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split('\n')[0])
     sub = ap.add_subparsers(dest='case', required=True)
@@ -175,6 +248,12 @@ def main(argv=None):
     a.add_argument('--block', type=int, default=1000)
     a.add_argument('--re-def', choices=('particle', 'shear'), default='particle')
     a.add_argument('--verbose', action='store_true')
+    c = sub.add_parser('rebound')
+    c.add_argument('--n-sub', type=int, nargs='+', default=[10])
+    c.add_argument('--dz', type=float, nargs='+', default=[0.0])
+    c.add_argument('--D', type=float, default=20.0)
+    c.add_argument('--storage', default='f32')
+    c.add_argument('--verbose', action='store_true')
     b = sub.add_parser('acceleration')
     b.add_argument('--D', type=float, default=20.0)
     b.add_argument('--storage', default='f32')
@@ -186,6 +265,11 @@ def main(argv=None):
                 res = shear_drag_lift(Ld, re, D=args.D, storage=args.storage, max_steps=args.max_steps,
                                       block=args.block, re_def=args.re_def, log=print if args.verbose else None)
                 print(json.dumps(res), flush=True)
+    elif args.case == 'rebound':
+        for n in args.n_sub:
+            for dz in args.dz:
+                print(json.dumps(sphere_wall_rebound(n_sub=n, D=args.D, dz=dz, storage=args.storage,
+                                                     log=print if args.verbose else None)), flush=True)
     else:
         print(json.dumps(artificial_acceleration(D=args.D, storage=args.storage, max_steps=args.max_steps)))
 

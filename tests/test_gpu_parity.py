@@ -253,6 +253,33 @@ def test_prescribed_motion(L, storage, tol):
     assert refills > 0
 
 
+def test_prescribed_approach_then_free_motion_f64(L):
+    # Sec. 4.4: the approach velocity is prescribed, then the sphere moves
+    # freely (DEM with gravity) from the current state on
+    case = prescribed_case('f64')
+    case['dem'] = dict(fixed_particles=2, gravity=(0.0, 0.0, -2e-5))
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    for t in range(1, 16):
+        u = prescribed_velocity(t)
+        ora.U = u.copy()
+        L.lbm_set_particle_velocity(ctx, u)
+        ora.step(1)
+        L.lbm_step(ctx, 1)
+    ora.set_motion(dem=True)
+    L.lbm_set_motion(ctx, L.MOTION_DEM)
+    for _ in range(3):
+        ora.step(5)
+        L.lbm_step(ctx, 5)
+        st = L.lbm_get_particle_state(ctx)
+        assert rel_l2(st['pos'], ora.X) < F64_TOL
+        assert rel_l2(st['vel'], ora.U) < 1e-10
+    rho, u, flags = L.lbm_get_fields(ctx)
+    assert np.array_equal((flags & L.FLAG_SOLID) != 0, ora.owner >= 0)
+    r_o, u_o = ora.fields()
+    assert rel_l2(u, u_o) < F64_TOL and rel_l2(rho, r_o) < F64_TOL
+
+
 def test_sphere_wall_workload_first_300_steps_f64(L):
     from paper_2003_01490_gb300 import workloads
     w = workloads.sphere_wall()
