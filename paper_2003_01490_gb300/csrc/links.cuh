@@ -241,8 +241,7 @@ static __constant__ signed char k_c[Q][3] = {{0, 0, 0},   {0, 1, 0},   {0, -1, 0
                                       {0, 1, -1},  {0, -1, -1}, {-1, 0, -1}, {1, 0, -1}};
 static __constant__ signed char k_opp[Q] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 16, 15, 18, 17, 12, 11, 14, 13};
 
-
-// inclusive prefix sum over the warp and the lane holding rank k of it
+// inclusive prefix sum over the warp
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -250,15 +249,6 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
         if (lane >= o) v += t;
     }
     return v;
-}
-__device__ __forceinline__ int owner_lane(int incl, int k) {
-    int src = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int t = __shfl_sync(0xffffffffu, incl, src + step - 1);
-        if (t <= k) src += step;
-    }
-    return src > 31 ? 31 : src;
 }
 
 }  // namespace lbmdem

@@ -34,15 +34,6 @@ __device__ __forceinline__ double min_image_dd(double d, int n, int per) {
     }
     return d;
 }
-__device__ __forceinline__ float min_image_ff(float d, int n, int per) {
-    if (per) {
-        float half = 0.5f * (float)n;
-        if (d > half) d -= (float)n;
-        if (d < -half) d += (float)n;
-    }
-    return d;
-}
-
 // ------------------------------------------------------------ tile scatter
 
 __device__ int axis_pieces(double xc, double r, int n, int per, int (&a)[2], int (&b)[2]) {

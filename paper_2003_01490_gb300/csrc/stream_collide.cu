@@ -29,7 +29,7 @@
 // base cell, g the fractional offset common to all links) are summed exactly
 // in integers; the remainder is summed per warp in float32 and per particle
 // in 64-bit fixed point (scale 2^32) through integer atomics. No float64
-// instruction runs per cell or link on the float32 path.
+// arithmetic runs per cell or link on the float32 path.
 #include "common.cuh"
 #include "launch.h"
 #include "links.cuh"
@@ -39,21 +39,15 @@
 #ifndef LBM_SC_MIN_BLOCKS
 #define LBM_SC_MIN_BLOCKS 4
 #endif
+// the same for float64 storage
+#ifndef LBM_SC_MIN_BLOCKS_F64
+#define LBM_SC_MIN_BLOCKS_F64 2
+#endif
 // longest chunk of consecutive z planes marched by one block (shorter when
 // the box is too small to give every SM several blocks); tuned on GB300
 #ifndef LBM_SC_ZCHUNK
 #define LBM_SC_ZCHUNK 24
 #endif
-// the same for float64 storage
-#ifndef LBM_SC_MIN_BLOCKS_F64
-#define LBM_SC_MIN_BLOCKS_F64 2
-#endif
-// cache policy: 0 default loads and stores, 1 streaming (evict-first) stores,
-// 2 streaming loads and stores
-#ifndef LBM_SC_HINTS
-#define LBM_SC_HINTS 0
-#endif
-
 namespace lbmdem {
 
 template <typename S, typename T>
@@ -169,27 +163,6 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
     return v;
 }
 
-template <typename S>
-__device__ __forceinline__ typename Store<S>::T sc_load(const S* p) {
-#if LBM_SC_HINTS >= 2
-    if constexpr (sizeof(S) == 8) return (typename Store<S>::T)__ldcs(reinterpret_cast<const double*>(p));
-    else if constexpr (sizeof(S) == 4) return (typename Store<S>::T)__ldcs(reinterpret_cast<const float*>(p));
-    else return Store<S>::load(p);
-#else
-    return Store<S>::load(p);
-#endif
-}
-template <typename S>
-__device__ __forceinline__ void sc_store(S* p, typename Store<S>::T v) {
-#if LBM_SC_HINTS >= 1
-    if constexpr (sizeof(S) == 8) __stcs(reinterpret_cast<double*>(p), (double)v);
-    else if constexpr (sizeof(S) == 4) __stcs(reinterpret_cast<float*>(p), (float)v);
-    else Store<S>::store(p, v);
-#else
-    Store<S>::store(p, v);
-#endif
-}
-
 // TRT+aB collision of one fluid cell (in place) and the store of its PDFs
 template <typename S, typename T>
 __device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], uint8_t fl, long long N, int idx) {
@@ -252,7 +225,7 @@ __device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], 
     }
     if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sc_store<S>(a.dst + q * N + idx, f[q]);
+    for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + q * N + idx, f[q]);
 }
 
 // a lane's open force sums between rows: particle, float sums and the exact
@@ -348,7 +321,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
             const int OZ[3] = {z == 0 ? (nz - 1) * plane : -plane, 0, z == nz - 1 ? (1 - nz) * plane : plane};
 #pragma unroll
             for (int q = 0; q < Q; ++q)
-                f[q] = sc_load<S>(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
+                f[q] = Store<S>::load(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
 #pragma unroll
             for (int q = 1; q < Q; ++q)
                 if (f[q] != f[q]) lmask |= 1u << q;   // marker of a solid upstream cell
