@@ -48,6 +48,10 @@
 #ifndef LBM_SC_ZCHUNK
 #define LBM_SC_ZCHUNK 24
 #endif
+// x extent of a block (a multiple of 32; 256 / LBM_SC_BX rows in y)
+#ifndef LBM_SC_BX
+#define LBM_SC_BX 128
+#endif
 namespace lbmdem {
 
 template <typename S, typename T>
@@ -445,7 +449,7 @@ void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
     a.acc_i = p.P.acc_i;
     a.acc_k = p.P.acc_k;
     const int nx = p.g.n[0];
-    int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
+    int bx = nx >= LBM_SC_BX ? LBM_SC_BX : ((nx + 31) / 32) * 32;
     int by = 256 / bx;
     dim3 block(bx, by, 1);
     const int bxy = ((nx + bx - 1) / bx) * ((p.g.n[1] + by - 1) / by);
