@@ -261,13 +261,20 @@ def dist_setup(n):
 
 
 def allreduce_max(v, world):
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device='cuda')
+    dev = 'cuda' if dist.get_backend() == 'nccl' else 'cpu'
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mlups(world, cells_per_rank, steps, ms_max):
+    """Cell updates of all ranks' replicas over the slowest rank's time."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e6
 
 
 def barrier(world):
@@ -339,7 +346,7 @@ def run_ours(args, rank, world, local):
     n_solid = int(solid.sum())
     n_links = count_links(solid, w['periodic'])
     ms_max = allreduce_max(ms, world)
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_mlups(world, cells, args.steps, ms_max)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     bf, bs = bytes_per_cell(storage)
