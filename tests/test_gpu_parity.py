@@ -332,18 +332,28 @@ def test_reduced_suspension(L, suspension_oracle, storage, tol_u, tol_x):
         assert rel_l2(st['force_hyd'], ora.Ffp) < 1e-10
 
 
-def test_full_size_suspension_mapping_sampled(L):
+@pytest.fixture(scope='module')
+def full_size(L):
+    """The 256 x 256 x 512 suspension (10,000 spheres) in the float32 launch
+    configuration bench.py times, spheres held in place with the workload's
+    velocities and seeded angular velocities, no gravity."""
+    from paper_2003_01490_gb300 import workloads
+    w = workloads.suspension()
+    om = np.random.default_rng(17).normal(0.0, 1e-4, size=(len(w['radius']), 3))
+    case = dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage='f32',
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], om),
+                dem=dict(w['dem'], fixed_particles=1, gravity=(0.0, 0.0, 0.0), fluid_counterforce=0))
+    ctx = build_gpu(case)
+    return dict(w=w, omega=om, ctx=ctx, case=case)
+
+
+def test_full_size_suspension_mapping_sampled(L, full_size):
     """256 x 256 x 512 cells, 10,000 spheres: the flags and owners of sampled
     cells equal a brute-force float64 evaluation over every nearby sphere."""
     from scipy.spatial import cKDTree
-    from paper_2003_01490_gb300 import workloads
     from oracle import Domain
     from oracle.particles import map_cells
-    w = workloads.suspension()
-    case = dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage='f32',
-                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']),
-                dem=dict(w['dem'], fixed_particles=1))
-    ctx = build_gpu(case)
+    w, ctx = full_size['w'], full_size['ctx']
     _, _, flags = L.lbm_get_fields(ctx)
     owner = L.lbm_get_owner(ctx)
     nx, ny, nz = w['shape']
@@ -366,6 +376,54 @@ def test_full_size_suspension_mapping_sampled(L):
         if want_owner >= 0:
             assert owner[z, y, x] == want_owner, (x, y, z)
         assert bool(fl & L.FLAG_SHELL) == bool(sh[0]), (x, y, z)
+
+
+def test_full_size_suspension_first_step_sampled(L, full_size):
+    """The same full-size launch, one step from rest: the post-collision PDFs
+    of sampled fluid cells next to sphere surfaces (particle links with CLI
+    values of moving, spinning walls) and of random fluid cells equal the
+    oracle's stream, boundary condition and collision evaluated on the 3x3x3
+    neighbourhood of each cell (its own mapping of the nearby spheres, its own
+    rest equilibrium as the start)."""
+    from scipy.spatial import cKDTree
+    from oracle import Domain, Params
+    from oracle.coupling import stream_and_couple
+    from oracle.lbm import collide
+    from oracle.particles import cell_centres, map_cells
+    w, ctx, om = full_size['w'], full_size['ctx'], full_size['omega']
+    nx, ny, nz = w['shape']
+    L.lbm_step(ctx, 1)
+    f_gpu = L.lbm_get_pdfs(ctx).reshape(19, nz, ny, nx)
+    r = np.random.default_rng(23)
+    # cells half a cell outside random sphere surfaces, and random cells
+    k = r.choice(len(w['radius']), 240, replace=False)
+    d = r.normal(size=(240, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    near = np.floor(w['pos'][k] + (w['radius'][k] + 0.6)[:, None] * d).astype(int)
+    cells = np.concatenate([near, r.integers(0, (nx, ny, nz), size=(80, 3))]) % np.array([nx, ny, nz])
+    L3 = np.array([nx, ny, nz], float)
+    tree = cKDTree(w['pos'], boxsize=L3)
+    dom_w = Domain(3, 3, 3, periodic=(False, False, False))
+    centres_w = cell_centres(dom_w)
+    s_bulk, s_shell = Params(tau=w['tau']).rates()
+    ft_w = equilibrium(np.ones((3, 3, 3)), np.zeros((3, 3, 3, 3)))
+    checked = links_seen = 0
+    for x, y, z in cells:
+        js = sorted(tree.query_ball_point([x + 0.5, y + 0.5, z + 0.5], r=w['radius'].max() + 2.0 + 2.0))
+        origin = np.array([x - 1, y - 1, z - 1], float)
+        Xw = w['pos'][js] - origin
+        Xw -= L3 * np.round((Xw - 1.5) / L3)            # image nearest to the window
+        Rw, Uw, Ow = w['radius'][js], w['vel'][js], om[js]
+        owner_w, shell_w = map_cells(centres_w, Xw, Rw, dom_w, 2.0)
+        if owner_w[1, 1, 1] >= 0:
+            continue
+        f_w, _, _ = stream_and_couple(ft_w, dom_w, owner_w, Xw, Uw, Ow, Rw)
+        links_seen += int((owner_w >= 0).any())
+        want = collide(f_w[:, 1:2, 1, 1], np.zeros(3), s_bulk, s_shell, shell_w[1:2, 1, 1])[:, 0]
+        got = f_gpu[:, z, y, x]
+        assert np.abs(got - want).max() < 1e-8, (x, y, z, np.abs(got - want).max())
+        checked += 1
+    assert checked > 200 and links_seen > 150
 
 
 @pytest.mark.parametrize('storage,bound', [('f16', 2e-2), ('bf16', 1e-1)])
