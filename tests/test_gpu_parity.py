@@ -384,7 +384,8 @@ def test_full_size_suspension_first_step_sampled(L, full_size):
     values of moving, spinning walls) and of random fluid cells equal the
     oracle's stream, boundary condition and collision evaluated on the 3x3x3
     neighbourhood of each cell (its own mapping of the nearby spheres, its own
-    rest equilibrium as the start)."""
+    rest equilibrium as the start), and the force and torque of sampled spheres
+    against the oracle on the box around each."""
     from scipy.spatial import cKDTree
     from oracle import Domain, Params
     from oracle.coupling import stream_and_couple
@@ -424,6 +425,26 @@ def test_full_size_suspension_first_step_sampled(L, full_size):
         assert np.abs(got - want).max() < 1e-8, (x, y, z, np.abs(got - want).max())
         checked += 1
     assert checked > 200 and links_seen > 150
+    # the momentum-exchange force and torque of sampled spheres (Eqs. (15)-(17)
+    # with the missing links), from the oracle on the box around each sphere
+    from oracle.coupling import missing_links
+    st = L.lbm_get_particle_state(ctx)
+    for i in r.choice(len(w['radius']), 12, replace=False):
+        R = w['radius'][i]
+        h = int(np.ceil(R)) + 3
+        base = np.floor(w['pos'][i]).astype(int) - h
+        dom_b = Domain(2 * h + 1, 2 * h + 1, 2 * h + 1, periodic=(False, False, False))
+        js = sorted(tree.query_ball_point(w['pos'][i], r=R + w['radius'].max() + 2 * h))
+        Xb = w['pos'][js] - base
+        Xb -= L3 * np.round((Xb - (h + 0.5)) / L3)
+        owner_b, _ = map_cells(cell_centres(dom_b), Xb, w['radius'][js], dom_b, 2.0)
+        ft_b = equilibrium(np.ones(owner_b.shape), np.zeros((3,) + owner_b.shape))
+        _, F, T = stream_and_couple(ft_b, dom_b, owner_b, Xb, w['vel'][js], om[js], w['radius'][js])
+        Fm, Tm = missing_links(dom_b, owner_b, Xb, w['radius'][js])
+        me = js.index(i)
+        want_F, want_T = F[me] + Fm[me], T[me] + Tm[me]
+        assert np.abs(st['force_hyd'][i] - want_F).max() < 1e-5 * np.abs(want_F).max() + 1e-9, i
+        assert np.abs(st['torque_hyd'][i] - want_T).max() < 1e-5 * np.abs(want_T).max() + 1e-9, i
 
 
 @pytest.mark.parametrize('storage,bound', [('f16', 2e-2), ('bf16', 1e-1)])
