@@ -205,6 +205,18 @@ lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *f);
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
 
+/* Checkpoints: the whole simulation state (device memory of the context and
+ * the host-side step state) in one host buffer of lbm_checkpoint_bytes()
+ * bytes. lbm_save copies it out (synchronises the stream; LBM_ERR_INVALID if
+ * the buffer is smaller); lbm_restore puts it back into a context created
+ * with the same grid, storage format and max_particles (LBM_ERR_INVALID
+ * otherwise, or for a buffer that is not a checkpoint). Stepping a restored
+ * context continues exactly where the saved one stood (bit for bit in the
+ * float32 and 16-bit formats, whose particle sums are exact integers). */
+lbm_status lbm_checkpoint_bytes(const lbm_ctx *ctx, size_t *bytes);
+lbm_status lbm_save(lbm_ctx *ctx, void *buf, size_t bytes);
+lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes);
+
 /* Wait for all queued work and report device-side errors (sticky). */
 lbm_status lbm_sync(lbm_ctx *ctx);
 

@@ -1,6 +1,7 @@
 // api.cu -- C ABI of the library (declared in include/lbmdem.h): context
 // management, device memory layout, particle insertion and the per-step
 // launch sequence of Algorithm 1 (Sec. 4.2).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1000,12 +1001,24 @@ lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* 
     return check_status(ctx);
 }
 
-lbm_status lbm_set_motion(lbm_ctx* ctx, int mode) {
-    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
-    if (mode < 0 || mode > 2) return fail(ctx, LBM_ERR_INVALID, "mode must be 0 (DEM), 1 (fixed) or 2 (prescribed motion)");
-    if (mode == ctx->dem.fixed_particles) return LBM_OK;
-    CK(cudaStreamSynchronize(ctx->stream));
-    // captured steps hold the old step structure
+// ------------------------------------------------------------ checkpoints
+
+// a checkpoint: this header, the host-side insertion copies (fixed size for
+// max_particles) and the whole device arena
+struct CkptHeader {
+    char magic[8];
+    int32_t version, storage, max_particles, n[3];
+    uint64_t arena_bytes;
+    int32_t cur, hcur, stepped, dem_restart, motion, np;
+    double ext_total[3], r_max;
+};
+constexpr char CKPT_MAGIC[8] = {'L', 'B', 'M', 'D', 'E', 'M', 'C', 'K'};
+
+static size_t ckpt_bytes(const lbm_ctx* ctx) {
+    return sizeof(CkptHeader) + 4 * sizeof(double) * (size_t)ctx->max_particles + ctx->bytes;
+}
+
+static void reset_graphs(lbm_ctx* ctx) {
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             if (ctx->step_graph[a][b]) {
@@ -1013,6 +1026,85 @@ lbm_status lbm_set_motion(lbm_ctx* ctx, int mode) {
                 ctx->step_graph[a][b] = nullptr;
                 ctx->graph_launches[a][b] = 0;
             }
+}
+
+lbm_status lbm_checkpoint_bytes(const lbm_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return fail(nullptr, LBM_ERR_INVALID, "NULL argument");
+    *bytes = ckpt_bytes(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t bytes) {
+    if (!ctx || !buf) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    if (bytes < ckpt_bytes(ctx)) return fail(ctx, LBM_ERR_INVALID, "buffer smaller than lbm_checkpoint_bytes()");
+    CK(cudaStreamSynchronize(ctx->stream));
+    lbm_status st = check_status(ctx);
+    if (st != LBM_OK) return st;
+    CkptHeader h{};
+    std::memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.storage = ctx->storage;
+    h.max_particles = ctx->max_particles;
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = ctx->g.n[a];
+        h.ext_total[a] = ctx->ext_total[a];
+    }
+    h.arena_bytes = ctx->bytes;
+    h.cur = ctx->cur;
+    h.hcur = ctx->hcur;
+    h.stepped = ctx->stepped;
+    h.dem_restart = ctx->dem_restart;
+    h.motion = ctx->dem.fixed_particles;
+    h.np = ctx->P.n;
+    h.r_max = ctx->r_max;
+    char* out = static_cast<char*>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    double* hd = reinterpret_cast<double*>(out + sizeof(h));
+    const size_t mp = (size_t)ctx->max_particles;
+    std::fill(hd, hd + 4 * mp, 0.0);
+    std::copy(ctx->hx.begin(), ctx->hx.end(), hd);
+    std::copy(ctx->hR.begin(), ctx->hR.end(), hd + 3 * mp);
+    CK(cudaMemcpy(out + sizeof(h) + 4 * sizeof(double) * mp, ctx->base, ctx->bytes, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx* ctx, const void* buf, size_t bytes) {
+    if (!ctx || !buf) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    CkptHeader h;
+    if (bytes < sizeof(h)) return fail(ctx, LBM_ERR_INVALID, "buffer too small for a checkpoint");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1)
+        return fail(ctx, LBM_ERR_INVALID, "not a checkpoint of this library");
+    if (h.storage != ctx->storage || h.max_particles != ctx->max_particles || h.n[0] != ctx->g.n[0] ||
+        h.n[1] != ctx->g.n[1] || h.n[2] != ctx->g.n[2] || h.arena_bytes != ctx->bytes)
+        return fail(ctx, LBM_ERR_INVALID, "checkpoint of a context with another grid, storage or capacity");
+    if (bytes < ckpt_bytes(ctx)) return fail(ctx, LBM_ERR_INVALID, "checkpoint truncated");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const char* in = static_cast<const char*>(buf);
+    const double* hd = reinterpret_cast<const double*>(in + sizeof(h));
+    const size_t mp = (size_t)ctx->max_particles;
+    CK(cudaMemcpy(ctx->base, in + sizeof(h) + 4 * sizeof(double) * mp, ctx->bytes, cudaMemcpyHostToDevice));
+    ctx->cur = h.cur;
+    ctx->hcur = h.hcur;
+    ctx->stepped = h.stepped != 0;
+    ctx->dem_restart = h.dem_restart != 0;
+    ctx->dem.fixed_particles = h.motion;
+    ctx->P.n = h.np;
+    ctx->r_max = h.r_max;
+    for (int a = 0; a < 3; ++a) ctx->ext_total[a] = h.ext_total[a];
+    ctx->hx.assign(hd, hd + 3 * (size_t)h.np);
+    ctx->hR.assign(hd + 3 * mp, hd + 3 * mp + (size_t)h.np);
+    reset_graphs(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_motion(lbm_ctx* ctx, int mode) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (mode < 0 || mode > 2) return fail(ctx, LBM_ERR_INVALID, "mode must be 0 (DEM), 1 (fixed) or 2 (prescribed motion)");
+    if (mode == ctx->dem.fixed_particles) return LBM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // captured steps hold the old step structure
+    reset_graphs(ctx);
     // the DEM's first Velocity-Verlet update needs F at the current state
     if (mode == 0 && ctx->stepped) ctx->dem_restart = true;
     ctx->dem.fixed_particles = mode;

@@ -26,7 +26,7 @@ STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CU
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
-           'lbm_set_motion',
+           'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
            'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
@@ -86,6 +86,9 @@ def load_library(path=LIB_PATH):
     lib.lbm_get_particle_state.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_set_particle_velocity.argtypes = [c_void_p, c_int, dp, dp]
     lib.lbm_set_motion.argtypes = [c_void_p, c_int]
+    lib.lbm_checkpoint_bytes.argtypes = [c_void_p, P(c_size_t)]
+    lib.lbm_save.argtypes = [c_void_p, c_void_p, c_size_t]
+    lib.lbm_restore.argtypes = [c_void_p, c_void_p, c_size_t]
     lib.lbm_get_fields.argtypes = [c_void_p, dp, dp, P(ctypes.c_ubyte)]
     lib.lbm_get_owner.argtypes = [c_void_p, P(c_int)]
     lib.lbm_get_pdfs.argtypes = [c_void_p, dp]
@@ -217,6 +220,22 @@ def lbm_set_motion(ctx, mode):
     """Move particles by the DEM (MOTION_DEM), hold them (MOTION_FIXED) or move them by their set
     velocities (MOTION_PRESCRIBED) from the next step on."""
     _check(load_library().lbm_set_motion(ctx.handle, int(mode)), ctx.handle)
+
+
+def lbm_save(ctx):
+    """The whole simulation state as a uint8 array (a checkpoint)."""
+    lib = load_library()
+    n = c_size_t(0)
+    _check(lib.lbm_checkpoint_bytes(ctx.handle, ctypes.byref(n)), ctx.handle)
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(lib.lbm_save(ctx.handle, buf.ctypes.data_as(c_void_p), n.value), ctx.handle)
+    return buf
+
+
+def lbm_restore(ctx, buf):
+    """Put a checkpoint of lbm_save back (same grid, storage and capacity)."""
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().lbm_restore(ctx.handle, buf.ctypes.data_as(c_void_p), buf.size), ctx.handle)
 
 
 def lbm_step(ctx, n_steps=1):

@@ -167,3 +167,44 @@ def test_served_jobs_equal_each_run_alone(L):
             assert np.array_equal(a['state'][k], b['state'][k]), (a['name'], k)
     summ = serve.summary(mixed)
     assert summ['jobs'] == 4 and summ['p99_latency_s'] >= summ['p50_latency_s'] > 0
+
+
+def checkpoint_case():
+    from paper_2003_01490_gb300 import workloads
+    w = workloads.suspension(shape=(48, 48, 64), n=24, D=12.0, seed=20030149, storage='f32', steps=0)
+    return dict(shape=w['shape'], periodic=w['periodic'], tau=w['tau'], storage='f32',
+                spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']), dem=w['dem'])
+
+
+def state(L, ctx):
+    st = L.lbm_get_particle_state(ctx)
+    return [st[k] for k in ('pos', 'vel', 'omega', 'force_hyd', 'torque_hyd')] + [L.lbm_get_pdfs(ctx)]
+
+
+def test_checkpoint_restore_continues_bit_for_bit(L):
+    case = checkpoint_case()
+    ctx = build_gpu(case)
+    L.lbm_step(ctx, 10)
+    buf = L.lbm_save(ctx)
+    L.lbm_step(ctx, 15)
+    a = state(L, ctx)
+    # back into the same context, and into a fresh one created the same way
+    L.lbm_restore(ctx, buf)
+    L.lbm_step(ctx, 15)
+    fresh = build_gpu(case)
+    L.lbm_restore(fresh, buf)
+    L.lbm_step(fresh, 15)
+    for b in (state(L, ctx), state(L, fresh)):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y, equal_nan=True)
+
+
+def test_restore_rejects_other_contexts_and_garbage(L):
+    ctx = build_gpu(checkpoint_case())
+    buf = L.lbm_save(ctx)
+    other = fresh(L)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_restore(other, buf)
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_INVALID']
+    with pytest.raises(L.LbmError):
+        L.lbm_restore(ctx, np.zeros(64, dtype=np.uint8))
