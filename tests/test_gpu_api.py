@@ -208,3 +208,26 @@ def test_restore_rejects_other_contexts_and_garbage(L):
     assert e.value.status == L.STATUS_CODES['LBM_ERR_INVALID']
     with pytest.raises(L.LbmError):
         L.lbm_restore(ctx, np.zeros(64, dtype=np.uint8))
+
+
+def test_unstable_runs_and_fast_particles_are_reported(L):
+    # failure detection without a GPU fault: the device status word turns a
+    # blown-up density and a particle faster than 0.5 cells per step into
+    # errors at the next synchronising call
+    ctx = build_gpu(dict(shape=(24, 24, 24), periodic=(1, 1, 0), tau=0.505, storage='f32',
+                         body_force=(0.02, 0.0, 0.0), spheres=spheres([[12.0, 12.0, 12.0]], [4.0]),
+                         dem=dict(fixed_particles=1)))
+    L.lbm_step(ctx, 500)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_sync(ctx)
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_UNSTABLE']
+    # the error is sticky in its context; a new context is unaffected
+    with pytest.raises(L.LbmError):
+        L.lbm_sync(ctx)
+    ctx2 = fresh(L)
+    add(L, ctx2, [[20.0, 18.0, 15.0]], [3.0])
+    L.lbm_set_particle_velocity(ctx2, np.array([[0.6, 0.0, 0.0]]))
+    L.lbm_step(ctx2, 1)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_sync(ctx2)
+    assert e.value.status == L.STATUS_CODES['LBM_ERR_UNSTABLE']
