@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbmdem.h"
 #include "common.cuh"
 #include "launch.h"
@@ -522,6 +524,13 @@ DemParams dem_params(lbm_ctx* ctx) {
 // record the next profiling event on the context stream (no-op when off)
 cudaError_t prof_mark(lbm_ctx* ctx) {
     if (!ctx->profiling) return cudaSuccess;
+    // an NVTX range per phase on the host side (profilers show it beside the
+    // launches); the device times come from the CUDA events
+    static const char* const PHASE_NAMES[LBM_PHASES] = {"boundary", "stream_collide", "force_finalize",
+                                                        "dem", "mapping", "refill"};
+    const size_t k = ctx->ev_used % (LBM_PHASES + 1);
+    if (k > 0) nvtxRangePop();
+    if (k < LBM_PHASES) nvtxRangePushA(PHASE_NAMES[k]);
     if (ctx->ev_used == ctx->events.size()) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
