@@ -11,6 +11,10 @@ against the paper's own simulation results instead.
   The paper prints them for L = 0.505, 1 and Re_s = G D^2 / nu = 1, 25
   (TRT+aB column of its drag/lift tables), next to the correlation of its
   reference.
+* :func:`stokes_array` -- Sec. 2.4: the normalised drag C of a periodic array
+  of fixed spheres in Stokes flow for the relaxation times of the paper's
+  sweep and the collision models SRT, TRT, TRT+B and TRT+aB, against the
+  quasi-analytical C_ref = 2.842 (the paper plots the errors).
 * :func:`sphere_wall_rebound` -- Sec. 4.4: a sphere (St = 27) driven towards
   the bottom wall of a closed box with the prescribed approach velocity, then
   released (DEM with gravity) when the gap is below one diameter; reports the
@@ -168,6 +172,44 @@ def artificial_acceleration(D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.3
                 wall_s=round(wall, 1))
 
 
+# collision models of Sec. 2.4 as relaxation parameters: magic Lambda (None: (tau - 1/2)^2, which
+# makes s- = s+, i.e. SRT), Lambda_b in the shell and in the bulk
+STOKES_MODELS = {'SRT': (None, 1.0, 1.0), 'TRT': (3.0 / 16.0, 1.0, 1.0), 'TRT+B': (3.0 / 16.0, 100.0, 100.0),
+                 'TRT+aB': (3.0 / 16.0, 100.0, 1.0)}
+C_REF_STOKES = 2.842
+
+
+def stokes_array(tau, model='TRT+aB', D=20.0, a=1e-8, storage='f64', block=500, rtol=1e-6, max_steps=400000):
+    """Normalised drag C = (F_x + pi/6 D^3 a) / (3 pi mu D u_bar) of a fixed sphere in a periodic
+    [2 x 2 x 2] D box driven by the body force a (Sec. 2.4), run until C changes by less than
+    rtol over one block; the reference is C_ref = 2.842."""
+    n = int(2 * D)
+    magic, lb_shell, lb_bulk = STOKES_MODELS[model]
+    r, d = L.lbm_default_params()
+    r.tau = tau
+    r.magic = (tau - 0.5) ** 2 if magic is None else magic
+    r.lambda_b_shell, r.lambda_b_bulk = lb_shell, lb_bulk
+    d.fixed_particles = L.MOTION_FIXED
+    ctx = L.lbm_create(L.make_grid((n, n, n), (1, 1, 1)), r, (a, 0.0, 0.0), d, storage, max_particles=1)
+    L.lbm_add_spheres(ctx, [[n / 2.0] * 3], np.zeros((1, 3)), np.zeros((1, 3)), np.array([D / 2.0]),
+                      np.array([1.0]))
+    nu = (tau - 0.5) / 3.0
+    prev, steps, C = None, 0, float('nan')
+    while steps < max_steps:
+        L.lbm_step(ctx, block)
+        steps += block
+        F = L.lbm_get_particle_state(ctx)['force_hyd'][0, 0]
+        _, u, _ = L.lbm_get_fields(ctx)
+        u_bar = u[0].sum() / n ** 3
+        C = (F + math.pi / 6.0 * D ** 3 * a) / (3.0 * math.pi * nu * D * u_bar)
+        if prev is not None and abs(C - prev) <= rtol * abs(C):
+            break
+        prev = C
+    del ctx
+    return dict(case='stokes array', model=model, tau=tau, D=D, storage=storage, steps=steps,
+                converged=steps < max_steps, C=round(C, 5), rel_err=round(C / C_REF_STOKES - 1, 5))
+
+
 # Sec. 4.4, St = 27 (the experiments' fluid and sphere): Re, rho_f, mu_f, D_p, rho_p, box / D_p
 SPHERE_WALL_ST27 = dict(Re=30.0, rho_f=965.0, mu_f=0.1, D_p=0.006, rho_p=7800.0, box=(12, 12, 48), e_dry=0.97)
 # the paper's rebound heights for n_sub = 10 (ten runs, start perturbed by up to a cell): min, max, mean
@@ -254,6 +296,10 @@ def main(argv=None):
     c.add_argument('--D', type=float, default=20.0)
     c.add_argument('--storage', default='f32')
     c.add_argument('--verbose', action='store_true')
+    d = sub.add_parser('stokes')
+    d.add_argument('--tau', type=float, nargs='+', default=[0.55, 0.6, 0.7, 0.8, 0.9, 1.0, 1.5])
+    d.add_argument('--model', nargs='+', default=list(STOKES_MODELS))
+    d.add_argument('--storage', default='f64')
     b = sub.add_parser('acceleration')
     b.add_argument('--D', type=float, default=20.0)
     b.add_argument('--storage', default='f32')
@@ -265,6 +311,10 @@ def main(argv=None):
                 res = shear_drag_lift(Ld, re, D=args.D, storage=args.storage, max_steps=args.max_steps,
                                       block=args.block, re_def=args.re_def, log=print if args.verbose else None)
                 print(json.dumps(res), flush=True)
+    elif args.case == 'stokes':
+        for m in args.model:
+            for tau in args.tau:
+                print(json.dumps(stokes_array(tau, m, storage=args.storage)), flush=True)
     elif args.case == 'rebound':
         for n in args.n_sub:
             for dz in args.dz:
