@@ -192,6 +192,13 @@ lbm_status lbm_set_particle_velocity(lbm_ctx *ctx, int n, const double *vel, con
  * the last step; both are 0 in solid cells. Synchronises the stream. */
 lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho, double *u, unsigned char *flags);
 
+/* Density at n points (pos: n x 3 doubles, lattice units; rho: n doubles):
+ * trilinear interpolation of the cell-centred density (cell i centred at
+ * i + 1/2), wrapping periodic axes and clamping at walls; solid cells count
+ * with the reference density 1 (a probe like the one of Sec. 2.3.3). n at
+ * most min(cells, 4 Mi). Synchronises the stream. */
+lbm_status lbm_sample_density(lbm_ctx *ctx, int n, const double *pos, double *rho);
+
 /* Copy the owning particle index of every cell (int32; -1 for fluid cells).
  * Synchronises the stream. */
 lbm_status lbm_get_owner(lbm_ctx *ctx, int *owner);

@@ -1168,6 +1168,29 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, unsigned char* f
     return check_status(ctx);
 }
 
+lbm_status lbm_sample_density(lbm_ctx* ctx, int n, const double* pos, double* rho) {
+    if (!ctx || (n > 0 && (!pos || !rho))) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
+    if (n < 0 || (long long)n > ctx->scratch_cells) return fail(ctx, LBM_ERR_INVALID, "n outside [0, scratch size]");
+    if (n == 0) return LBM_OK;
+    cudaStream_t sm = ctx->stream;
+    // points and results in the scratch buffer (4 doubles per scratch cell)
+    CK(cudaMemcpyAsync(ctx->scratch, pos, 24 * (size_t)n, cudaMemcpyHostToDevice, sm));
+    SampleParams sp{};
+    sp.storage = ctx->storage;
+    sp.f = ctx->f[ctx->cur];
+    sp.flags = ctx->flags;
+    sp.g = ctx->g;
+    sp.n = n;
+    sp.pos = ctx->scratch;
+    sp.out = ctx->scratch + 3 * (size_t)n;
+    launch_sample_density(sp, sm);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(rho, sp.out, 8 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    CK(cudaStreamSynchronize(sm));
+    return check_status(ctx);
+}
+
 lbm_status lbm_get_owner(lbm_ctx* ctx, int* owner) {
     if (!ctx || !owner) return fail(ctx, LBM_ERR_INVALID, "NULL argument");
     CK(cudaMemcpyAsync(owner, ctx->owner, 4 * (size_t)ctx->g.ncells, cudaMemcpyDeviceToHost, ctx->stream));

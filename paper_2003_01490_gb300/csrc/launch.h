@@ -91,6 +91,17 @@ struct FieldsParams {
 };
 void launch_fields(const FieldsParams& p, cudaStream_t st);
 
+struct SampleParams {
+    int storage;
+    const void* f;
+    const uint8_t* flags;
+    Geom g;
+    int n;
+    const double* pos;      // [3n] sample points
+    double* out;            // [n] density at each point
+};
+void launch_sample_density(const SampleParams& p, cudaStream_t st);
+
 struct FinalizeParams {
     Particles P;
     int use_fixed;          // accumulators in fixed point (float32 path)

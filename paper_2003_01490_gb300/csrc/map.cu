@@ -577,4 +577,60 @@ void launch_fields(const FieldsParams& p, cudaStream_t st) {
     }
 }
 
+// density at sample points: trilinear interpolation of the cell-centred
+// density (cell i has its centre at i + 1/2); periodic axes wrap, wall axes
+// clamp to the first and last cell; solid cells count with the reference
+// density 1
+template <typename S>
+__global__ void sample_density_kernel(const SampleParams p) {
+    using T = typename Store<S>::T;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.n) return;
+    const S* f = static_cast<const S*>(p.f);
+    const long long N = p.g.ncells;
+    int i0[3];
+    double t[3];
+    for (int d = 0; d < 3; ++d) {
+        const double g = p.pos[3 * k + d] - 0.5;
+        const double b = floor(g);
+        i0[d] = (int)b;
+        t[d] = g - b;
+    }
+    double v = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int idx3[3];
+        double wgt = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            const int o = (c >> d) & 1;
+            int i = i0[d] + o;
+            const int n = p.g.n[d];
+            if (p.g.per[d]) i = ((i % n) + n) % n;
+            else i = i < 0 ? 0 : (i >= n ? n - 1 : i);
+            idx3[d] = i;
+            wgt *= o ? t[d] : 1.0 - t[d];
+        }
+        const long long idx = ((long long)idx3[2] * p.g.n[1] + idx3[1]) * p.g.n[0] + idx3[0];
+        double rho = 1.0;
+        if (!(p.flags[idx] & FL_SOLID)) {
+            T dr = T(0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) dr += Store<S>::load(f + (long long)q * N + idx);
+            rho = 1.0 + (double)dr;
+        }
+        v += wgt * rho;
+    }
+    p.out[k] = v;
+}
+
+void launch_sample_density(const SampleParams& p, cudaStream_t st) {
+    if (p.n <= 0) return;
+    const int blocks = (p.n + 127) / 128;
+    switch (p.storage) {
+        case 0: sample_density_kernel<double><<<blocks, 128, 0, st>>>(p); break;
+        case 1: sample_density_kernel<float><<<blocks, 128, 0, st>>>(p); break;
+        case 2: sample_density_kernel<__half><<<blocks, 128, 0, st>>>(p); break;
+        default: sample_density_kernel<__nv_bfloat16><<<blocks, 128, 0, st>>>(p); break;
+    }
+}
+
 }  // namespace lbmdem

@@ -26,7 +26,7 @@ STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CU
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
-           'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore',
+           'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore', 'lbm_sample_density',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
            'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
@@ -86,6 +86,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_get_particle_state.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_set_particle_velocity.argtypes = [c_void_p, c_int, dp, dp]
     lib.lbm_set_motion.argtypes = [c_void_p, c_int]
+    lib.lbm_sample_density.argtypes = [c_void_p, c_int, dp, dp]
     lib.lbm_checkpoint_bytes.argtypes = [c_void_p, P(c_size_t)]
     lib.lbm_save.argtypes = [c_void_p, c_void_p, c_size_t]
     lib.lbm_restore.argtypes = [c_void_p, c_void_p, c_size_t]
@@ -220,6 +221,14 @@ def lbm_set_motion(ctx, mode):
     """Move particles by the DEM (MOTION_DEM), hold them (MOTION_FIXED) or move them by their set
     velocities (MOTION_PRESCRIBED) from the next step on."""
     _check(load_library().lbm_set_motion(ctx.handle, int(mode)), ctx.handle)
+
+
+def lbm_sample_density(ctx, pos):
+    """Density at points pos ((n, 3) lattice units) by trilinear interpolation."""
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    out = np.zeros(len(pos))
+    _check(load_library().lbm_sample_density(ctx.handle, len(pos), _dptr(pos), _dptr(out)), ctx.handle)
+    return out
 
 
 def lbm_save(ctx):

@@ -23,8 +23,10 @@ against the paper's own simulation results instead.
 * :func:`artificial_acceleration` -- Sec. 2.3.3: a sphere whose settling
   velocity is prescribed every step, u_p(t) = -u_s (1 - exp(-c_acc t / t_St)),
   with a density probe moving along at x_p + (D, 0, 0) (trilinear
-  interpolation); the paper shows the probe's spectrum as a figure only, so
-  the run reports the probe series.
+  interpolation, every step); the paper shows the probe's spectrum for TRT,
+  TRT+B (10, 100) and TRT+aB as a figure and states that the fluctuations
+  stay below 0.01 % of the mean density, so the run reports the relative
+  fluctuation and the spectrum's power per frequency band for each model.
 
 Command line: ``python -m paper_2003_01490_gb300.validation shear --re 1``
 prints one JSON line per case.
@@ -124,28 +126,22 @@ def shear_drag_lift(L_dist, re, D=20.0, storage='f32', box=(48, 16, 8), u_w=0.1,
     return out
 
 
-def trilinear(field, p):
-    """Trilinear interpolation of a cell-centred field [z][y][x] at point p."""
-    nz, ny, nx = field.shape
-    g = np.asarray(p, dtype=np.float64) - 0.5
-    i0 = np.floor(g).astype(int)
-    t = g - i0
-    v = 0.0
-    for dz in (0, 1):
-        for dy in (0, 1):
-            for dx in (0, 1):
-                wgt = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
-                v += wgt * field[(i0[2] + dz) % nz, (i0[1] + dy) % ny, (i0[0] + dx) % nx]
-    return v
+# Lambda_b of the settling test of Sec. 2.3.3: (shell, bulk)
+ACCEL_MODELS = {'TRT': (1.0, 1.0), 'TRT+B(10)': (10.0, 10.0), 'TRT+B(100)': (100.0, 100.0),
+                'TRT+aB': (100.0, 1.0)}
 
 
-def artificial_acceleration(D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.34, c_acc=10.0,
-                            storage='f32', t_ref_units=24.0, probe_every=50, max_steps=None):
-    """Sphere with prescribed settling velocity and a density probe moving with it."""
+def artificial_acceleration(model='TRT+aB', D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.34,
+                            c_acc=10.0, storage='f32', t_ref_units=24.0, max_steps=None):
+    """Sphere with the prescribed settling velocity of Sec. 2.3.3 and a
+    density probe moving with it at x_p + (D, 0, 0), sampled every step.
+    Reports the probe's relative density fluctuation over the second half of
+    the run and the share of its power spectrum in three frequency bands."""
     nx, ny, nz = int(box[0] * D), int(box[1] * D), int(box[2] * D)
     nu = u_s * D / re
     r, d = L.lbm_default_params()
     r.tau = 3.0 * nu + 0.5
+    r.lambda_b_shell, r.lambda_b_bulk = ACCEL_MODELS[model]
     d.fixed_particles = L.MOTION_PRESCRIBED
     grid = L.make_grid((nx, ny, nz), (0, 0, 1))
     ctx = L.lbm_create(grid, r, (0.0, 0.0, 0.0), d, storage, max_particles=1)
@@ -153,23 +149,34 @@ def artificial_acceleration(D=20.0, box=(4, 4, 8), u_s=0.02, re=164.0, ratio=8.3
                       np.array([D / 2.0]), np.array([ratio]))
     t_st = ratio * D * D / (18.0 * nu)
     steps = int(t_ref_units * D / u_s) if max_steps is None else max_steps
-    series = []
+    rho = np.empty(steps)
+    x = np.array([nx / 2.0, ny / 2.0, nz / 2.0])
     t0 = time.time()
     for t in range(1, steps + 1):
         u = -u_s * (1.0 - math.exp(-c_acc * t / t_st))
         L.lbm_set_particle_velocity(ctx, np.array([[0.0, 0.0, u]]))
         L.lbm_step(ctx, 1)
-        if t % probe_every == 0:
-            x = L.lbm_get_particle_state(ctx)['pos'][0]
-            rho, _, _ = L.lbm_get_fields(ctx)
-            series.append((t, trilinear(rho, x + np.array([D, 0.0, 0.0]))))
+        x[2] = (x[2] + u) % nz
+        rho[t - 1] = L.lbm_sample_density(ctx, x + np.array([D, 0.0, 0.0]))[0]
     wall = time.time() - t0
     del ctx
-    s = np.array(series)
-    late = s[len(s) // 2:, 1] if len(s) else np.zeros(1)
-    return dict(case='artificial acceleration', D=D, shape=[nx, ny, nz], tau=r.tau, storage=storage, steps=steps,
-                probe_samples=len(s), probe_rho_mean=float(late.mean()), probe_rho_std=float(late.std()),
-                wall_s=round(wall, 1))
+    late = rho[steps // 2:]
+    dev = late - late.mean()
+    power = np.abs(np.fft.rfft(dev)) ** 2
+    freq = np.fft.rfftfreq(len(dev))
+    total = power[1:].sum()
+    bands = {'low (< 1e-3 / step)': (0.0, 1e-3), 'mid (1e-3 - 1e-2)': (1e-3, 1e-2), 'high (> 1e-2)': (1e-2, 1.0)}
+    share = {k: float(power[(freq > lo) & (freq <= hi)].sum() / total) for k, (lo, hi) in bands.items()}
+    # fluctuation about the slow pressure signal of the moving sphere: the
+    # deviation from a 1000-step running mean
+    k = 1000
+    slow = np.convolve(rho, np.ones(k) / k, mode='same')
+    fast = (rho - slow)[steps // 2:steps - k // 2]
+    return dict(case='artificial acceleration', model=model, D=D, shape=[nx, ny, nz], tau=r.tau, storage=storage,
+                steps=steps, probe_rho_mean=float(late.mean()), probe_rel_fluctuation=float(dev.std() / late.mean()),
+                probe_rel_fluctuation_fast=float(fast.std() / late.mean()),
+                probe_rel_max=float(np.abs(dev).max() / late.mean()), spectrum_share=share,
+                band_power={k: float(v * total) for k, v in share.items()}, wall_s=round(wall, 1))
 
 
 # collision models of Sec. 2.4 as relaxation parameters: magic Lambda (None: (tau - 1/2)^2, which
@@ -301,6 +308,7 @@ def main(argv=None):
     d.add_argument('--model', nargs='+', default=list(STOKES_MODELS))
     d.add_argument('--storage', default='f64')
     b = sub.add_parser('acceleration')
+    b.add_argument('--model', nargs='+', default=list(ACCEL_MODELS))
     b.add_argument('--D', type=float, default=20.0)
     b.add_argument('--storage', default='f32')
     b.add_argument('--max-steps', type=int, default=None)
@@ -321,7 +329,9 @@ def main(argv=None):
                 print(json.dumps(sphere_wall_rebound(n_sub=n, D=args.D, dz=dz, storage=args.storage,
                                                      log=print if args.verbose else None)), flush=True)
     else:
-        print(json.dumps(artificial_acceleration(D=args.D, storage=args.storage, max_steps=args.max_steps)))
+        for m in args.model:
+            print(json.dumps(artificial_acceleration(m, D=args.D, storage=args.storage, max_steps=args.max_steps)),
+                  flush=True)
 
 
 if __name__ == '__main__':

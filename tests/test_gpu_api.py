@@ -231,3 +231,19 @@ def test_unstable_runs_and_fast_particles_are_reported(L):
     with pytest.raises(L.LbmError) as e:
         L.lbm_sync(ctx2)
     assert e.value.status == L.STATUS_CODES['LBM_ERR_UNSTABLE']
+
+
+def test_density_probe_interpolates_a_linear_field_exactly(L):
+    # lbm_sample_density: trilinear interpolation of the cell-centred density;
+    # a density linear in x (equilibrium at rest) is reproduced at any point
+    # between cell centres
+    shape = (24, 20, 16)
+    ctx = build_gpu(dict(shape=shape, periodic=(1, 1, 1), tau=0.7, storage='f32'))
+    nx, ny, nz = shape
+    rho_x = 1.0 + 1e-3 * np.arange(nx)
+    W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = W[:, None, None, None] * rho_x[None, None, None, :] * np.ones((1, nz, ny, 1))
+    L.lbm_set_pdfs(ctx, f.reshape(19, -1))
+    pts = np.random.default_rng(3).uniform([0.5, 0.0, 0.0], [nx - 0.5, ny, nz], size=(50, 3))
+    got = L.lbm_sample_density(ctx, pts)
+    assert np.abs(got - (1.0 + 1e-3 * (pts[:, 0] - 0.5))).max() < 1e-6
