@@ -7,11 +7,13 @@
 // float64 PDF storage and in float32 (separations and overlaps from float64
 // positions) for the other formats.
 //
-// One thread per particle gathers every interaction of its particle, so no
-// force atomics are needed; a pair is evaluated by both partners with exactly
-// mirrored operands (n_ji = -n_ij, u_ji = -u_ij, ...), which makes the pair
-// forces exactly opposite. Each particle keeps its own copy of the
-// tangential spring of every active contact (double buffered per subcycle).
+// Each particle gathers every interaction of its own (its block evaluates
+// the queued pairs with all threads, then sums them per particle in slot
+// order), so no force atomics are needed; a pair is evaluated by both
+// partners with mirrored operands (n_ji = -n_ij, u_ji = -u_ij, ...). Each
+// particle keeps its own copy of the tangential spring of every active
+// contact (double buffered per subcycle). Up to 32 particles run a whole
+// step's subcycles in one block.
 #include "common.cuh"
 #include "launch.h"
 
