@@ -24,6 +24,11 @@ Readings where the paper is silent (listed in the design notes):
     cell count of the current mapping) so that no net momentum is injected.
   * positions are wrapped into [0, L) on periodic axes after each
     position update.
+  * prescribed motion (Sec. 2.3.3 sets a sphere's velocity every step): the
+    velocity set before a step is the boundary velocity of that step, the
+    position advances by it over the step, the refill uses it; switching to
+    the DEM later evaluates the first Velocity-Verlet force at the current
+    state with the current averaged fluid force.
 """
 import math
 
