@@ -12,6 +12,8 @@
  * (Sec. 4.2), n_sub DEM subcycles with lubrication (Eqs. (25)-(33)), linear
  * spring-dashpot contact (Eqs. (39)-(52)) and Velocity Verlet (Eqs. (37)-(38)),
  * then the particle mapping update and PDF refill (Sec. 2.2, Eq. (18)).
+ * Particles may instead be held fixed or moved by prescribed velocities
+ * (lbm_dem.fixed_particles, lbm_set_motion, lbm_set_particle_velocity).
  *
  * Units are lattice units (dx = dt = rho0 = 1, c_s^2 = 1/3, Sec. 2.1). Cell
  * (i, j, k) has its centre at (i + 1/2, j + 1/2, k + 1/2); walls lie on the
@@ -45,7 +47,8 @@ typedef enum {
     LBM_ERR_INVALID = -1,   /* bad argument: size, parameter range, overlap, ... */
     LBM_ERR_OOM = -2,       /* device allocation failed or arena too small       */
     LBM_ERR_CUDA = -3,      /* a CUDA runtime call failed                        */
-    LBM_ERR_UNSTABLE = -4,  /* NaN or |rho - 1| > 0.5 detected on the device      */
+    LBM_ERR_UNSTABLE = -4,  /* NaN or |rho - 1| > 0.5 on the device, or a particle
+                               faster than 0.5 cells per step                    */
     LBM_ERR_CAPACITY = -5,  /* a fixed-capacity device list overflowed           */
     LBM_ERR_STATE = -7      /* call not allowed in the current state             */
 } lbm_status;
