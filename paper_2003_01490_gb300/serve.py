@@ -43,12 +43,26 @@ def _record(job, t_arrive, t_admit, t_done, state):
             'latency': t_done - t_arrive, 'cell_updates': cells * job['steps'], 'state': state}
 
 
+def admissions(pending, arrival, need, now, used, budget_bytes):
+    """Jobs to admit now: the waiting jobs in arrival order, as long as the
+    next one has arrived and its memory fits the budget (the first that does
+    not fit waits at the head of the queue). Returns (admitted, used)."""
+    admitted = []
+    for k in pending:
+        if arrival[k] > now or used + need[k] > budget_bytes:
+            break
+        admitted.append(k)
+        used += need[k]
+    return admitted, used
+
+
 def serve(jobs, budget_bytes, chunk=25, keep_state=False):
     """Run `jobs` (each with an 'arrival' time in seconds from the start) with
     continuous batching; returns one record per job in arrival order."""
     import torch
     order = sorted(range(len(jobs)), key=lambda k: jobs[k]['arrival'])
     need = [job_bytes(j) for j in jobs]
+    arrival = [j['arrival'] for j in jobs]
     pending = list(order)
     running = []          # [job index, ctx, stream, steps left, admit time, done event]
     used = 0
@@ -57,12 +71,12 @@ def serve(jobs, budget_bytes, chunk=25, keep_state=False):
     while pending or running:
         now = time.perf_counter() - t0
         # admission: arrived jobs in order, while the budget allows
-        while pending and jobs[pending[0]]['arrival'] <= now and used + need[pending[0]] <= budget_bytes:
-            k = pending.pop(0)
+        admitted, used = admissions(pending, arrival, need, now, used, budget_bytes)
+        for k in admitted:
+            pending.remove(k)
             st = torch.cuda.Stream()
             with torch.cuda.stream(st):
                 ctx = make_context(jobs[k])
-            used += need[k]
             running.append([k, ctx, st, jobs[k]['steps'], time.perf_counter() - t0, None])
         if not running:
             if pending:   # nothing admitted yet: wait for the next arrival
