@@ -20,7 +20,7 @@ import pytest
 
 from oracle import Domain, Params, Simulation
 from oracle.d3q19 import C, W
-from oracle.lbm import equilibrium, momentum
+from oracle.lbm import density, equilibrium, momentum
 from oracle.coupling import stream_and_couple, missing_links, refill
 from oracle.particles import map_cells, cell_centres, link_fraction
 
@@ -259,3 +259,60 @@ def test_prescribed_motion_at_rest_equals_fixed_particles():
         runs.append(sim)
     assert np.array_equal(runs[0].ft, runs[1].ft)
     assert np.array_equal(runs[0].Ffp, runs[1].Ffp)
+
+
+def refill_expect(S, s_nu, u_t=np.zeros(3), rho_bar=1.0):
+    """Eq. (18) written out for a given strain S = grad u + grad u^T."""
+    out = np.zeros(19)
+    for q in range(19):
+        cq = C[q].astype(float)
+        cu = cq @ u_t
+        out[q] = W[q] * (rho_bar + 3 * rho_bar * cu + 4.5 * rho_bar * cu * cu - 1.5 * rho_bar * u_t @ u_t
+                         - 1.5 / s_nu * rho_bar * (cq @ S @ cq - np.trace(S) / 3))
+    return out
+
+
+def test_refill_gradient_is_central_for_a_quadratic_field():
+    # Eq. (18) with second-order central differences: exact for a quadratic
+    # velocity field (a one-sided difference would pick up the curvature)
+    n = 9
+    dom = Domain(n, n, n)
+    d = cell_centres(dom) - 4.5
+    u = np.stack([2e-3 * d[..., 1] + 3e-4 * d[..., 1] ** 2,
+                  -1e-3 * d[..., 2] + 2e-4 * d[..., 0] ** 2,
+                  5e-4 * d[..., 0] - 4e-4 * d[..., 2] ** 2])
+    ft = equilibrium(np.ones((n, n, n)), u)
+    owner_old = np.full((n, n, n), -1)
+    owner_old[4, 4, 4] = 0
+    s_nu = 1 / 0.9
+    refill(ft, dom, owner_old, np.full((n, n, n), -1), np.array([[4.5, 4.5, 4.5]]), np.zeros((1, 3)),
+           np.zeros((1, 3)), s_nu, np.zeros(3))
+    G = np.array([[0.0, 2e-3, 0.0], [0.0, 0.0, -1e-3], [5e-4, 0.0, 0.0]])   # gradient at the cell
+    rho_bar = np.mean([density(ft)[4 + C[q][2], 4 + C[q][1], 4 + C[q][0]] for q in range(1, 19)])
+    assert np.abs(ft[:, 4, 4, 4] - refill_expect(G + G.T, s_nu, rho_bar=rho_bar)).max() < 1e-14
+
+
+def test_refill_falls_back_to_one_sided_differences_next_to_a_solid():
+    # a solid neighbour in +x: d u / d x from the cell's own (particle) velocity
+    # and the -x neighbour, exact for a linear field whose value at the cell is
+    # the particle velocity there
+    n = 9
+    dom = Domain(n, n, n)
+    d = cell_centres(dom) - 4.5
+    G = np.array([[1e-3, 0.0, 2e-4], [-5e-4, 3e-4, 0.0], [0.0, 1e-3, -4e-4]])
+    u0 = np.array([0.01, -0.02, 0.005])
+    u = u0[:, None, None, None] + np.einsum('ab,zyxb->azyx', G, d)
+    ft = equilibrium(np.ones((n, n, n)), u)
+    owner_old = np.full((n, n, n), -1)
+    owner_old[4, 4, 4] = 0
+    owner_new = np.full((n, n, n), -1)
+    owner_new[4, 4, 5] = 1                      # the +x neighbour is (still) solid
+    ft[:, 4, 4, 5] = equilibrium(np.array(1.2), np.array([0.1, 0.1, 0.1]))   # and its PDFs unusable
+    X = np.array([[4.5, 4.5, 4.5], [6.5, 4.5, 4.5]])
+    s_nu = 1 / 0.75
+    refill(ft, dom, owner_old, owner_new, X, np.stack([u0, u0]), np.zeros((2, 3)), s_nu, np.zeros(3))
+    fluid_nbrs = [q for q in range(1, 19) if not (C[q][0] == 1 and C[q][1] == 0 and C[q][2] == 0)
+                  and owner_new[4 + C[q][2], 4 + C[q][1], 4 + C[q][0]] < 0]
+    rho_bar = np.mean([density(ft)[4 + C[q][2], 4 + C[q][1], 4 + C[q][0]] for q in fluid_nbrs])
+    got = ft[:, 4, 4, 4]
+    assert np.abs(got - refill_expect(G + G.T, s_nu, u_t=u0, rho_bar=rho_bar)).max() < 1e-14
