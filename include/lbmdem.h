@@ -120,7 +120,9 @@ typedef struct {
 lbm_status lbm_default_params(lbm_relax *relax, lbm_dem *dem);
 
 /* Device bytes that lbm_create_in_arena() needs for this box, storage format
- * and particle capacity. */
+ * and particle capacity. Host arithmetic only (no CUDA call).
+ * Errors: LBM_ERR_INVALID (NULL grid or bytes_out, an axis of fewer than 3
+ * cells, max_particles < 0, an unknown storage format). */
 lbm_status lbm_required_bytes(const lbm_grid *grid, lbm_storage storage, int max_particles,
                               size_t *bytes_out);
 
@@ -130,8 +132,10 @@ lbm_status lbm_required_bytes(const lbm_grid *grid, lbm_storage storage, int max
  * queued on it. The fluid starts at rest with rho = 1 and no particles.
  * Device memory is allocated by the library and released by lbm_destroy().
  * Errors: LBM_ERR_INVALID (bad sizes, a box of more than 2^31 - 2^24 cells,
- * tau <= 1/2, max_particles outside [0, 4,000,000]), LBM_ERR_OOM,
- * LBM_ERR_CUDA. */
+ * tau <= 1/2, max_particles outside [0, 4,000,000], an unknown storage
+ * format, n_sub < 1, e_dry outside (0, 1], nu_p outside [0, 1), mu_p < 0, a
+ * lubrication cut-off <= 0, fixed_particles outside {0, 1, 2}; all checked
+ * before any CUDA call), LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_grid *grid, const lbm_relax *relax, const double *body_force,
                       const lbm_dem *dem, lbm_storage storage, int max_particles,
                       void *cuda_stream, lbm_ctx **out);

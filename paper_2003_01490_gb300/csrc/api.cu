@@ -596,6 +596,8 @@ lbm_status lbm_default_params(lbm_relax* relax, lbm_dem* dem) {
 lbm_status lbm_required_bytes(const lbm_grid* grid, lbm_storage storage, int max_particles, size_t* bytes_out) {
     if (!grid || !bytes_out || max_particles < 0 || grid->nx < 3 || grid->ny < 3 || grid->nz < 3)
         return fail(nullptr, LBM_ERR_INVALID, "invalid arguments");
+    if (storage < LBM_STORE_F64 || storage > LBM_STORE_BF16)
+        return fail(nullptr, LBM_ERR_INVALID, "unknown storage format");
     Sizes s = compute_sizes(grid, max_particles);
     Layout L;
     build_layout(grid, storage, max_particles, L, s);

@@ -79,3 +79,102 @@ def test_required_bytes_scales_with_storage(lib):
     assert b32 - b16 == pytest.approx(2 * 19 * 2 * n, rel=0.01)
     with pytest.raises(lbmdem.LbmError):
         lbmdem.lbm_required_bytes(lbmdem.make_grid((2, 64, 64)), 'f32', 1)
+
+
+def raw_create(lib, **change):
+    """lbm_create through the raw C call with one parameter changed; the
+    argument checks all come before the first CUDA call."""
+    from paper_2003_01490_gb300 import lbmdem
+    r, d = lbmdem.lbm_default_params()
+    shape = change.pop('shape', (16, 16, 32))
+    storage = change.pop('storage', 1)
+    max_particles = change.pop('max_particles', 4)
+    for k, v in change.items():
+        setattr(r if hasattr(r, k) else d, k, v)
+    g = lbmdem.make_grid(shape)
+    h = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(g), ctypes.byref(r), None, ctypes.byref(d), storage,
+                        max_particles, None, ctypes.byref(h))
+    return st, h.value, lib.lbm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("change, words", [
+    (dict(tau=0.5), 'tau'),
+    (dict(storage=4), 'storage'),
+    (dict(max_particles=-1), 'max_particles'),
+    (dict(max_particles=4000001), 'max_particles'),
+    (dict(shape=(2, 16, 16)), 'at least 3'),
+    (dict(shape=(2048, 1024, 1024)), '2^31'),
+    (dict(n_sub=0), 'n_sub'),
+    (dict(e_dry=0.0), 'e_dry'),
+    (dict(e_dry=1.5), 'e_dry'),
+    (dict(nu_p=1.0), 'nu_p'),
+    (dict(mu_p=-0.1), 'mu_p'),
+    (dict(lub_cut_tt=0.0), 'cut-offs'),
+    (dict(magic=0.0), 'magic'),
+    (dict(shell_width=-1.0), 'shell_width'),
+    (dict(fixed_particles=3), 'fixed_particles'),
+])
+def test_create_rejects_invalid_parameters(lib, change, words):
+    st, handle, msg = raw_create(lib, **change)
+    assert st == -1 and handle is None
+    assert words in msg
+
+
+def test_calls_on_a_null_context_fail_cleanly(lib):
+    from paper_2003_01490_gb300 import lbmdem
+    P = ctypes.POINTER
+    n = ctypes.c_int(0)
+    size = ctypes.c_size_t(0)
+    dp = P(ctypes.c_double)()
+    calls = {
+        'lbm_add_spheres': (None, 0, dp, dp, dp, dp, dp, None),
+        'lbm_step': (None, 1),
+        'lbm_sync': (None,),
+        'lbm_get_particle_state': (None, 0, dp, dp, dp, dp, dp, ctypes.byref(n)),
+        'lbm_set_particle_velocity': (None, 0, dp, dp),
+        'lbm_set_motion': (None, 0),
+        'lbm_checkpoint_bytes': (None, ctypes.byref(size)),
+        'lbm_save': (None, None, 0),
+        'lbm_restore': (None, None, 0),
+        'lbm_sample_density': (None, 0, dp, dp),
+        'lbm_get_fields': (None, dp, dp, None),
+        'lbm_get_owner': (None, None),
+        'lbm_get_pdfs': (None, dp),
+        'lbm_set_pdfs': (None, dp),
+        'lbm_profile': (None, 1),
+        'lbm_profile_read': (None, dp, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == -1, name
+        assert lib.lbm_last_error(None).decode(), name
+    assert lib.lbm_launch_count(None) == 0
+    lib.lbm_destroy(None)
+    for name in lbmdem.EXPORTS:
+        assert name in calls or name in (
+            'lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
+            'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error', 'lbm_destroy'), name
+
+
+def test_create_in_arena_and_mapping_entry_reject_bad_arguments(lib):
+    from paper_2003_01490_gb300 import lbmdem
+    r, d = lbmdem.lbm_default_params()
+    g = lbmdem.make_grid((16, 16, 32))
+    h = ctypes.c_void_p()
+    assert lib.lbm_create_in_arena(ctypes.byref(g), ctypes.byref(r), None, ctypes.byref(d), 1, 4, None,
+                                   None, 0, ctypes.byref(h)) == -1
+    assert 'arena' in lib.lbm_last_error(None).decode()
+    assert lib.lbm_create(ctypes.byref(g), ctypes.byref(r), None, ctypes.byref(d), 1, 4, None, None) == -1
+    # the allocation-free mapping entry checks its arguments before any CUDA call
+    buf = ctypes.c_void_p(16)    # never dereferenced: every call below fails its checks first
+    for args in [(ctypes.byref(g), 2.0, -1, buf, buf, buf, buf, None),
+                 (ctypes.byref(g), 2.0, 1, None, buf, buf, buf, None),
+                 (ctypes.byref(g), 2.0, 0, None, None, None, buf, None),
+                 (ctypes.byref(lbmdem.make_grid((2, 16, 16))), 2.0, 0, None, None, buf, buf, None),
+                 (ctypes.byref(g), -1.0, 0, None, None, buf, buf, None),
+                 (ctypes.byref(g), 2.0, 65537, buf, buf, buf, buf, None),
+                 (None, 2.0, 0, None, None, buf, buf, None)]:
+        assert lib.lbm_map_spheres_noalloc(*args) == -1
+    with pytest.raises(lbmdem.LbmError, match='storage'):
+        size = ctypes.c_size_t(0)
+        lbmdem._check(lib.lbm_required_bytes(ctypes.byref(g), 5, 1, ctypes.byref(size)))
