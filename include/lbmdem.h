@@ -224,7 +224,9 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *f);
  * bytes. lbm_save copies it out (synchronises the stream; LBM_ERR_INVALID if
  * the buffer is smaller); lbm_restore puts it back into a context created
  * with the same grid, storage format and max_particles (LBM_ERR_INVALID
- * otherwise, or for a buffer that is not a checkpoint). Stepping a restored
+ * otherwise, or for a buffer that is not a checkpoint, is truncated or
+ * carries a particle count, buffer parity or motion mode out of range; the
+ * context is left unchanged then). Stepping a restored
  * context continues exactly where the saved one stood (bit for bit in the
  * float32 and 16-bit formats, whose particle sums are exact integers). */
 lbm_status lbm_checkpoint_bytes(const lbm_ctx *ctx, size_t *bytes);

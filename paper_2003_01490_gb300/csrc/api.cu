@@ -1090,6 +1090,10 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* buf, size_t bytes) {
         h.n[1] != ctx->g.n[1] || h.n[2] != ctx->g.n[2] || h.arena_bytes != ctx->bytes)
         return fail(ctx, LBM_ERR_INVALID, "checkpoint of a context with another grid, storage or capacity");
     if (bytes < ckpt_bytes(ctx)) return fail(ctx, LBM_ERR_INVALID, "checkpoint truncated");
+    // the host-side state it carries must be one this context can hold
+    if (h.np < 0 || h.np > ctx->max_particles || (h.cur != 0 && h.cur != 1) || (h.hcur != 0 && h.hcur != 1) ||
+        h.motion < 0 || h.motion > 2 || !(h.r_max >= 0.0 && h.r_max <= 100.0))
+        return fail(ctx, LBM_ERR_INVALID, "checkpoint header out of range");
     CK(cudaStreamSynchronize(ctx->stream));
     const char* in = static_cast<const char*>(buf);
     const double* hd = reinterpret_cast<const double*>(in + sizeof(h));
