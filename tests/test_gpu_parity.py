@@ -253,6 +253,38 @@ def test_prescribed_motion(L, storage, tol):
     assert refills > 0
 
 
+@pytest.mark.parametrize('storage,tol', [('f64', 1e-13), ('f32', 1e-6)])
+@pytest.mark.parametrize('prescribed', [True, False])
+def test_sphere_carried_by_uniform_flow(L, storage, tol, prescribed):
+    # an exact solution of the coupled step (Algorithm 1): a sphere moving with
+    # a uniform flow in a periodic box leaves the fluid in that flow's
+    # equilibrium with zero force while it crosses cells; prescribed on an
+    # oblique path, free (DEM) along x through mirror planes of the lattice
+    n, steps = 14, 16
+    U = np.array([0.071, -0.043, 0.029]) if prescribed else np.array([0.083, 0.0, 0.0])
+    X0 = np.array([6.8, 7.3, 6.6]) if prescribed else np.array([6.8, 7.0, 7.0])
+    f0 = equilibrium(np.ones((n, n, n)), np.broadcast_to(U[:, None, None, None], (3, n, n, n)))
+    case = dict(shape=(n, n, n), periodic=(1, 1, 1), tau=0.8, storage=storage, init_pdfs=f0,
+                spheres=spheres([X0], [2.7], density=[1.7], vel=[U]),
+                dem=dict(fixed_particles=2 if prescribed else 0))
+    ora = build_oracle(case)
+    ctx = build_gpu(case)
+    ora.step(steps)
+    L.lbm_step(ctx, steps)
+    st = L.lbm_get_particle_state(ctx)
+    _, _, flags = L.lbm_get_fields(ctx)
+    solid = (flags & L.FLAG_SOLID) != 0
+    assert np.array_equal(solid, ora.owner >= 0)
+    assert np.abs(st['pos'][0] - (X0 + steps * U) % n).max() < (1e-12 if storage == 'f64' else 1e-6)
+    f = L.lbm_get_pdfs(ctx)
+    feq = equilibrium(np.array(1.0), U)
+    assert np.abs(f[:, ~solid] - feq[:, None]).max() < tol
+    assert np.abs(st['force_hyd']).max() < 1e3 * tol
+    if not prescribed:
+        assert np.abs(st['vel'][0] - U).max() < 1e3 * tol
+        assert np.abs(st['torque_hyd']).max() < 1e3 * tol
+
+
 def test_prescribed_approach_then_free_motion_f64(L):
     # Sec. 4.4: the approach velocity is prescribed, then the sphere moves
     # freely (DEM with gravity) from the current state on
