@@ -11,7 +11,7 @@ Paper passages followed (Sec. 2.2):
     per-particle force and torque sums.
   * missing fluid-solid links near other bodies get F_q = 2 w_q c_q.
   * Eq. (18): refill of cells uncovered by a particle.
-Readings (listed in the design notes):
+Readings where the paper is silent or ambiguous:
   * walls sit halfway between cells on the domain faces; a wall link uses
     Eq. (14) with delta = 1/2 and the face velocity as u_b and adds no force.
   * in the bounce-back fallback only the coefficients of Eq. (14) take
@@ -33,7 +33,9 @@ from .particles import link_fraction, rel_vec, dist2
 
 
 def _shift(pos, c, dom):
-    """Neighbour index pos + c with periodic wrap. Returns (idx, out, wall_axis)."""
+    """Neighbour index pos + c with periodic wrap; outside a wall axis the
+    neighbour is the wall of Eq. (14) with delta = 1/2. Returns (idx, out,
+    wall_axis)."""
     n = dom.shape
     idx = pos + np.asarray(c, dtype=np.int64)
     out = np.zeros(len(pos), dtype=bool)
@@ -49,7 +51,8 @@ def _shift(pos, c, dom):
 
 
 def _at(arr, idx):
-    """arr[..., z, y, x] gathered at integer positions idx (K, 3) = (x, y, z)."""
+    """arr[..., z, y, x] gathered at integer positions idx (K, 3) = (x, y, z)
+    (indexing helper)."""
     return arr[..., idx[:, 2], idx[:, 1], idx[:, 0]]
 
 
@@ -172,6 +175,8 @@ def refill(ft, dom, owner_old, owner_new, X, U, Om, s_nu, accel):
         i = owner_old[z, y, x]
 
         def neighbour(c):
+            """Neighbour pos + c if it is fluid before and after the update
+            (the cells Eq. (18)'s averages and differences may use), else None."""
             nb = pos + c
             for a in range(3):
                 if dom.periodic[a]:

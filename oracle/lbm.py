@@ -7,7 +7,7 @@ Paper passages followed:
     u = (1/rho0) sum f c (incompressible form with rho0 = 1).
   * Sec. 2.1.1, Eq. (5): collision in moment space C = M^-1 S (m^eq - M f).
   * App. A, Eq. (A.2): equilibrium moments.
-Readings where the paper is silent (each one is listed in the design notes):
+Readings where the paper is silent:
   * body force: Guo forcing in moment space, m += (I - S/2) M F with
     F_q = w_q [3 (c_q - u).a + 9 (c_q.u)(c_q.a)], and the velocity that
     enters m^eq is u = (j + a/2)/rho0.
@@ -23,7 +23,8 @@ from .d3q19 import C, W, M, M_INV, Q, RHO0, equilibrium_moments
 
 
 def equilibrium(rho, u):
-    """Incompressible second-order equilibrium (reading, see module doc).
+    """Incompressible second-order equilibrium (Sec. 2.1; its moments under M
+    are Eq. (A.2); reading, see module doc).
 
     rho: (...); u: (3, ...). Returns f_eq with shape (19, ...).
     """
@@ -47,7 +48,8 @@ def momentum(f):
 def guo_source(u, accel):
     """Forcing populations F_q = w_q [3 (c_q - u).a + 9 (c_q.u)(c_q.a)].
 
-    u: (3, ...); accel: (3,). Reading of the unspecified forcing scheme.
+    u: (3, ...); accel: (3,). Reading of the forcing scheme, which the paper
+    leaves open (the body force a of Sec. 2.4 and of the suspension).
     """
     a = np.asarray(accel, dtype=np.float64)
     cf = C.astype(np.float64)
@@ -85,7 +87,8 @@ def collide(f, accel, s_diag, s_diag_alt=None, alt_mask=None):
 
 
 def velocity_from_post_collision(ft, accel):
-    """Physical velocity of a cell whose PDFs are post-collision values.
+    """Physical velocity of a cell whose PDFs are post-collision values
+    (moments of Eq. (2) with the forcing reading of the module doc).
 
     The collision adds the body force a to j, while the velocity used in the
     collision was (j_pre + a/2)/rho0; hence u = (sum f~ c - a/2)/rho0.

@@ -12,7 +12,7 @@ Paper passages followed:
   * Sec. 4.1.2, Eqs. (39)-(52): linear spring-dashpot contact with Coulomb
     limited tangential spring.
   * App. B, Eqs. (B.1)-(B.8): particle and pair definitions.
-Readings (listed in the design notes):
+Readings where the paper is silent or ambiguous:
   * Eq. (B.1) is printed as u + (x - x_p) x omega, which is the rigid-body
     velocity with the wrong sign; the oracle uses u + omega x (x - x_p).
   * cell centres are at index + 1/2; the inside test is
@@ -39,7 +39,9 @@ CS = 1.0 / math.sqrt(3.0)
 # --------------------------------------------------------------------------
 
 def min_image(d, length, periodic):
-    """Minimum-image wrap of a coordinate difference along one axis.
+    """Minimum-image wrap of a coordinate difference along one axis (periodic
+    boxes of Sec. 4.2; the nearest image is the one the mapping and the pair
+    laws see).
 
     Works elementwise on arrays. Uses one conditional shift by the box length
     (exact in float64 for |d| < 1.5 L).
@@ -53,7 +55,8 @@ def min_image(d, length, periodic):
 
 
 def rel_vec(x, xp, dom):
-    """x - xp with minimum image on periodic axes. x, xp: (..., 3), broadcast."""
+    """x - xp with minimum image on periodic axes (Sec. 2.2 mapping and the
+    pair laws of Secs. 3.1, 4.1). x, xp: (..., 3), broadcast."""
     x = np.asarray(x, dtype=np.float64)
     xp = np.asarray(xp, dtype=np.float64)
     out = np.empty(np.broadcast(x, xp).shape, dtype=np.float64)
@@ -63,13 +66,15 @@ def rel_vec(x, xp, dom):
 
 
 def dist2(x, xp, dom):
-    """Squared distance in the fixed summation order ((dx dx + dy dy) + dz dz)."""
+    """Squared distance in the fixed summation order ((dx dx + dy dy) + dz dz),
+    the inside test of the mapping (Sec. 2.2, reading of the cell centre)."""
     r = rel_vec(x, xp, dom)
     return (r[..., 0] * r[..., 0] + r[..., 1] * r[..., 1]) + r[..., 2] * r[..., 2]
 
 
 def cell_centres(dom):
-    """Centres of all cells, shape (nz, ny, nx, 3), centre of cell i is i + 1/2."""
+    """Centres of all cells (Sec. 2.2 maps a cell by its centre), shape
+    (nz, ny, nx, 3), centre of cell i is i + 1/2."""
     nx, ny, nz = dom.shape
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing='ij')
     return np.stack([x + 0.5, y + 0.5, z + 0.5], axis=-1).astype(np.float64)

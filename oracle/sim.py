@@ -14,7 +14,7 @@ One call of :meth:`Simulation.step` advances t -> t+1:
      contact (Eqs. (39)-(50)), external force V (rho_p - rho_f) g
      (Sec. 4.1.1), Velocity-Verlet velocity update (Eq. (38));
   5. mapping update and refill (Sec. 2.2, Eq. (18)).
-Readings where the paper is silent (listed in the design notes):
+Readings where the paper is silent:
   * first step: F^fp(t-1) := F^fp(0); the force F(t) that the first
     Velocity-Verlet position update needs is the lubrication + contact +
     external force at the initial state (no history update).
@@ -43,7 +43,8 @@ from .particles import (map_cells, cell_centres, rel_vec, lubrication_on_i, lubr
 
 
 class Domain:
-    """Box of nx x ny x nz cells; cell (i, j, k) has its centre at (i+1/2, j+1/2, k+1/2).
+    """Box of nx x ny x nz cells (Sec. 4.2); cell (i, j, k) has its centre at
+    (i+1/2, j+1/2, k+1/2).
 
     An axis is either periodic or bounded by two no-slip walls on its faces.
     wall_vel[side][axis] is the velocity of the wall at the low (side 0) or
@@ -132,6 +133,8 @@ class Simulation:
 
     # ------------------------------------------------------------------ setup
     def add_spheres(self, X, U, Om, R, rho_p):
+        """Add spheres (centre, velocity, angular velocity, radius, density
+        ratio rho_p / rho_f) and map them onto the cells (Sec. 2.2)."""
         self.X = np.vstack([self.X, np.asarray(X, dtype=np.float64).reshape(-1, 3)])
         self.U = np.vstack([self.U, np.asarray(U, dtype=np.float64).reshape(-1, 3)])
         self.Om = np.vstack([self.Om, np.asarray(Om, dtype=np.float64).reshape(-1, 3)])
@@ -140,23 +143,29 @@ class Simulation:
         self.remap()
 
     def remap(self):
+        """Solid cells, owners and the TRT+aB shell from the current positions
+        (Sec. 2.2, Sec. 2.3.2)."""
         self.owner, self.shell = map_cells(cell_centres(self.dom), self.X, self.R, self.dom,
                                            self.p.shell_width)
 
     def set_pdfs(self, ft):
-        """Replace the post-collision PDFs (19, nz, ny, nx)."""
+        """Replace the post-collision PDFs f~ of Eq. (1), shape (19, nz, ny, nx)."""
         self.ft = np.array(ft, dtype=np.float64)
 
     @property
     def volume(self):
+        """Analytic sphere volume pi D^3 / 6 (a reading: the paper gives no
+        other volume for the particle mass)."""
         return math.pi * (2.0 * self.R) ** 3 / 6.0
 
     @property
     def mass(self):
+        """m = rho_p V (Sec. 4.1)."""
         return self.rho_p * self.volume
 
     @property
     def inertia(self):
+        """Moment of inertia of a solid sphere, 2/5 m R^2 (Sec. 4.1)."""
         return 0.4 * self.mass * self.R * self.R
 
     # ---------------------------------------------------------------- DEM
@@ -165,7 +174,10 @@ class Simulation:
         return (self.volume * (self.rho_p - RHO0))[:, None] * self.p.gravity[None, :]
 
     def dem_forces(self, Fbar, Tbar, dt_p, update_history):
-        """Total force and torque on every particle at the current state."""
+        """Total force and torque on every particle at the current state
+        (Algorithm 1, inner loop): lubrication (Eqs. (25)-(34), (56)), contact
+        (Eqs. (39)-(52)), the averaged fluid force and torque (Sec. 4.2) and
+        V (rho_p - rho_f) g (Sec. 4.1.1)."""
         p, dom = self.p, self.dom
         X, U, Om, R, m = self.X, self.U, self.Om, self.R, self.mass
         N = len(R)
@@ -267,6 +279,8 @@ class Simulation:
         return list(zip(ii.tolist(), jj.tolist()))
 
     def wrap_positions(self):
+        """Positions back into [0, L) on periodic axes after an update (reading
+        of the periodic boxes of Sec. 4.2)."""
         for a in range(3):
             if self.dom.periodic[a]:
                 L = float(self.dom.shape[a])
@@ -291,6 +305,9 @@ class Simulation:
 
     # --------------------------------------------------------------- step
     def fluid_accel(self):
+        """Fluid body force of the step: the given a, minus the particles'
+        V (rho_p - rho_f) g spread over the fluid cells when the counterforce
+        reading is on (periodic sedimentation)."""
         a = self.p.body_force.copy()
         if self.p.fluid_counterforce and len(self.R):
             n_fluid = int((self.owner < 0).sum())
@@ -307,10 +324,12 @@ class Simulation:
         self.p.fixed_particles, self.p.prescribed_motion = fixed, prescribed
 
     def step(self, n=1):
+        """n time steps of Algorithm 1 (Sec. 4.2)."""
         for _ in range(n):
             self._step()
 
     def _step(self):
+        """One time step of Algorithm 1 in the order of the module doc."""
         p, dom = self.p, self.dom
         N = len(self.R)
         if self.F_prev is None and N and not p.fixed_particles and not p.prescribed_motion:
@@ -356,7 +375,7 @@ class Simulation:
 
     # ------------------------------------------------------------- output
     def fields(self):
-        """(rho, u) per cell from the stored post-collision PDFs; zero in solid cells."""
+        """(rho, u) per cell (Eq. (2)) from the stored post-collision PDFs; zero in solid cells."""
         fluid = self.owner < 0
         rho = np.where(fluid, density(self.ft), 0.0)
         u = np.where(fluid[None], velocity_from_post_collision(self.ft, self.accel), 0.0)

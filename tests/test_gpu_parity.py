@@ -484,7 +484,7 @@ def test_reduced_precision_storage_error(L, suspension_oracle, storage, bound):
     """Shifted f16 / bf16 PDF storage (float32 collision, float64 particles):
     the measured error against the float64 oracle after 6 steps stays within
     a bound set by the storage precision (2^-11 and 2^-8 relative rounding of
-    f_q - w_q); the value is printed for the design notes."""
+    f_q - w_q); the measured error is printed beside the bound."""
     ora = suspension_oracle
     ctx = build_gpu(suspension_case(storage))
     L.lbm_step(ctx, 6)
