@@ -118,6 +118,9 @@ __device__ __forceinline__ void missing_links(const BcArgs<S>& a, long long idx,
     }
 }
 
+// mode BC_ACCEL: one thread forms the fluid body force of the step; mode
+// BC_LINKS: the missing-link terms 2 w_q c_q of Sec. 2.2 and their torques, one
+// thread per listed solid cell, committed per warp
 template <typename S>
 __global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mode) {
     using T = typename Store<S>::T;

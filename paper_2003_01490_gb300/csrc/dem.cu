@@ -97,6 +97,8 @@ __device__ __forceinline__ void write_view(const Particles& P, int i) {
     P.view[i] = v;
 }
 
+// rebuild the float view of every particle (after insertion or a velocity
+// change): the link arithmetic of Eqs. (14)-(17) reads it
 __global__ void view_kernel(const Particles P) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
@@ -110,6 +112,9 @@ void launch_view_update(const Particles& P, cudaStream_t st) {
 
 // ------------------------------------------------------------ finalisation
 
+// per particle: the step's hydrodynamic force and torque (Eqs. (16)-(17)) from
+// the float64 or fixed-point link sums and the exact integer missing-link
+// sums, their two-step average (Sec. 4.2), and the accumulators cleared
 __global__ void finalize_kernel(const FinalizeParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
@@ -167,6 +172,8 @@ __device__ __forceinline__ int bin_coord(float x, float bs, int nb) {
     return b < 0 ? 0 : (b >= nb ? nb - 1 : b);
 }
 
+// particles into uniform bins no smaller than the largest interaction reach,
+// for the neighbour search of the lubrication and contact pairs (Secs. 3.1, 4.1)
 __global__ void bin_fill_kernel(const DemParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
@@ -275,6 +282,8 @@ __device__ __forceinline__ void position_update(const DemParams& p, int i) {
     }
 }
 
+// the first Velocity-Verlet position update of a step (Eq. (37)); later
+// subcycles update positions inside the subcycle kernel
 __global__ void position_kernel(const DemParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
@@ -725,6 +734,9 @@ __device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int h
     }
 }
 
+// one DEM subcycle of Algorithm 1: lubrication (Eqs. (25)-(34)) and contact
+// (Eqs. (39)-(52)) for every pair and wall, then the Velocity-Verlet velocity
+// update (Eq. (38)) and the next position update (Eq. (37))
 template <typename T>
 __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
     subcycle_body<T>(p, cur, p.hin, p.hout, init, last);
