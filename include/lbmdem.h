@@ -270,11 +270,12 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
  * 256 x 256 x 512 cells) and 65,536 spheres; larger inputs return
  * LBM_ERR_INVALID before any work. The first call on a device looks up the
  * device address of that array with the device current; make that first call
- * before any stream capture. All calls share the array and it keeps the
- * contents of the last call, so calls that overlap on the GPU (different
- * streams or devices sharing a context) race: serialise them. The call queues
- * its work on cuda_stream (a cudaStream_t, NULL = legacy default stream) and
- * synchronises that stream before returning. Errors: LBM_ERR_INVALID,
+ * before any stream capture. All calls on a device share the array; a host
+ * lock per device, held from the first queued copy to the final stream
+ * synchronise, serialises them, so calls from several host threads are safe
+ * (and never overlap on the GPU). The call queues its work on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream) and synchronises that stream
+ * before returning; it cannot be captured into a graph. Errors: LBM_ERR_INVALID,
  * LBM_ERR_CAPACITY (more than 64 spheres reach one tile), LBM_ERR_CUDA; the
  * message is returned by lbm_last_error(NULL). */
 lbm_status lbm_map_spheres_noalloc(const lbm_grid *grid, double shell_width, int n,

@@ -58,6 +58,9 @@ namespace {
 
 std::mutex g_mutex;
 NoallocScratch* g_scratch_ptr[64] = {nullptr};
+// one lock per device, held for a whole call (which ends with a stream
+// synchronise), so calls from several host threads never share the scratch
+std::mutex g_call_mutex[64];
 
 lbm_status noalloc_fail(lbm_status s, const std::string& m) {
     set_global_error(m);   // reported by lbm_last_error(NULL)
@@ -100,6 +103,7 @@ extern "C" lbm_status lbm_map_spheres_noalloc(const lbm_grid* grid, double shell
         }
         s = g_scratch_ptr[dev];
     }
+    std::lock_guard<std::mutex> call_lock(g_call_mutex[dev]);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // outputs start as a box without particles; shared counters start at zero
     if ((e = cudaMemsetAsync(d_flags, 0, (size_t)ncells, st)) != cudaSuccess ||
