@@ -62,6 +62,11 @@ def serve(jobs, budget_bytes, chunk=25, keep_state=False):
     import torch
     order = sorted(range(len(jobs)), key=lambda k: jobs[k]['arrival'])
     need = [job_bytes(j) for j in jobs]
+    too_big = [jobs[k]['name'] for k in order if need[k] > budget_bytes]
+    if too_big:
+        # such a job would wait at the head of the queue for ever
+        raise ValueError('jobs larger than the memory budget of %d bytes: %s'
+                         % (budget_bytes, ', '.join(too_big[:5])))
     arrival = [j['arrival'] for j in jobs]
     pending = list(order)
     running = []          # [job index, ctx, stream, steps left, admit time, done event]

@@ -34,3 +34,16 @@ def test_summary_latencies_and_throughput():
     lat = np.array([r['latency'] for r in recs])
     assert abs(s['p50_latency_s'] - np.percentile(lat, 50)) < 1e-4
     assert abs(s['p99_latency_s'] - np.percentile(lat, 99)) < 1e-4
+
+
+def test_a_job_larger_than_the_budget_is_rejected_before_any_work():
+    # it could never be admitted and would hold the head of the queue for ever
+    import os
+    import pytest
+    from paper_2003_01490_gb300 import build, lbmdem, workloads
+    if not os.path.exists(lbmdem.LIB_PATH):
+        build.build()
+    jobs = workloads.served(n=3)
+    need = [serve.job_bytes(j) for j in jobs]
+    with pytest.raises(ValueError, match='memory budget'):
+        serve.serve(jobs, budget_bytes=max(need) - 1)
