@@ -1,0 +1,32 @@
+"""The stored oracle trajectory (tests/golden/suspension_32x32x64_trajectory.txt,
+which the long-run GPU precision test compares against) is the output of the
+oracle as it stands: its first checkpoint is recomputed here (CPU only)."""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, 'golden'))
+
+import make_precision_trajectory as gen  # noqa: E402
+from oracle.sim import Domain, Params, Simulation  # noqa: E402
+
+
+def test_first_checkpoint_of_the_stored_trajectory_is_reproduced():
+    w = gen.case()
+    dem = w['dem']
+    p = Params(tau=w['tau'], body_force=w['body_force'], e_dry=dem['e_dry'], Tc=dem['Tc'],
+               nu_p=dem['nu_p'], mu_p=dem['mu_p'], n_sub=dem['n_sub'], gravity=dem['gravity'],
+               fluid_counterforce=bool(dem.get('fluid_counterforce', 0)))
+    sim = Simulation(Domain(*w['shape'], periodic=tuple(bool(v) for v in w['periodic'])), p)
+    sim.add_spheres(w['pos'], w['vel'], w['omega'], w['radius'], w['density'])
+    sim.step(gen.CHECKPOINTS[0])
+    lines = open(gen.OUT).read().splitlines()
+    i = lines.index('step %d' % gen.CHECKPOINTS[0])
+    n = len(w['radius'])
+    ref = np.array([[float(v) for v in lines[i + 1 + k].split()] for k in range(n)])
+    stats = np.array([float(v) for v in lines[i + 1 + n].split()[1:]])
+    assert np.abs(sim.X - ref[:, :3]).max() <= 1e-12 * np.abs(ref[:, :3]).max()
+    assert np.abs(sim.U - ref[:, 3:]).max() <= 1e-12 * np.abs(ref[:, 3:]).max()
+    assert np.allclose(gen.field_stats(sim), stats, rtol=1e-10, atol=0)
