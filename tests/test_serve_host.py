@@ -47,3 +47,24 @@ def test_a_job_larger_than_the_budget_is_rejected_before_any_work():
     need = [serve.job_bytes(j) for j in jobs]
     with pytest.raises(ValueError, match='memory budget'):
         serve.serve(jobs, budget_bytes=max(need) - 1)
+
+
+def test_cancellation_picks_due_jobs_that_wait_or_run():
+    cancel_at = {0: 0.5, 2: 0.1, 5: 0.2, 7: 9.0}
+    # job 2 waits and is due; job 5 runs and is due; job 7 is not due yet;
+    # job 0 is due but already finished (neither waiting nor running)
+    drop_wait, drop_run = serve.cancellations([2, 3, 7], [4, 5], cancel_at, now=0.6)
+    assert drop_wait == [2] and drop_run == [5]
+    assert serve.cancellations([2, 3], [5], cancel_at, now=0.05) == ([], [])
+    assert serve.cancellations([], [], {}, now=1.0) == ([], [])
+
+
+def test_summary_counts_cancelled_work_but_not_their_latency():
+    recs = [dict(arrival=0.0, done=1.0, latency=1.0, cell_updates=2_000_000),
+            dict(arrival=0.0, done=2.0, latency=2.0, cell_updates=2_000_000, cancelled=False),
+            dict(arrival=0.5, done=0.7, latency=0.2, cell_updates=500_000, cancelled=True)]
+    s = serve.summary(recs)
+    assert s['jobs'] == 2 and s['cancelled'] == 1
+    assert s['makespan_s'] == 2.0 and s['jobs_per_s'] == 1.0
+    assert abs(s['mlups'] - 4.5e6 / 2.0 / 1e6) <= 0.05 + 1e-12      # rounded to 0.1
+    assert abs(s['p50_latency_s'] - 1.5) < 1e-9
