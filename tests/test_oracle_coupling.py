@@ -129,6 +129,22 @@ def test_missing_links_close_pair_and_wall():
     assert np.abs(F + Fm).max() < 1e-13
 
 
+def test_missing_links_cancel_the_torque_of_an_oblique_pair():
+    # off-axis neighbours: the fluid at rest exerts a torque on each body of a
+    # close pair (and on a sphere near a wall) through the links it lacks; the
+    # missing-link terms (Sec. 2.2), applied at points of the same lattice
+    # lines, cancel force and torque exactly
+    dom = Domain(24, 14, 16, periodic=(True, True, False))
+    R = np.array([3.5, 3.6, 3.0])
+    X = np.array([[4.9, 7.2, 11.3], [4.9 + 7.1 + 0.15, 8.1, 12.0], [18.6, 6.8, 3.08]])
+    owner, _ = map_cells(cell_centres(dom), X, R, dom, 2.0)
+    _, F, T = stream_and_couple(rest_state(dom), dom, owner, X, np.zeros((3, 3)),
+                                np.zeros((3, 3)), R)
+    Fm, Tm = missing_links(dom, owner, X, R)
+    assert np.abs(T).max() > 0.1
+    assert np.abs(F + Fm).max() < 1e-13 and np.abs(T + Tm).max() < 1e-13
+
+
 def test_momentum_balance_with_resting_particles():
     dom = Domain(18, 16, 17)
     X = np.array([[5.2, 8.1, 8.4], [12.9, 7.7, 9.0]])
