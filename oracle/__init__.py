@@ -20,8 +20,9 @@ complete coupled step is pinned as a whole by exact solutions it must keep
 (a sphere carried by a uniform flow, prescribed or free, stays in it with
 zero force) and by the Stokes drag of a periodic sphere array. A general
 trajectory of interacting particles is pinned only by its parts and by its
-invariance under a rotation of the lattice that permutes the axes, not by
-values (parity unpinned for the complete step at the large configurations).
+invariance under a rotation of the lattice that permutes the axes and under
+a mirror of one axis, not by values (parity unpinned for the complete step
+at the large configurations).
 """
 from .d3q19 import C, W, OPP, M, M_INV, Q, CS2, RHO0  # noqa: F401
 from .sim import Domain, Params, Simulation  # noqa: F401

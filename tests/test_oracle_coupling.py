@@ -20,7 +20,7 @@
   velocity without spinning;
 * interacting particles (contact, lubrication, walls, periodic sides,
   refill): the complete trajectory is invariant under a cyclic permutation
-  of the axes, a rotation of the lattice.
+  of the axes (a rotation of the lattice) and under a mirror of one axis.
 """
 import itertools
 
@@ -439,5 +439,52 @@ def test_interacting_particles_are_invariant_under_axis_rotation(perm):
     assert a[-1].shape == (3, 18, 14, 16) and b[-1].shape == a[-1].shape
     assert pair_gap < 0 and wall_gap < 0.05          # contact, and wall lubrication
     assert np.allclose(gaps_b, (pair_gap, wall_gap), rtol=0, atol=1e-12)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def mirrored_run(axis, steps=30):
+    """interacting_run's spheres, gravity and walls mirrored on the plane
+    x_axis = L_axis / 2 (None: not mirrored); the final state is mirrored
+    back. Vectors flip their axis component, pseudovectors (angular velocity,
+    torque) the two others."""
+    shape = np.array([16, 14, 18])
+    periodic = np.array([1, 1, 0])
+    g = np.array([0.0, 0.0, -2e-4])
+    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
+    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
+    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
+    R = np.array([2.6, 2.4, 2.2])
+    sv = np.ones(3)                  # sign of a vector's components
+    if axis is not None:
+        sv[axis] = -1.0
+        X = X.copy()
+        X[:, axis] = shape[axis] - X[:, axis]
+    sp = sv * np.prod(sv)            # sign of a pseudovector's components
+    dom = Domain(*shape, periodic=tuple(bool(v) for v in periodic))
+    sim = Simulation(dom, Params(tau=0.8, gravity=tuple(g * sv), Tc=10.0))
+    sim.add_spheres(X, U * sv, Om * sp, R, [8.0, 6.0, 9.0])
+    for _ in range(steps):
+        sim.step(1)
+    _, u = sim.fields()
+    Xb = sim.X.copy()
+    if axis is None:
+        return [Xb, sim.U, sim.Om, sim.Ffp, sim.Tfp, u]
+    Xb[:, axis] = shape[axis] - Xb[:, axis]
+    if periodic[axis]:
+        Xb[:, axis] %= shape[axis]
+    u = np.flip(u * sv[:, None, None, None], axis=1 + 2 - axis)
+    return [Xb, sim.U * sv, sim.Om * sp, sim.Ffp * sv, sim.Tfp * sp, u]
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_interacting_particles_are_invariant_under_a_mirror(axis):
+    # D3Q19 and every law of the step are symmetric under a reflection of one
+    # axis (Secs. 2-4): the run of interacting_run mirrored on a periodic (x)
+    # or walled (z) axis equals the original to rounding. This catches code
+    # that treats +c and -c differently (one branch of a one-sided
+    # difference, one of the two walls)
+    a = mirrored_run(None)
+    b = mirrored_run(axis)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
