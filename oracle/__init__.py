@@ -20,8 +20,8 @@ complete coupled step is pinned as a whole by exact solutions it must keep
 (a sphere carried by a uniform flow, prescribed or free, stays in it with
 zero force) and by the Stokes drag of a periodic sphere array. A general
 trajectory of interacting particles is pinned only by its parts and by its
-invariance under a rotation of the lattice that permutes the axes and under
-a mirror of one axis, not by values (parity unpinned for the complete step
+invariance under a rotation of the lattice that permutes the axes, a mirror
+of one axis and a whole-cell translation along periodic axes, not by values (parity unpinned for the complete step
 at the large configurations).
 """
 from .d3q19 import C, W, OPP, M, M_INV, Q, CS2, RHO0  # noqa: F401

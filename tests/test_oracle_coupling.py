@@ -20,7 +20,8 @@
   velocity without spinning;
 * interacting particles (contact, lubrication, walls, periodic sides,
   refill): the complete trajectory is invariant under a cyclic permutation
-  of the axes (a rotation of the lattice) and under a mirror of one axis.
+  of the axes (a rotation of the lattice), under a mirror of one axis and
+  under a translation by whole cells along the periodic axes.
 """
 import itertools
 
@@ -439,6 +440,36 @@ def test_interacting_particles_are_invariant_under_axis_rotation(perm):
     assert a[-1].shape == (3, 18, 14, 16) and b[-1].shape == a[-1].shape
     assert pair_gap < 0 and wall_gap < 0.05          # contact, and wall lubrication
     assert np.allclose(gaps_b, (pair_gap, wall_gap), rtol=0, atol=1e-12)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def shifted_run(shift, steps=30):
+    """interacting_run's spheres translated by whole cells along the periodic
+    axes x and y; the final state and field are translated back."""
+    shape = np.array([16, 14, 18])
+    shift = np.array([shift[0], shift[1], 0])
+    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
+    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
+    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
+    dom = Domain(*shape, periodic=(True, True, False))
+    sim = Simulation(dom, Params(tau=0.8, gravity=(0.0, 0.0, -2e-4), Tc=10.0))
+    sim.add_spheres((X + shift) % shape, U, Om, [2.6, 2.4, 2.2], [8.0, 6.0, 9.0])
+    for _ in range(steps):
+        sim.step(1)
+    _, u = sim.fields()
+    u = np.roll(u, shift=(-shift[1], -shift[0]), axis=(2, 3))
+    return [(sim.X - shift) % shape, sim.U, sim.Om, sim.Ffp, sim.Tfp, u]
+
+
+@pytest.mark.parametrize("shift", [(5, -3), (-13, 7)])
+def test_interacting_particles_are_invariant_under_a_periodic_shift(shift):
+    # a translation by whole cells along periodic axes is a symmetry of the
+    # periodic box: the collisions that happen across the periodic sides in
+    # interacting_run happen inside the box after the shift (and the
+    # reverse), with the same result to rounding
+    a = shifted_run((0, 0))
+    b = shifted_run(shift)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
 
