@@ -20,8 +20,9 @@
   velocity without spinning;
 * interacting particles (contact, lubrication, walls, periodic sides,
   refill): the complete trajectory is invariant under a cyclic permutation
-  of the axes (a rotation of the lattice), under a mirror of one axis and
-  under a translation by whole cells along the periodic axes.
+  of the axes (a rotation of the lattice), under a mirror of one axis, under
+  a translation by whole cells along the periodic axes and under a new
+  order of the particles.
 """
 import itertools
 
@@ -470,6 +471,37 @@ def test_interacting_particles_are_invariant_under_a_periodic_shift(shift):
     # reverse), with the same result to rounding
     a = shifted_run((0, 0))
     b = shifted_run(shift)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def relabelled_run(order, steps=30):
+    """interacting_run's spheres inserted in another order; the final state
+    is put back into the original order."""
+    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
+    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
+    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
+    R = np.array([2.6, 2.4, 2.2])
+    rho = np.array([8.0, 6.0, 9.0])
+    p = list(order)
+    sim = Simulation(Domain(16, 14, 18, periodic=(True, True, False)),
+                     Params(tau=0.8, gravity=(0.0, 0.0, -2e-4), Tc=10.0))
+    sim.add_spheres(X[p], U[p], Om[p], R[p], rho[p])
+    for _ in range(steps):
+        sim.step(1)
+    back = np.argsort(p)
+    _, u = sim.fields()
+    return [sim.X[back], sim.U[back], sim.Om[back], sim.Ffp[back], sim.Tfp[back], u]
+
+
+@pytest.mark.parametrize("order", [(1, 0, 2), (2, 1, 0)])
+def test_interacting_particles_do_not_depend_on_their_labels(order):
+    # no cell lies inside two spheres here, so the particle index enters
+    # nothing but bookkeeping: the two members of a colliding or lubricated
+    # pair must get the same forces and torques whichever of them comes first
+    # (Eqs. (25)-(33), (39)-(50) act on i and on j alike)
+    a = relabelled_run((0, 1, 2))
+    b = relabelled_run(order)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
 
