@@ -396,36 +396,57 @@ def test_free_sphere_carried_by_uniform_flow_moves_with_it(X0):
     assert np.abs(sim.U - U).max() < 1e-14 and np.abs(sim.Om).max() < 1e-15
 
 
-def interacting_run(perm, steps=30):
-    """Three spheres with spin in a box periodic in x, y and bounded by walls in
-    z, under gravity: a pair that comes into contact (through lubrication)
-    across the periodic side x = 0, and a sphere across the periodic side y = 0
-    rising against gravity towards the top wall. The axes are renamed by perm (a
-    cyclic permutation is a rotation of the lattice); returns the final
-    particle state with the axes named back, and the smallest gaps seen."""
-    shape = np.array([16, 14, 18])
-    periodic = np.array([1, 1, 0])
-    g = np.array([0.0, 0.0, -2e-4])
-    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
-    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
-    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
-    R = np.array([2.6, 2.4, 2.2])
-    p = list(perm)
-    dom = Domain(*shape[p], periodic=tuple(bool(v) for v in periodic[p]))
-    sim = Simulation(dom, Params(tau=0.8, gravity=tuple(g[p]), Tc=10.0))
-    sim.add_spheres(X[:, p], U[:, p], Om[:, p], R, [8.0, 6.0, 9.0])
-    pair_gap, wall_gap = np.inf, np.inf
+# Three spheres with spin in a box periodic in x, y and bounded by walls in z,
+# under gravity: a pair that comes into contact (through lubrication) across
+# the periodic side x = 0, and a sphere across the periodic side y = 0 rising
+# against gravity into the top wall's lubrication range.
+PAIR_WALL = dict(shape=np.array([16, 14, 18]), periodic=np.array([1, 1, 0]),
+                 g=np.array([0.0, 0.0, -2e-4]),
+                 X=np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]]),
+                 U=np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]]),
+                 Om=np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]]),
+                 R=np.array([2.6, 2.4, 2.2]), rho=np.array([8.0, 6.0, 9.0]))
+
+
+def run_pair_wall(shape, periodic, g, X, U, Om, R, rho, steps=30, watch=None):
+    """The complete coupled step, `steps` times, for PAIR_WALL (or a
+    transformed copy of it); watch(sim) is called after every step."""
+    dom = Domain(*shape, periodic=tuple(bool(v) for v in periodic))
+    sim = Simulation(dom, Params(tau=0.8, gravity=tuple(g), Tc=10.0))
+    sim.add_spheres(X, U, Om, R, rho)
     for _ in range(steps):
         sim.step(1)
-        wall_gap = min(wall_gap, shape[2] - sim.X[2, p.index(2)] - R[2])
-        pair_gap = min(pair_gap, np.sqrt(dist2(sim.X[0], sim.X[1], sim.dom)) - R[0] - R[1])
+        if watch:
+            watch(sim)
+    return sim
+
+
+def close(a, b):
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def rotated_run(perm):
+    """PAIR_WALL with its axes renamed by perm (a cyclic permutation is a
+    rotation of the lattice); returns the final particle state and velocity
+    field with the axes named back, and the smallest pair and wall gaps."""
+    c = PAIR_WALL
+    p = list(perm)
+    gaps = [np.inf, np.inf]
+
+    def watch(sim):
+        gaps[0] = min(gaps[0], np.sqrt(dist2(sim.X[0], sim.X[1], sim.dom)) - c['R'][0] - c['R'][1])
+        gaps[1] = min(gaps[1], c['shape'][2] - sim.X[2, p.index(2)] - c['R'][2])
+
+    sim = run_pair_wall(c['shape'][p], c['periodic'][p], c['g'][p], c['X'][:, p], c['U'][:, p],
+                        c['Om'][:, p], c['R'], c['rho'], watch=watch)
     back = np.argsort(p)
     state = [a[:, back] for a in (sim.X, sim.U, sim.Om, sim.Ffp, sim.Tfp)]
     # the velocity field with its components and array axes named back (array
     # axis j holds coordinate 2 - j)
     _, u = sim.fields()
     u = np.transpose(u[back], [0] + [1 + 2 - back[2 - j] for j in range(3)])
-    return state + [u], (pair_gap, wall_gap)
+    return state + [u], gaps
 
 
 @pytest.mark.parametrize("perm", [(2, 0, 1), (1, 2, 0)])
@@ -436,59 +457,42 @@ def test_interacting_particles_are_invariant_under_axis_rotation(perm):
     # trajectory of interacting particles has no closed form, but it must be
     # the same, to rounding, in the rotated frame: this catches any axis that
     # is treated differently from the others
-    a, (pair_gap, wall_gap) = interacting_run((0, 1, 2))
-    b, gaps_b = interacting_run(perm)
+    a, (pair_gap, wall_gap) = rotated_run((0, 1, 2))
+    b, gaps_b = rotated_run(perm)
     assert a[-1].shape == (3, 18, 14, 16) and b[-1].shape == a[-1].shape
     assert pair_gap < 0 and wall_gap < 0.05          # contact, and wall lubrication
     assert np.allclose(gaps_b, (pair_gap, wall_gap), rtol=0, atol=1e-12)
-    for x, y in zip(a, b):
-        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    close(a, b)
 
 
-def shifted_run(shift, steps=30):
-    """interacting_run's spheres translated by whole cells along the periodic
-    axes x and y; the final state and field are translated back."""
-    shape = np.array([16, 14, 18])
+def shifted_run(shift):
+    """PAIR_WALL translated by whole cells along the periodic axes x and y;
+    the final state and field are translated back."""
+    c = PAIR_WALL
     shift = np.array([shift[0], shift[1], 0])
-    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
-    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
-    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
-    dom = Domain(*shape, periodic=(True, True, False))
-    sim = Simulation(dom, Params(tau=0.8, gravity=(0.0, 0.0, -2e-4), Tc=10.0))
-    sim.add_spheres((X + shift) % shape, U, Om, [2.6, 2.4, 2.2], [8.0, 6.0, 9.0])
-    for _ in range(steps):
-        sim.step(1)
+    sim = run_pair_wall(c['shape'], c['periodic'], c['g'], (c['X'] + shift) % c['shape'], c['U'], c['Om'],
+                        c['R'], c['rho'])
     _, u = sim.fields()
     u = np.roll(u, shift=(-shift[1], -shift[0]), axis=(2, 3))
-    return [(sim.X - shift) % shape, sim.U, sim.Om, sim.Ffp, sim.Tfp, u]
+    return [(sim.X - shift) % c['shape'], sim.U, sim.Om, sim.Ffp, sim.Tfp, u]
 
 
 @pytest.mark.parametrize("shift", [(5, -3), (-13, 7)])
 def test_interacting_particles_are_invariant_under_a_periodic_shift(shift):
     # a translation by whole cells along periodic axes is a symmetry of the
     # periodic box: the collisions that happen across the periodic sides in
-    # interacting_run happen inside the box after the shift (and the
-    # reverse), with the same result to rounding
-    a = shifted_run((0, 0))
-    b = shifted_run(shift)
-    for x, y in zip(a, b):
-        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    # PAIR_WALL happen inside the box after the shift (and the reverse), with
+    # the same result to rounding
+    close(shifted_run((0, 0)), shifted_run(shift))
 
 
-def relabelled_run(order, steps=30):
-    """interacting_run's spheres inserted in another order; the final state
-    is put back into the original order."""
-    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
-    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
-    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
-    R = np.array([2.6, 2.4, 2.2])
-    rho = np.array([8.0, 6.0, 9.0])
+def relabelled_run(order):
+    """PAIR_WALL's spheres inserted in another order; the final state is put
+    back into the original order."""
+    c = PAIR_WALL
     p = list(order)
-    sim = Simulation(Domain(16, 14, 18, periodic=(True, True, False)),
-                     Params(tau=0.8, gravity=(0.0, 0.0, -2e-4), Tc=10.0))
-    sim.add_spheres(X[p], U[p], Om[p], R[p], rho[p])
-    for _ in range(steps):
-        sim.step(1)
+    sim = run_pair_wall(c['shape'], c['periodic'], c['g'], c['X'][p], c['U'][p], c['Om'][p], c['R'][p],
+                        c['rho'][p])
     back = np.argsort(p)
     _, u = sim.fields()
     return [sim.X[back], sim.U[back], sim.Om[back], sim.Ffp[back], sim.Tfp[back], u]
@@ -500,41 +504,29 @@ def test_interacting_particles_do_not_depend_on_their_labels(order):
     # nothing but bookkeeping: the two members of a colliding or lubricated
     # pair must get the same forces and torques whichever of them comes first
     # (Eqs. (25)-(33), (39)-(50) act on i and on j alike)
-    a = relabelled_run((0, 1, 2))
-    b = relabelled_run(order)
-    for x, y in zip(a, b):
-        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    close(relabelled_run((0, 1, 2)), relabelled_run(order))
 
 
-def mirrored_run(axis, steps=30):
-    """interacting_run's spheres, gravity and walls mirrored on the plane
+def mirrored_run(axis):
+    """PAIR_WALL's spheres, gravity and walls mirrored on the plane
     x_axis = L_axis / 2 (None: not mirrored); the final state is mirrored
     back. Vectors flip their axis component, pseudovectors (angular velocity,
     torque) the two others."""
-    shape = np.array([16, 14, 18])
-    periodic = np.array([1, 1, 0])
-    g = np.array([0.0, 0.0, -2e-4])
-    X = np.array([[13.6, 7.2, 8.0], [2.75, 6.9, 8.3], [8.0, 1.0, 15.72]])
-    U = np.array([[0.05, 0.002, 0.0], [-0.05, 0.0, -0.004], [0.0, -0.01, 0.08]])
-    Om = np.array([[0.0, 0.01, 0.002], [0.003, 0.0, -0.01], [0.0, 0.0, 0.0]])
-    R = np.array([2.6, 2.4, 2.2])
+    c = PAIR_WALL
+    shape = c['shape']
     sv = np.ones(3)                  # sign of a vector's components
+    X = c['X'].copy()
     if axis is not None:
         sv[axis] = -1.0
-        X = X.copy()
         X[:, axis] = shape[axis] - X[:, axis]
     sp = sv * np.prod(sv)            # sign of a pseudovector's components
-    dom = Domain(*shape, periodic=tuple(bool(v) for v in periodic))
-    sim = Simulation(dom, Params(tau=0.8, gravity=tuple(g * sv), Tc=10.0))
-    sim.add_spheres(X, U * sv, Om * sp, R, [8.0, 6.0, 9.0])
-    for _ in range(steps):
-        sim.step(1)
+    sim = run_pair_wall(shape, c['periodic'], c['g'] * sv, X, c['U'] * sv, c['Om'] * sp, c['R'], c['rho'])
     _, u = sim.fields()
     Xb = sim.X.copy()
     if axis is None:
         return [Xb, sim.U, sim.Om, sim.Ffp, sim.Tfp, u]
     Xb[:, axis] = shape[axis] - Xb[:, axis]
-    if periodic[axis]:
+    if c['periodic'][axis]:
         Xb[:, axis] %= shape[axis]
     u = np.flip(u * sv[:, None, None, None], axis=1 + 2 - axis)
     return [Xb, sim.U * sv, sim.Om * sp, sim.Ffp * sv, sim.Tfp * sp, u]
@@ -543,11 +535,8 @@ def mirrored_run(axis, steps=30):
 @pytest.mark.parametrize("axis", [0, 2])
 def test_interacting_particles_are_invariant_under_a_mirror(axis):
     # D3Q19 and every law of the step are symmetric under a reflection of one
-    # axis (Secs. 2-4): the run of interacting_run mirrored on a periodic (x)
-    # or walled (z) axis equals the original to rounding. This catches code
-    # that treats +c and -c differently (one branch of a one-sided
-    # difference, one of the two walls)
-    a = mirrored_run(None)
-    b = mirrored_run(axis)
-    for x, y in zip(a, b):
-        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    # axis (Secs. 2-4): PAIR_WALL mirrored on a periodic (x) or walled (z)
+    # axis equals the original to rounding. This catches code that treats +c
+    # and -c differently (one branch of a one-sided difference, one of the two
+    # walls)
+    close(mirrored_run(None), mirrored_run(axis))
