@@ -8,6 +8,12 @@
   linear oscillator; dry normal impacts on a wall and between two spheres
   give e_dry; a dry oblique impact in gross sliding follows rigid-body
   impulse theory, Psi_out = Psi_in - (1 + e) mu (1 + 1/K), K = 2/5;
+* sticking contact (Eqs. (45), (49), (50)): an undamped sticking contact
+  oscillates at sqrt(k_t (1/m + r_c^2/I)) with first-order amplitude growth in
+  dt_p; a rigidly rotating pair keeps its spring length and force (the Eq. (49)
+  rescale); a sphere on an incline rolls at 5/7 g sin(theta) below
+  tan(theta) = 7/2 mu_p and slides (Coulomb, slip rate g (sin - 7/2 mu cos))
+  above it;
 * Velocity Verlet (Eqs. (37)-(38)) is exact for a constant force.
 """
 import math
@@ -191,3 +197,153 @@ def test_velocity_verlet_is_exact_for_constant_force():
     x = np.mod(x, 64.0)
     assert np.allclose(sim.X[0], x, atol=1e-12)
     assert np.allclose(sim.U[0], np.array([0.01, 0, 0.02]) + acc * t, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# sticking branch of the tangential contact (Sec. 4.1.2, Eqs. (45), (49), (50))
+# ---------------------------------------------------------------------------
+
+def resting_on_wall(R, rho, g_vec, Tc, e, mu, nu, n_sub, u0=(0.0, 0.0, 0.0)):
+    """A dry sphere resting on the wall z = 0 at the equilibrium overlap of its
+    weight's normal part (no lubrication, no fluid)."""
+    dom = Domain(64, 64, 64, periodic=(True, True, False))
+    m = rho * math.pi * (2 * R) ** 3 / 6
+    kn, _, _, _ = contact_coefficients(m, e, Tc, nu)
+    f_ext = math.pi * (2 * R) ** 3 / 6 * (rho - 1.0) * np.asarray(g_vec, float)
+    delta0 = f_ext[2] / kn                        # < 0: weight pressing into the wall
+    sim = dry_sim(dom, [[32.0, 32.0, R + delta0]], [u0], [[0, 0, 0]], [R], [rho], n_sub,
+                  Tc=Tc, e_dry=e, mu_p=mu, nu_p=nu, gravity=tuple(g_vec))
+    return sim, m, delta0
+
+
+def contact_slip(sim, delta):
+    """Tangential velocity of the contact point of a sphere on the wall z = 0
+    (Eq. (B.7) with the lever arm R + delta/2 of the wall contact point)."""
+    rc = sim.R[0] + 0.5 * delta
+    return sim.U[0, 0] - rc * sim.Om[0, 1], rc
+
+
+def sticking_oscillation(n_sub, steps=120):
+    """Slip velocity of the contact point, one sample per time step, of an
+    undamped sphere set sliding at 5e-4 along a wall it rests on."""
+    R, rho, Tc, mu, nu = 4.0, 8.0, 20.0, 0.15, 0.23
+    sim, m, delta0 = resting_on_wall(R, rho, (0.0, 0.0, -1e-3), Tc, 1.0, mu, nu, n_sub,
+                                     u0=(5e-4, 0.0, 0.0))
+    _, _, kt, dt_ = contact_coefficients(m, 1.0, Tc, nu)
+    assert dt_ == 0.0
+    rc = R + 0.5 * delta0
+    I = 0.4 * m * R * R
+    omega_t = math.sqrt(kt * (1.0 / m + rc * rc / I))
+    slip = []
+    for k in range(steps):
+        s, _ = contact_slip(sim, delta0)
+        slip.append(s)
+        sim.dem_subcycles(np.zeros((1, 3)), np.zeros((1, 3)))
+        # still sticking: the spring force stays inside the Coulomb cone
+        d = sim.hist[(0, 'wall', 2, 0)]
+        assert kt * math.sqrt(d @ d) < mu * m * (rho - 1) / rho * 1e-3
+    return np.array(slip), omega_t
+
+
+def test_sticking_contact_oscillates_at_the_tangential_spring_frequency():
+    # Undamped (e_dry = 1) sticking contact: the spring delta_t integrates the
+    # contact-point velocity (Eq. (50)) and pulls back with -k_t delta_t
+    # (Eq. (45)). With F_x = -k_t delta_t acting at the contact point, the slip
+    # velocity obeys d^2 delta_t / dt^2 = -k_t (1/m + r_c^2 / I) delta_t, a
+    # harmonic oscillator of angular frequency sqrt(k_t (1/m + r_c^2 / I)).
+    slip, omega_t = sticking_oscillation(40)
+    t = np.arange(len(slip), dtype=float)
+    # zero crossings of u0 cos(omega_t t) lie at (j + 1/2) pi / omega_t
+    z = [t[k] + slip[k] / (slip[k] - slip[k + 1]) for k in range(len(t) - 1)
+         if slip[k] > 0 >= slip[k + 1] or slip[k] < 0 <= slip[k + 1]]
+    assert len(z) >= 8
+    half_period = (z[-1] - z[0]) / (len(z) - 1)
+    assert abs(half_period / (math.pi / omega_t) - 1.0) < 0.01
+    assert abs(z[0] / (0.5 * math.pi / omega_t) - 1.0) < 0.02
+    # The spring is integrated explicitly with the velocity of the start of
+    # each subcycle and pulls with the value it had there, so the undamped
+    # oscillation gains energy at a rate proportional to dt_p: halving dt_p
+    # halves the amplitude's growth over the same time (first order).
+    g40 = np.abs(slip[-25:]).max() / 5e-4 - 1.0
+    slip80, _ = sticking_oscillation(80)
+    g80 = np.abs(slip80[-25:]).max() / 5e-4 - 1.0
+    assert 0.0 < g80 < g40 < 0.3
+    assert abs(g40 / g80 - 2.0) < 0.25
+
+
+@pytest.mark.parametrize('t0', [(0.0, 2e-3, 0.0), (0.0, 2e-3, 1e-3)])
+def test_rigidly_rotating_contact_keeps_its_spring_length(t0):
+    # Two spheres in sticking contact rotate together as one rigid body about
+    # the z axis through their midpoint: the contact point has no relative
+    # velocity, so the stored spring must only turn with the contact frame
+    # (Eq. (49): projection on the new tangent plane, rescaled to the old
+    # length), never shrink or grow, and its force -k_t delta_t keeps its size.
+    # A spring in the plane of rotation turns exactly with the pair.
+    R, eps, Om = 3.0, 0.02, 0.01
+    dom = Domain(40, 40, 40)
+    c = np.array([20.0, 20.0, 20.0])
+    half = R - 0.5 * eps
+    p = Params(tau=0.8, n_sub=10, lubrication=False, e_dry=0.97, Tc=15.0, mu_p=0.5, nu_p=0.23)
+    sim = Simulation(dom, p)
+    sim.R = np.array([R, R])
+    sim.rho_p = np.array([2.5, 2.5])
+    t0 = np.array(t0)
+    sim.hist[(0, 1)] = t0.copy()
+    dth = 0.1
+    m = sim.mass[0]
+    kn, _, kt, _ = contact_coefficients(0.5 * m, p.e_dry, 15.0, p.nu_p)
+    assert kt * np.linalg.norm(t0) < p.mu_p * kn * eps
+    for k in range(1, 16):
+        th = k * dth
+        n = np.array([math.cos(th), math.sin(th), 0.0])
+        sim.X = np.array([c + half * n, c - half * n])
+        w = np.array([0.0, 0.0, Om])
+        sim.U = np.array([np.cross(w, sim.X[0] - c), np.cross(w, sim.X[1] - c)])
+        sim.Om = np.array([w, w])
+        F, T = sim.dem_forces(np.zeros((2, 3)), np.zeros((2, 3)), 0.1, update_history=True)
+        d = sim.hist[(0, 1)]
+        assert abs(np.linalg.norm(d) / np.linalg.norm(t0) - 1.0) < 1e-12
+        assert abs(d @ n) < 1e-15
+        if t0[2] == 0.0:
+            tang = np.array([-math.sin(th), math.cos(th), 0.0])
+            assert np.allclose(d, t0[1] * tang, rtol=0, atol=1e-12 * np.linalg.norm(t0))
+        # contact force on sphere 0: the normal spring plus -k_t times the
+        # turned tangential spring (no damping: no relative velocity)
+        Fn = -kn * (-eps) * n
+        assert np.allclose(F[0], Fn - kt * d, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize('ratio,sticks', [(0.9, True), (1.1, False)])
+def test_sphere_on_an_incline_rolls_below_and_slides_above_the_friction_limit(ratio, sticks):
+    # A sphere on a plane inclined at theta (gravity tilted against the wall
+    # z = 0) rolls without slipping while the friction it needs,
+    # (2/7) m g sin(theta), stays below mu_p m g cos(theta), i.e. for
+    # tan(theta) < 7/2 mu_p: the contact sticks (Eq. (50)) and the centre
+    # accelerates at 5/7 g sin(theta). Above that limit it slides with the
+    # Coulomb force mu_p |F_n| (Eq. (47)): the centre accelerates at
+    # g (sin - mu_p cos) and the contact point slips at the rate
+    # g (sin - 7/2 mu_p cos).
+    R, rho, Tc, mu, nu, g = 4.0, 8.0, 20.0, 0.15, 0.23, 2e-4
+    th = math.atan(ratio * 3.5 * mu)
+    g_vec = (g * math.sin(th), 0.0, -g * math.cos(th))
+    sim, m, delta0 = resting_on_wall(R, rho, g_vec, Tc, 0.3, mu, nu, 20)
+    geff = g * (rho - 1.0) / rho
+    U0, S0 = None, None
+    t1, t2 = 150, 350
+    for k in range(t2 + 1):
+        if k == t1:
+            U0 = sim.U[0, 0]
+            S0, _ = contact_slip(sim, delta0)
+        if k >= t1:
+            s, _ = contact_slip(sim, delta0)
+            if sticks:
+                assert abs(s) < 1e-3 * geff * k
+        sim.dem_subcycles(np.zeros((1, 3)), np.zeros((1, 3)))
+    a = (sim.U[0, 0] - U0) / (t2 - t1 + 1)
+    S1, _ = contact_slip(sim, delta0)
+    if sticks:
+        assert abs(a / (5.0 / 7.0 * geff * math.sin(th)) - 1.0) < 0.01
+    else:
+        assert abs(a / (geff * (math.sin(th) - mu * math.cos(th))) - 1.0) < 0.01
+        rate = (S1 - S0) / (t2 - t1 + 1)
+        assert abs(rate / (geff * (math.sin(th) - 3.5 * mu * math.cos(th))) - 1.0) < 0.02
