@@ -260,9 +260,10 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
  * caller: d_pos (n x 3 doubles) and d_radius (n doubles) are read; d_flags
  * (nx*ny*nz bytes, LBM_FLAG_SOLID/SHELL/NEAR/MISS bits) and d_owner (nx*ny*nz
  * int32, the lowest sphere index whose sphere holds the cell centre, -1 for
- * fluid) are cleared and written, x fastest, as lbm_add_spheres() maps the same
- * spheres into a new context (Sec. 2.2 solid test, Sec. 2.3.2 shell of width
- * shell_width). grid->wall_vel_* are ignored.
+ * fluid) are cleared and written, x fastest, exactly as lbm_add_spheres() maps
+ * the same spheres into a new context (solid cells, and the shell of width
+ * shell_width around each sphere). grid->wall_vel_* are ignored. All four
+ * buffers must be memory of the current device (LBM_ERR_INVALID otherwise).
  *
  * The temporary tile lists live in one file-scope device array of about 29 MB
  * that every GPU which loads the library holds until the process exits.
@@ -275,7 +276,7 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
  * synchronise, serialises them, so calls from several host threads are safe
  * (and never overlap on the GPU). The call queues its work on cuda_stream (a
  * cudaStream_t, NULL = legacy default stream) and synchronises that stream
- * before returning; it cannot be captured into a graph. Errors: LBM_ERR_INVALID,
+ * before returning, on errors too once work is queued. Errors: LBM_ERR_INVALID,
  * LBM_ERR_CAPACITY (more than 64 spheres reach one tile), LBM_ERR_CUDA; the
  * message is returned by lbm_last_error(NULL). */
 lbm_status lbm_map_spheres_noalloc(const lbm_grid *grid, double shell_width, int n,

@@ -103,8 +103,35 @@ extern "C" lbm_status lbm_map_spheres_noalloc(const lbm_grid* grid, double shell
         }
         s = g_scratch_ptr[dev];
     }
+    // every buffer must live on the current device, the one whose scratch
+    // this call uses
+    {
+        const void* bufs[4] = {d_flags, d_owner, d_pos, d_radius};
+        const char* names[4] = {"d_flags", "d_owner", "d_pos", "d_radius"};
+        for (int b = 0; b < (n > 0 ? 4 : 2); ++b) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, bufs[b]) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+                at.device != dev) {
+                cudaGetLastError();
+                return noalloc_fail(LBM_ERR_INVALID,
+                                    std::string(names[b]) + " is not device memory of the current device");
+            }
+        }
+    }
     std::lock_guard<std::mutex> call_lock(g_call_mutex[dev]);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // every return after the first queued operation waits for the stream, so
+    // the next holder of the lock never overlaps this call's work on the scratch
+    struct SyncOnExit {
+        cudaStream_t st;
+        bool armed = true;
+        ~SyncOnExit() {
+            if (armed) {
+                cudaStreamSynchronize(st);
+                cudaGetLastError();
+            }
+        }
+    } sync_on_exit{st};
     // outputs start as a box without particles; shared counters start at zero
     if ((e = cudaMemsetAsync(d_flags, 0, (size_t)ncells, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(d_owner, 0xff, 4 * (size_t)ncells, st)) != cudaSuccess ||
@@ -148,6 +175,7 @@ extern "C" lbm_status lbm_map_spheres_noalloc(const lbm_grid* grid, double shell
     if ((e = cudaMemcpyAsync(&status, &s->status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return noalloc_fail(LBM_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    sync_on_exit.armed = false;   // the stream was synchronised just above
     if (status & ST_TILE_OVERFLOW)
         return noalloc_fail(LBM_ERR_CAPACITY, "more than 64 spheres reach one 32x4x4 tile");
     return LBM_OK;

@@ -333,14 +333,26 @@ def lbm_map_spheres_noalloc(grid, shell_width, pos, radius, flags, owner):
     """
     import torch
     n = radius.numel()
+    # sizes first (the C side writes nx*ny*nz flag bytes and owners and reads
+    # 3n positions, so an undersized buffer must be refused here)
+    ncells = int(grid.nx) * int(grid.ny) * int(grid.nz)
+    if pos.numel() != 3 * n:
+        raise ValueError('pos must hold 3 x %d values (one centre per radius), got %d' % (n, pos.numel()))
+    if flags.numel() != ncells or owner.numel() != ncells:
+        raise ValueError('flags and owner must hold nx*ny*nz = %d cells, got %d and %d'
+                         % (ncells, flags.numel(), owner.numel()))
     for t, dt in ((pos, torch.float64), (radius, torch.float64), (flags, torch.uint8), (owner, torch.int32)):
         if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
             raise ValueError('expected contiguous CUDA tensors of the documented dtypes')
-    stream = torch.cuda.current_stream(pos.device).cuda_stream
-    _check(load_library().lbm_map_spheres_noalloc(ctypes.byref(grid), float(shell_width), int(n),
-                                                  c_void_p(pos.data_ptr()), c_void_p(radius.data_ptr()),
-                                                  c_void_p(flags.data_ptr()), c_void_p(owner.data_ptr()),
-                                                  c_void_p(stream)))
+    dev = flags.device
+    if any(t.device != dev for t in (pos, radius, owner)):
+        raise ValueError('pos, radius, flags and owner must be on one device')
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        _check(load_library().lbm_map_spheres_noalloc(ctypes.byref(grid), float(shell_width), int(n),
+                                                      c_void_p(pos.data_ptr()), c_void_p(radius.data_ptr()),
+                                                      c_void_p(flags.data_ptr()), c_void_p(owner.data_ptr()),
+                                                      c_void_p(stream)))
 
 
 def lbm_launch_count(ctx):

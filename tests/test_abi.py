@@ -178,3 +178,24 @@ def test_create_in_arena_and_mapping_entry_reject_bad_arguments(lib):
     with pytest.raises(lbmdem.LbmError, match='storage'):
         size = ctypes.c_size_t(0)
         lbmdem._check(lib.lbm_required_bytes(ctypes.byref(g), 5, 1, ctypes.byref(size)))
+
+
+def test_mapping_entry_wrapper_refuses_mismatched_sizes_before_any_gpu_work():
+    # the C side writes nx*ny*nz flag bytes and owners and reads 3 n positions:
+    # buffers of other sizes are refused by the binding (CPU tensors here, so
+    # nothing could have reached a device)
+    torch = pytest.importorskip('torch')
+    from paper_2003_01490_gb300 import lbmdem
+    g = lbmdem.make_grid((16, 16, 32))
+    cells = 16 * 16 * 32
+    ok = dict(pos=torch.zeros(6, dtype=torch.float64), radius=torch.ones(2, dtype=torch.float64),
+              flags=torch.zeros(cells, dtype=torch.uint8), owner=torch.zeros(cells, dtype=torch.int32))
+    bad = [dict(ok, pos=torch.zeros(5, dtype=torch.float64)),
+           dict(ok, flags=torch.zeros(cells - 1, dtype=torch.uint8)),
+           dict(ok, owner=torch.zeros(cells // 2, dtype=torch.int32))]
+    for kw in bad:
+        with pytest.raises(ValueError, match='pos must|flags and owner'):
+            lbmdem.lbm_map_spheres_noalloc(g, 2.0, kw['pos'], kw['radius'], kw['flags'], kw['owner'])
+    # right sizes, but host tensors: refused as not CUDA tensors
+    with pytest.raises(ValueError, match='CUDA'):
+        lbmdem.lbm_map_spheres_noalloc(g, 2.0, ok['pos'], ok['radius'], ok['flags'], ok['owner'])
