@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument('--e2e-steps', type=int, default=200)
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-configs', action='store_true',
+                    help='skip the sphere-wall, precision, batched and served lines of the default run')
     ap.add_argument('--cpu-sample', action='store_true', help=argparse.SUPPRESS)
     ap.add_argument('--cpu-seconds', type=float, default=15.0)
     ap.add_argument('--sample-shape', default='64x64x128', help=argparse.SUPPRESS)
@@ -116,7 +118,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ('stream_collide.cu', 'links.cuh', 'common.cuh'):
+    for f in ('stream_collide.cu', 'stream_collide_staged.cu', 'sc_common.cuh', 'links.cuh', 'common.cuh'):
         with open(os.path.join(ROOT, 'paper_2003_01490_gb300', 'csrc', f), 'rb') as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -242,6 +244,48 @@ def run_cpu_subprocess(seconds, steps=None, warmup=0, shape=(64, 64, 128)):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_cpu_all_cores(seconds, shape=(64, 64, 128)):
+    """One single-threaded oracle replica per host core, all running at once
+    on the same sample box; the value is the sum of their rates (the oracle
+    is a serial program, so its all-core throughput is that of independent
+    replicas)."""
+    n = host_cores()
+    env = dict(os.environ, OMP_NUM_THREADS='1', OPENBLAS_NUM_THREADS='1', MKL_NUM_THREADS='1')
+    cmd = [sys.executable, os.path.abspath(__file__), '--cpu-sample', '--cpu-seconds', str(seconds),
+           '--sample-shape', 'x'.join(str(v) for v in shape)]
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for _ in range(n)]
+    res = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError('oracle sample failed: ' + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    value = sum(r['value'] for r in res)
+    return {'value': value, 'unit': 'MLUPS', 'cores': n, 'kind': 'oracle',
+            'sample': '%d concurrent single-thread replicas of: %s' % (n, res[0]['sample'])}
+
+
+def cpu_baseline_both(seconds):
+    """The oracle timed on one core and on all host cores (value: all cores)."""
+    one = run_cpu_subprocess(seconds)
+    one = {k: one[k] for k in ('value', 'unit', 'cores', 'kind', 'sample')}
+    try:
+        allc = run_cpu_all_cores(seconds)
+    except Exception as ex:   # reported, not fatal
+        allc = dict(one, all_cores_error=str(ex)[:200])
+    out = dict(allc)
+    out['one_core'] = one
+    return out
+
+
 # ------------------------------------------------------------------ main arms
 
 def dist_setup(n):
@@ -304,21 +348,19 @@ def count_links(solid, periodic):
     return n
 
 
-def run_ours(args, rank, world, local):
-    import numpy as np
+def measure_box(w, steps, warmup, world, local, profile_steps=None):
+    """Time `steps` steady-state steps of one context (CUDA graphs, CUDA events
+    on the context's stream, clocks sampled meanwhile), then the same number of
+    steps (or profile_steps) as plain launches with CUDA events between the
+    phases. Returns a dict of the measurements and the final mapping."""
     import torch
     from paper_2003_01490_gb300 import lbmdem as L
-    w = workload(args.workload, args.storage, seed_offset=rank, shape=args.shape,
-                 particles=args.particles)
-    storage = w['storage']
     cells = w['shape'][0] * w['shape'][1] * w['shape'][2]
     ctx = make_context(w)
     add_spheres(ctx, w)
-    L.lbm_step(ctx, args.warmup)
+    L.lbm_step(ctx, warmup)
     L.lbm_sync(ctx)
     stream = torch.cuda.current_stream()
-    # timed region 1 (the value): the production path, steady-state steps
-    # replayed as CUDA graphs
     launches0 = L.lbm_launch_count(ctx)
     clocks = ClockSampler(local)
     clocks.start()
@@ -326,7 +368,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    L.lbm_step(ctx, args.steps)
+    L.lbm_step(ctx, steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -334,10 +376,8 @@ def run_ours(args, rank, world, local):
     L.lbm_sync(ctx)
     ms = e0.elapsed_time(e1)
     launches = L.lbm_launch_count(ctx) - launches0
-    # timed region 2 (the phase split and the kernel time of the roofline):
-    # the same steps with CUDA events between the phases (plain launches)
     L.lbm_profile(ctx, 1)
-    L.lbm_step(ctx, args.steps)
+    L.lbm_step(ctx, profile_steps or steps)
     L.lbm_sync(ctx)
     phases, nsteps = L.lbm_profile_read(ctx)
     L.lbm_profile(ctx, 0)
@@ -345,50 +385,88 @@ def run_ours(args, rank, world, local):
     solid = (flags & L.FLAG_SOLID) != 0
     n_solid = int(solid.sum())
     n_links = count_links(solid, w['periodic'])
+    del ctx
+    torch.cuda.synchronize()
     ms_max = allreduce_max(ms, world)
-    value = whole_job_mlups(world, cells, args.steps, ms_max)
+    return dict(cells=cells, ms=ms_max, value=whole_job_mlups(world, cells, steps, ms_max), clocks=clk,
+                launches=launches, phases=phases, nsteps=nsteps, n_solid=n_solid, n_links=n_links)
 
-    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+
+_FP64_PEAK = None
+
+
+def fp64_peak():
+    """Measured float64 FMA throughput (TFLOP/s) of this device, once per run."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        from paper_2003_01490_gb300 import lbmdem as L
+        try:
+            _FP64_PEAK = (L.lbm_fp64_fma_rate(), 'measured: lbm_fp64_fma_rate (8 independent FMA chains per '
+                                                 'thread, 8 x 256 threads per SM, CUDA events, best of 3)')
+        except Exception as ex:
+            _FP64_PEAK = (FP64_PEAK_TFLOPS, 'derived (measurement failed: %s): 152 SMs x 2.07 GHz x 2 '
+                                            'float64 FMA per clock x 2 FLOP' % str(ex)[:80])
+    return _FP64_PEAK
+
+
+def dense_roofline(m, storage, workload_name):
+    """Roofline of the dense kernel: algorithmic bytes per launch (fluid cells
+    x (2 x 19 PDFs + 1 flag byte), solid cells x 1 flag byte) over its mean
+    launch time from the CUDA events of the profiled region."""
+    cells, n_solid, n_links, phases, nsteps = m['cells'], m['n_solid'], m['n_links'], m['phases'], m['nsteps']
     bf, bs = bytes_per_cell(storage)
-    # per link the kernel also reads f~_p(x) and f~_q(x) at the cell itself
-    # (CLI, Eq. (14)), values no pull reads
+    alg_bytes = (cells - n_solid) * bf + n_solid * bs
+    # not algorithmic: per link the kernel also reads f~_p(x) and f~_q(x) at
+    # the cell itself (CLI, Eq. (14)), values no pull reads
     es = {'f64': 8, 'f32': 4}.get(storage, 2)
-    alg_bytes = (cells - n_solid) * bf + n_solid * bs + n_links * 2 * es
     k_ms = phases['stream_collide'] / max(nsteps, 1)
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = recorded_traffic(storage, args.workload)
+    traffic = recorded_traffic(storage, workload_name)
     share = {k: round(v / sum(phases.values()), 4) for k, v in phases.items()} if sum(phases.values()) else {}
     roofline = {'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
                 'frac': round(achieved / peak, 4), 'traffic': traffic,
-                'kernel': 'stream_collide_kernel (pull stream with the particle links: CLI condition and '
-                          'momentum exchange; wall bounce-back; TRT+aB collision)',
+                'kernel': ('stream_collide_kernel' if storage == 'f64' else 'stream_collide_staged_kernel') +
+                          ' (pull stream with the particle links: CLI condition and momentum exchange; wall '
+                          'bounce-back; TRT+aB collision)',
                 'kernel_ms_per_launch': round(k_ms, 5), 'alg_bytes_per_launch': int(alg_bytes),
-                'links_per_launch': int(n_links),
+                'links_per_launch': int(n_links), 'link_bytes_per_launch': int(n_links * 2 * es),
                 'peak_source': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
                 else 'fallback 6.8 TB/s', 'phase_share': share}
     if storage == 'f64':
-        # float64: GB300's float64 units (1.26 TFLOP/s) bind before HBM
-        # (305 B and ~230 FLOP per fluid cell)
+        # float64: GB300's float64 units bind before HBM (305 B and ~230 FLOP
+        # per fluid cell)
+        fpk, fsrc = fp64_peak()
         flops = (cells - n_solid) * FLOP_PER_FLUID_CELL + n_links * FLOP_PER_LINK
         achieved_tf = flops / (k_ms * 1e-3) / 1e12
-        roofline.update({'bound': 'alu', 'achieved': round(achieved_tf, 4), 'peak': FP64_PEAK_TFLOPS,
-                         'unit': 'TFLOP/s', 'frac': round(achieved_tf / FP64_PEAK_TFLOPS, 4),
-                         'alg_flops_per_launch': int(flops),
-                         'peak_source': 'derived: 152 SMs x 2.07 GHz x 2 float64 FMA per clock x 2 FLOP',
+        roofline.update({'bound': 'alu', 'achieved': round(achieved_tf, 4), 'peak': round(fpk, 4),
+                         'unit': 'TFLOP/s', 'frac': round(achieved_tf / fpk, 4),
+                         'alg_flops_per_launch': int(flops), 'peak_source': fsrc,
                          'hbm': {'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
                                  'frac': round(achieved / peak, 4)}})
+    return roofline
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    w = workload(args.workload, args.storage, seed_offset=rank, shape=args.shape,
+                 particles=args.particles)
+    storage = w['storage']
+    cells = w['shape'][0] * w['shape'][1] * w['shape'][2]
+    m = measure_box(w, args.steps, args.warmup, world, local)
+    value, ms_max, clk, launches, n_solid = m['value'], m['ms'], m['clocks'], m['launches'], m['n_solid']
+    roofline = dense_roofline(m, storage, args.workload)
 
     e2e = None
     if not args.no_e2e:
-        del ctx
-        torch.cuda.synchronize()
         e2e = run_e2e(args, w, world)
+    configs = None
+    if not args.no_configs and args.workload == 'suspension' and not args.shape:
+        configs = measure_configs(args, rank, world, local)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cpu = run_cpu_subprocess(args.cpu_seconds)
-            cpu = {k: cpu[k] for k in ('value', 'unit', 'cores', 'kind', 'sample')}
+            cpu = cpu_baseline_both(args.cpu_seconds)
         except Exception as ex:  # reported, not fatal
             cpu = {'value': None, 'error': str(ex)[:200]}
     line = {
@@ -404,6 +482,8 @@ def run_ours(args, rank, world, local):
         'roofline': roofline, 'cpu_baseline': cpu, 'e2e': e2e, 'clocks': clk,
         'gpu_launches': int(launches),
     }
+    if configs is not None:
+        line['configs'] = configs
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -470,17 +550,16 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, world, local):
+def measure_batched(n_inst, steps_divisor, storage, rank, world, local):
     """Many small independent boxes: every instance has its own context and
     CUDA stream, and all of them advance concurrently (steady-state steps are
-    graph launches). The value is the aggregate MLUPS over all instances; the
-    same work run one instance at a time (the plain per-job loop) is reported
-    beside it."""
+    graph launches). Returns the aggregate MLUPS over all instances and the
+    same work run one instance at a time (the plain per-job loop)."""
     import torch
     from paper_2003_01490_gb300 import lbmdem as L
     from paper_2003_01490_gb300 import workloads
-    inst = workloads.batched(n=args.instances, seed=20030149 + 1000 * rank,
-                             storage=args.storage or 'f32', steps_divisor=args.steps_divisor)
+    inst = workloads.batched(n=n_inst, seed=20030149 + 1000 * rank, storage=storage,
+                             steps_divisor=steps_divisor)
     work = sum(w['shape'][0] * w['shape'][1] * w['shape'][2] * w['steps'] for w in inst)
 
     def build():
@@ -530,57 +609,115 @@ def run_batched(args, rank, world, local):
     for ctx, _ in ctxs:
         L.lbm_sync(ctx)
     launches = sum(L.lbm_launch_count(c) for c, _ in ctxs) - launches0
-    value = world * work / t_bat / 1e6
+    del ctxs
+    torch.cuda.synchronize()
     cells = [w['shape'][0] * w['shape'][1] * w['shape'][2] for w in inst]
-    line = {
-        'metric': 'MLUPS', 'value': round(value, 1), 'unit': 'MLUPS', 'n_gpus': world,
-        'steps': sum(w['steps'] for w in inst), 'warmup': 3, 'ms_per_step': None,
-        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
-        'dtype': args.storage or 'f32', 'data': 'synthetic',
-        'config': {'workload': 'batched: %d sphere-wall boxes, sides 32-96 (s x s x 2s), %d-%d cells, '
-                               'steps 2000-10000 / %d' % (len(inst), min(cells), max(cells), args.steps_divisor),
-                   'cell_updates': int(work), 'streams': len(inst),
-                   'l2': 'working set %.1f GB of PDFs > 129 MB L2' % (sum(cells) * 2 * 19 * 4 / 1e9),
-                   'parallelism': 'replicas' if world > 1 else 'single GPU'},
+    return {
+        'value': round(world * work / t_bat / 1e6, 1), 'unit': 'MLUPS',
+        'workload': 'batched: %d sphere-wall boxes, sides 32-96 (s x s x 2s), %d-%d cells, steps 2000-10000 / %d, %s'
+                    % (len(inst), min(cells), max(cells), steps_divisor, storage),
+        'cell_updates': int(work), 'steps': sum(w['steps'] for w in inst), 'streams': len(inst),
+        'l2': 'working set %.1f GB of PDFs > 129 MB L2' % (sum(cells) * 2 * 19 * 4 / 1e9),
         'sequential': {'value': round(world * work / t_seq / 1e6, 1), 'unit': 'MLUPS',
                        'kind': 'the same instances one at a time (plain per-job loop)'},
         'wall_s': {'batched': round(t_bat, 3), 'sequential': round(t_seq, 3)},
-        'clocks': clk, 'gpu_launches': int(launches),
+        'clocks': clk, 'gpu_launches': int(launches)}
+
+
+def run_batched(args, rank, world, local):
+    storage = args.storage or 'f32'
+    r = measure_batched(args.instances, args.steps_divisor, storage, rank, world, local)
+    line = {
+        'metric': 'MLUPS', 'value': r['value'], 'unit': 'MLUPS', 'n_gpus': world,
+        'steps': r['steps'], 'warmup': 3, 'ms_per_step': None,
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': storage, 'data': 'synthetic',
+        'config': {'workload': r['workload'], 'cell_updates': r['cell_updates'], 'streams': r['streams'],
+                   'l2': r['l2'], 'parallelism': 'replicas' if world > 1 else 'single GPU'},
+        'sequential': r['sequential'], 'wall_s': r['wall_s'], 'clocks': r['clocks'],
+        'gpu_launches': r['gpu_launches'],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_served(n_jobs, steps_divisor, rank, local):
+    """A seeded stream of jobs (Poisson arrivals; sphere-wall and suspension
+    cubes of 32^3 to 128^3) served with continuous batching in float16 and in
+    float32 storage, and the plain float32 FIFO loop, all on the same trace:
+    float16-served against float32-served isolates the precision gain,
+    float32-served against the float32 FIFO loop the concurrency gain."""
+    import torch
+    from paper_2003_01490_gb300 import serve, workloads
+    jobs = workloads.served(n=n_jobs, seed=20030149 + 1000 * rank, storage='f16', steps_divisor=steps_divisor)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    out = {'workload': 'served: %d jobs, Poisson arrivals (mean gap 4 ms), sphere-wall and suspension '
+                       'cubes 32^3-128^3, steps 1000-20000 / %d' % (len(jobs), steps_divisor),
+           'budget_bytes': budget}
+    for key, storage, fn in (('served_f16', 'f16', 'serve'), ('served_f32', 'f32', 'serve'),
+                             ('fifo_f32', 'f32', 'fifo')):
+        js = [dict(j, storage=storage) for j in jobs]
+        clocks = ClockSampler(local)
+        clocks.start()
+        rec = serve.serve(js, budget) if fn == 'serve' else serve.fifo(js)
+        clk = clocks.stop()
+        out[key] = dict(serve.summary(rec), clocks=clk)
+    return out
 
 
 def run_served(args, rank, world, local):
-    """A seeded stream of jobs (Poisson arrivals; sphere-wall and suspension
-    cubes of 32^3 to 128^3) served with continuous batching in float16
-    storage, against the plain float32 FIFO loop on the same trace."""
-    import torch
-    from paper_2003_01490_gb300 import serve, workloads
-    jobs = workloads.served(n=args.instances if '--instances' in sys.argv else 48,
-                            seed=20030149 + 1000 * rank, storage=args.storage or 'f16',
-                            steps_divisor=args.steps_divisor if '--steps-divisor' in sys.argv else 50)
-    free, total = torch.cuda.mem_get_info()
-    budget = int(0.8 * free)
-    clocks = ClockSampler(local)
-    clocks.start()
-    rec = serve.serve(jobs, budget)
-    clk = clocks.stop()
-    base_jobs = [dict(j, storage='f32') for j in jobs]
-    base = serve.fifo(base_jobs)
-    s_srv, s_fifo = serve.summary(rec), serve.summary(base)
+    n = args.instances if '--instances' in sys.argv else 48
+    div = args.steps_divisor if '--steps-divisor' in sys.argv else 50
+    r = measure_served(n, div, rank, local)
+    s_srv = r['served_f16']
     line = {
         'metric': 'MLUPS', 'value': s_srv['mlups'], 'unit': 'MLUPS', 'n_gpus': world,
-        'steps': sum(j['steps'] for j in jobs), 'warmup': 0, 'ms_per_step': None,
+        'steps': None, 'warmup': 0, 'ms_per_step': None,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
-        'dtype': args.storage or 'f16', 'data': 'synthetic',
-        'config': {'workload': 'served: %d jobs, Poisson arrivals (mean gap 4 ms), sphere-wall and suspension '
-                               'cubes 32^3-128^3, steps 1000-20000 / 50' % len(jobs),
-                   'budget_bytes': budget, 'parallelism': 'replicas' if world > 1 else 'single GPU'},
-        'served': s_srv, 'fifo_f32': s_fifo, 'clocks': clk,
+        'dtype': 'f16', 'data': 'synthetic',
+        'config': {'workload': r['workload'], 'budget_bytes': r['budget_bytes'],
+                   'parallelism': 'replicas' if world > 1 else 'single GPU'},
+        'served': s_srv, 'served_f32': r['served_f32'], 'fifo_f32': r['fifo_f32'], 'clocks': s_srv['clocks'],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_configs(args, rank, world, local):
+    """The other workloads, each in a short timed region with its own clocks
+    record: the float64 sphere-wall collision over its 2000 steps, the
+    suspension in float16 and bfloat16 storage, the batched boxes and the
+    served job stream."""
+    out = {}
+    try:
+        w = workload('sphere-wall')
+        m = measure_box(w, 2000, 5, world, local, profile_steps=200)
+        out['sphere_wall_f64'] = {'workload': w['name'] + ', 2000 steps', 'value': round(m['value'], 1),
+                                  'unit': 'MLUPS', 'us_per_step': round(m['ms'] / 2000 * 1e3, 2),
+                                  'roofline': dense_roofline(m, 'f64', 'sphere-wall'), 'clocks': m['clocks'],
+                                  'gpu_launches': int(m['launches'])}
+    except Exception as ex:   # reported, not fatal
+        out['sphere_wall_f64'] = {'error': str(ex)[:300]}
+    for st in ('f16', 'bf16'):
+        try:
+            w = workload('suspension', st)
+            m = measure_box(w, 200, 5, world, local, profile_steps=100)
+            out['suspension_' + st] = {'workload': w['name'], 'value': round(m['value'], 1), 'unit': 'MLUPS',
+                                       'ms_per_step': round(m['ms'] / 200, 5),
+                                       'roofline': dense_roofline(m, st, 'suspension'), 'clocks': m['clocks'],
+                                       'gpu_launches': int(m['launches'])}
+        except Exception as ex:
+            out['suspension_' + st] = {'error': str(ex)[:300]}
+    try:
+        out['batched'] = measure_batched(64, 20, 'f32', rank, world, local)
+    except Exception as ex:
+        out['batched'] = {'error': str(ex)[:300]}
+    try:
+        out['served'] = measure_served(48, 50, rank, local)
+    except Exception as ex:
+        out['served'] = {'error': str(ex)[:300]}
+    return out
 
 
 def main():
@@ -595,6 +732,18 @@ def main():
         world = int(os.environ.get('WORLD_SIZE', '1'))
         run_reference(args, rank, world)
         return
+    if args.gpus > 1 and 'WORLD_SIZE' not in os.environ:
+        # not under torch.distributed.run yet: launch one rank per GPU
+        import socket
+        with socket.socket() as so:
+            so.bind(('127.0.0.1', 0))
+            port = so.getsockname()[1]
+        cmd = [sys.executable, '-m', 'torch.distributed.run', '--nnodes=1', '--nproc-per-node', str(args.gpus),
+               '--master-addr', '127.0.0.1', '--master-port', str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        os.execv(sys.executable, cmd)
+    if int(os.environ.get('WORLD_SIZE', '1')) != args.gpus:
+        sys.exit('bench.py: --gpus %d but WORLD_SIZE=%s ranks were launched'
+                 % (args.gpus, os.environ.get('WORLD_SIZE')))
     rank, world, local = dist_setup(args.gpus)
     if args.workload == 'batched':
         run_batched(args, rank, world, local)

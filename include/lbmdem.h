@@ -50,6 +50,7 @@ typedef enum {
     LBM_ERR_UNSTABLE = -4,  /* NaN or |rho - 1| > 0.5 on the device, or a particle
                                faster than 0.5 cells per step                    */
     LBM_ERR_CAPACITY = -5,  /* a fixed-capacity device list overflowed           */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded wait inside a kernel ran out (1 s)      */
     LBM_ERR_STATE = -7      /* call not allowed in the current state             */
 } lbm_status;
 
@@ -282,6 +283,16 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *phase_ms, long long *steps);
 lbm_status lbm_map_spheres_noalloc(const lbm_grid *grid, double shell_width, int n,
                                    const double *d_pos, const double *d_radius,
                                    unsigned char *d_flags, int *d_owner, void *cuda_stream);
+
+/* Measured float64 FMA throughput of the current device in TFLOP/s (2 FLOP
+ * per FMA): a kernel of eight independent FMA chains per thread, 8 blocks of
+ * 256 threads per multiprocessor, iters FMAs per chain, best of three timed
+ * launches (CUDA events on a private stream). The paper has no counterpart;
+ * it is the peak of the float64 roofline that bench.py reports for the
+ * float64 storage form. Allocates and frees one small device buffer.
+ * Errors: LBM_ERR_INVALID (iters < 1, tflops_out NULL), LBM_ERR_CUDA; the
+ * message is returned by lbm_last_error(NULL). */
+lbm_status lbm_fp64_fma_rate(int iters, double *tflops_out);
 
 /* Number of kernel launches this context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);

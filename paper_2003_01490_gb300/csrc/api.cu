@@ -179,7 +179,7 @@ void build_layout(const lbm_grid* g, lbm_storage st, int np, Layout& L, const Si
     const size_t n = (size_t)np;
     L.add(19 * N * es);                 // 0 f[0]
     L.add(19 * N * es);                 // 1 f[1]
-    L.add(N);                           // 2 flags
+    L.add(N + 256);                     // 2 flags (+ padding: the staged dense kernel copies whole 16-byte units)
     L.add(4 * N);                       // 3 owner
     L.add(4 * s.ntiles);                // 4 tile_count
     L.add(4 * s.ntiles * TILE_CAP);     // 5 tile_list
@@ -552,6 +552,8 @@ lbm_status check_status(lbm_ctx* ctx) {
         return fail(ctx, LBM_ERR_CAPACITY, buf);
     }
     if (st & ST_FAST_PARTICLE) return fail(ctx, LBM_ERR_UNSTABLE, "particle speed above 0.5 cells per step");
+    if (st & ST_TIMEOUT)
+        return fail(ctx, LBM_ERR_TIMEOUT, "a wait of the staged dense kernel on its copy pipeline ran out");
     return LBM_OK;
 }
 

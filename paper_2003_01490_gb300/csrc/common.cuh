@@ -73,7 +73,7 @@ constexpr uint8_t FL_SOLID = 0x01, FL_SHELL = 0x02, FL_NEAR = 0x04, FL_MISS = 0x
 // device status bits (sticky, reported to the host by lbm_sync)
 constexpr int ST_UNSTABLE = 1, ST_TILE_OVERFLOW = 2, ST_NBR_OVERFLOW = 4, ST_BIN_OVERFLOW = 8,
               ST_REFILL_OVERFLOW = 16, ST_HIST_OVERFLOW = 32, ST_FAST_PARTICLE = 64,
-              ST_FIXED_OVERFLOW = 128;
+              ST_FIXED_OVERFLOW = 128, ST_TIMEOUT = 256;
 
 // capacities of the fixed-size device lists
 constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;   // mapping tile (512 cells)

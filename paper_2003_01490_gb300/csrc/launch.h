@@ -29,6 +29,8 @@ struct LbmStepParams {
     int num_sms;                     // multiprocessors of the device (grid sizing)
     double* accel_d;                 // out: fluid body force of the step [3]
     float* accel_f;
+    int use_staged;                  // 1: the dense kernel with bulk-copy staging where it applies
+    int staged_zchunk;               // z planes per work item of the staged kernel (0: automatic)
 };
 // BC_ACCEL: the fluid body force of the step; BC_LINKS: the missing links
 constexpr int BC_ACCEL = 1, BC_LINKS = 2;
@@ -36,6 +38,10 @@ void launch_boundary(const LbmStepParams& p, cudaStream_t st, int mode);
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st);
 // kernel attributes on the current device (before any launch or capture)
 cudaError_t prepare_stream_collide(int storage);
+// the dense kernel with bulk-copy staging of the pulls (4- and 2-byte formats)
+bool staged_applicable(const LbmStepParams& p);
+void launch_stream_collide_staged(const LbmStepParams& p, cudaStream_t st);
+cudaError_t prepare_stream_collide_staged(int storage);
 
 struct MapParams {
     Geom g;

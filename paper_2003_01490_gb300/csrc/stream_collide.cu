@@ -30,9 +30,7 @@
 // in integers; the remainder is summed per warp in float32 and per particle
 // in 64-bit fixed point (scale 2^32) through integer atomics. No float64
 // arithmetic runs per cell or link on the float32 path.
-#include "common.cuh"
-#include "launch.h"
-#include "links.cuh"
+#include "sc_common.cuh"
 
 // minimum resident blocks per SM requested for the kernel with 4-byte or
 // smaller storage (a register cap of 64 at 256 threads); tuned on GB300
@@ -53,184 +51,6 @@
 #define LBM_SC_BX 128
 #endif
 namespace lbmdem {
-
-template <typename S, typename T>
-struct SCArgs {
-    const S* __restrict__ src;
-    S* __restrict__ dst;
-    const uint8_t* __restrict__ flags;
-    Geom g;
-    T s_plus, s_minus, s_b_shell, s_b_bulk;
-    T uw[2][3][3];                   // wall velocities [side][axis][component]
-    int bulk_corr;
-    const T* __restrict__ accel;     // [3]
-    int* status;
-    int zchunk;                      // z planes per block
-    // particles (for the links)
-    int np;
-    const int* __restrict__ owner;   // particle of a solid cell, -1 for fluid
-    const double* __restrict__ px;
-    const double* __restrict__ pu;
-    const double* __restrict__ pom;
-    const double* __restrict__ pR;
-    const PartView* __restrict__ view;
-    double* acc_d;
-    long long* acc_i;
-    long long* acc_k;
-};
-
-// NaN marker of a solid cell of particle owner, and a plain NaN
-template <typename T>
-__device__ __forceinline__ T solid_marker(int owner);
-template <> __device__ __forceinline__ float solid_marker<float>(int owner) { return __uint_as_float(marker_bits32(owner)); }
-template <> __device__ __forceinline__ double solid_marker<double>(int owner) {
-    return __longlong_as_double((long long)marker_bits64(owner));
-}
-template <typename T>
-__device__ __forceinline__ T plain_nan() { return solid_marker<T>(MARKER_PAYLOAD - 1); }
-
-// CLI value f_q(x, t+1) of the link of fluid cell (x, y, z) in pull direction
-// q into the solid cell x - c_q, and its force and torque into acc (float32
-// path: the remainder part in floats, the constant part as exact integers)
-// per-direction word of the link code: c_q + 1 in bits 0-1, 2-3, 4-5, the
-// opposite direction in bits 6-10 (read from shared memory: a warp's lanes
-// hold different directions)
-__host__ __device__ constexpr int qinfo(int q) { return (cx(q) + 1) | ((cy(q) + 1) << 2) | ((cz(q) + 1) << 4) | (opp(q) << 6); }
-
-template <typename S, typename T>
-__device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int z, int q, int qi, int key1,
-                                        unsigned lm_src, T fdown_raw, Acc<T>& acc, const Sinks& sk) {
-    const int nx = a.g.n[0], ny = a.g.n[1];
-    const int plane = nx * ny;
-    const long long N = a.g.ncells;
-    const int c[3] = {(qi & 3) - 1, ((qi >> 2) & 3) - 1, ((qi >> 4) & 3) - 1};
-    const int p = (qi >> 6) & 31;
-    const int idx = z * plane + y * nx + x;
-    // the particle from the marker's payload (the owner array for 16-bit storage)
-    int i = key1 - 1;
-    if (key1 <= 0) {
-        const int uv[3] = {wrap_idx(x - c[0], nx), wrap_idx(y - c[1], ny), wrap_idx(z - c[2], a.g.n[2])};
-        i = a.owner[uv[2] * plane + uv[1] * nx + uv[0]];
-    }
-    if (i < 0 || i >= a.np) return plain_nan<T>();   // a NaN from a fluid cell: left for the stability check
-    const T fout = Store<S>::load(a.src + p * N + idx);
-    const T fin = Store<S>::load(a.src + q * N + idx);
-    // CLI needs x + c_q fluid and inside the box; its post-collision f_p is the
-    // cell's own pull in direction p (marker there: bounce-back coefficients)
-    bool cli = !((lm_src >> p) & 1u);
-    if (!a.g.per[0] && (x + c[0] < 0 || x + c[0] >= nx)) cli = false;
-    if (!a.g.per[1] && (y + c[1] < 0 || y + c[1] >= ny)) cli = false;
-    if (!a.g.per[2] && (z + c[2] < 0 || z + c[2] >= a.g.n[2])) cli = false;
-    const T fdown = cli ? fdown_raw : T(0);
-    T r[3], R, u[3], om[3];
-    int n[3];
-    T cc;   // |r|^2 - R^2
-    if constexpr (sizeof(T) == 4) {
-        float g[3], C;
-        PartOps<T>::load(a, i, x, y, z, r, n, g, C, R, u, om);
-        cc = surface_cc_split(n, g, C);
-    } else {
-        PartOps<T>::load(a, i, x, y, z, r, n, R, u, om);
-        cc = surface_cc<T>(r, R);
-    }
-    const int cp[3] = {-c[0], -c[1], -c[2]};
-    const T cp0 = (T)cp[0], cp1 = (T)cp[1], cp2 = (T)cp[2];
-    const int cc2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    const T w = cc2 == 1 ? T(1) / T(18) : T(1) / T(36);
-    const T delta = link_root<T>(r, cc, cp0, cp1, cp2, (T)cc2);
-    const T dbc = cli ? delta : T(0.5);
-    const T inv = fast_div(T(1), T(1) + T(2) * dbc);
-    const T kappa = (T(1) - T(2) * dbc) * inv;
-    const T rb[3] = {r[0] + delta * cp0, r[1] + delta * cp1, r[2] + delta * cp2};
-    const T ub[3] = {u[0] + (om[1] * rb[2] - om[2] * rb[1]), u[1] + (om[2] * rb[0] - om[0] * rb[2]),
-                     u[2] + (om[0] * rb[1] - om[1] * rb[0])};
-    const T ubc = ub[0] * cp0 + ub[1] * cp1 + ub[2] * cp2;
-    const T v = fout + kappa * (fdown - fin) - (T(12) * w * inv) * ubc;
-    // Eq. (15) on shifted PDFs: F = c_p (2 w + f~_p + f_q) - u_b (f~_p - f_q)
-    const T dif = fout - v;
-    int K[6] = {0, 0, 0, 0, 0, 0};
-    T sum;
-    if (sizeof(T) == 4) {
-        // 2 w_p c_p and its torque 2 w_p (n x c_p) as exact integers (x 36)
-        const int kw = cc2 == 1 ? 4 : 2;
-        sum = fout + v;
-        K[0] = kw * cp[0]; K[1] = kw * cp[1]; K[2] = kw * cp[2];
-        K[3] = kw * (n[1] * cp[2] - n[2] * cp[1]);
-        K[4] = kw * (n[2] * cp[0] - n[0] * cp[2]);
-        K[5] = kw * (n[0] * cp[1] - n[1] * cp[0]);
-    } else {
-        sum = T(2) * w + fout + v;
-    }
-    const T F[3] = {cp0 * sum - ub[0] * dif, cp1 * sum - ub[1] * dif, cp2 * sum - ub[2] * dif};
-    const T Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
-    accumulate<T>(i, F, Tq, K, acc, sk);
-    return v;
-}
-
-// TRT+aB collision of one fluid cell (in place) and the store of its PDFs
-template <typename S, typename T>
-__device__ __forceinline__ void collide_store(const SCArgs<S, T>& a, T (&f)[Q], uint8_t fl, long long N, int idx) {
-    // ------------------------------------------- TRT+aB collision (in place)
-    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        drho += f[q];
-        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
-        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
-        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
-    }
-    const T ax = a.accel[0], ay = a.accel[1], az = a.accel[2];
-    const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
-    const T usq = ux * ux + uy * uy + uz * uz;
-    const T ua = ux * ax + uy * ay + uz * az;
-    const T sp = a.s_plus, sm = a.s_minus;
-    const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
-    // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) of the streamed
-    // PDFs relax with s_b in shell cells (and everywhere when Lambda_b,bulk != 1)
-    const bool shell = (fl & FL_SHELL) != 0;
-    const bool bulk = shell || a.bulk_corr;
-    T k4 = T(0), k5 = T(0);
-    if (bulk) {
-        const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
-        T saxis = T(0), sdiag = T(0);
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            if (c2(q) == 1) saxis += f[q]; else sdiag += f[q];
-        }
-        const T m4 = -f[0] + sdiag;
-        const T m5 = f[0] - T(2) * saxis + sdiag;
-        // M^-1 e_k = w_q M_kq / (sum_q w_q M_kq^2): norms 2/3 (row 4) and 2 (row 5)
-        k4 = T(1.5) * (ds * ((usq - m4) - ua));
-        k5 = T(0.5) * (ds * (-m5));
-    }
-    {
-        const T w0 = wq<T>(0);
-        const T feq0 = w0 * (drho - T(1.5) * usq);
-        f[0] = f[0] - sp * (f[0] - feq0) + gp * (w0 * (T(-3) * ua)) + w0 * (k5 - k4);
-    }
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const int qb = opp(q);
-        if (qb < q) continue;
-        const T w = wq<T>(q);
-        const T cu = (T)cx(q) * ux + (T)cy(q) * uy + (T)cz(q) * uz;
-        const T ca = (T)cx(q) * ax + (T)cy(q) * ay + (T)cz(q) * az;
-        const T ep = w * (drho + T(4.5) * cu * cu - T(1.5) * usq);
-        const T em = w * (T(3) * cu);
-        const T Fp = w * (T(-3) * ua + T(9) * cu * ca);
-        const T Fm = w * (T(3) * ca);
-        const T fp = T(0.5) * (f[q] + f[qb]);
-        const T fm = T(0.5) * (f[q] - f[qb]);
-        const T corr = c2(q) == 1 ? w * (T(-2) * k5) : w * (k4 + k5);
-        const T dp = -sp * (fp - ep) + gp * Fp + corr;
-        const T dm = -sm * (fm - em) + gm * Fm;
-        f[q] = f[q] + dp + dm;
-        f[qb] = f[qb] + dp - dm;
-    }
-    if (!(drho < T(0.5) && drho > T(-0.5))) atomicOr(a.status, ST_UNSTABLE);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) Store<S>::store(a.dst + q * N + idx, f[q]);
-}
 
 // a lane's open force sums between rows: particle, float sums and the exact
 // integer sums (float32 path) as two 16-bit halves per word; sums that could
@@ -312,20 +132,26 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
 
     const int z_begin = blockIdx.z * a.zchunk;
     const int z_end = min(nz, z_begin + a.zchunk);
+    // the 19 pulls of cell (x, y, zz) with periodic wrap (walls are handled
+    // below), issued only for a fluid cell
+    auto pull_row = [&](int zz, bool fluid_zz, T (&g)[Q]) {
+        if (!fluid_zz) return;
+        const int idz = zz * plane + y * nx + x;
+        const int OX[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
+        const int OY[3] = {y == 0 ? plane - nx : -nx, 0, y == ny - 1 ? nx - plane : nx};
+        const int OZ[3] = {zz == 0 ? (nz - 1) * plane : -plane, 0, zz == nz - 1 ? (1 - nz) * plane : plane};
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            g[q] = Store<S>::load(a.src + q * N + (idz + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
+    };
     for (int z = z_begin; z < z_end; ++z) {
         const int idx = z * plane + y * nx + x;
-        const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
-        const bool fluid = !(fl & FL_SOLID);
         T f[Q];
+        const uint8_t fl = valid ? a.flags[idx] : FL_SOLID;
+        pull_row(z, !(fl & FL_SOLID), f);
+        const bool fluid = !(fl & FL_SOLID);
         unsigned lmask = 0;   // pull directions of this cell that are particle links
         if (fluid) {
-            // neighbour offsets with periodic wrap (walls are handled below)
-            const int OX[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
-            const int OY[3] = {y == 0 ? plane - nx : -nx, 0, y == ny - 1 ? nx - plane : nx};
-            const int OZ[3] = {z == 0 ? (nz - 1) * plane : -plane, 0, z == nz - 1 ? (1 - nz) * plane : plane};
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                f[q] = Store<S>::load(a.src + q * N + (idx + OX[1 - cx(q)] + OY[1 - cy(q)] + OZ[1 - cz(q)]));
 #pragma unroll
             for (int q = 1; q < Q; ++q)
                 if (f[q] != f[q]) lmask |= 1u << q;   // marker of a solid upstream cell
@@ -406,6 +232,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
         if (fluid) {
             collide_store<S, T>(a, f, fl, N, idx);
         }
+
     }
     if (open) {   // warp-uniform
         Acc<T> acc;
@@ -424,30 +251,7 @@ template <typename S>
 void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
     using T = typename Store<S>::T;
     SCArgs<S, T> a;
-    a.src = static_cast<const S*>(p.src);
-    a.dst = static_cast<S*>(p.dst);
-    a.flags = p.flags;
-    a.g = p.g;
-    a.s_plus = (T)p.s_plus;
-    a.s_minus = (T)p.s_minus;
-    a.s_b_shell = (T)p.s_b_shell;
-    a.s_b_bulk = (T)p.s_b_bulk;
-    for (int s = 0; s < 2; ++s)
-        for (int ax = 0; ax < 3; ++ax)
-            for (int c = 0; c < 3; ++c) a.uw[s][ax][c] = (T)p.g.wall_vel[s][ax][c];
-    a.bulk_corr = p.bulk_corr;
-    a.accel = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)p.accel_d : (const void*)p.accel_f);
-    a.status = p.status;
-    a.np = p.P.n;
-    a.owner = p.owner;
-    a.px = p.P.x;
-    a.pu = p.P.u;
-    a.pom = p.P.om;
-    a.pR = p.P.R;
-    a.view = p.P.view;
-    a.acc_d = p.P.acc_d;
-    a.acc_i = p.P.acc_i;
-    a.acc_k = p.P.acc_k;
+    fill_sc_args<S, T>(p, a);
     const int nx = p.g.n[0];
     int bx = nx >= LBM_SC_BX ? LBM_SC_BX : ((nx + 31) / 32) * 32;
     int by = 256 / bx;
@@ -472,15 +276,24 @@ cudaError_t prepare_t() {
 }
 
 cudaError_t prepare_stream_collide(int storage) {
+    cudaError_t e;
     switch (storage) {
-        case 0: return prepare_t<double>();
-        case 1: return prepare_t<float>();
-        case 2: return prepare_t<__half>();
-        default: return prepare_t<__nv_bfloat16>();
+        case 0: e = prepare_t<double>(); break;
+        case 1: e = prepare_t<float>(); break;
+        case 2: e = prepare_t<__half>(); break;
+        default: e = prepare_t<__nv_bfloat16>(); break;
     }
+    return e == cudaSuccess ? prepare_stream_collide_staged(storage) : e;
 }
 
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st) {
+    // on request, for 4- and 2-byte formats on boxes whose rows start on
+    // 16-byte boundaries: the kernel with bulk-copy staging
+    // (stream_collide_staged.cu)
+    if (p.use_staged && staged_applicable(p)) {
+        launch_stream_collide_staged(p, st);
+        return;
+    }
     switch (p.storage) {
         case 0: launch_stream_collide_t<double>(p, st); break;
         case 1: launch_stream_collide_t<float>(p, st); break;

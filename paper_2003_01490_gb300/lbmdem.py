@@ -22,14 +22,15 @@ STORAGE = {'f64': 0, 'f32': 1, 'f16': 2, 'bf16': 3}
 MOTION_DEM, MOTION_FIXED, MOTION_PRESCRIBED = 0, 1, 2
 FLAG_SOLID, FLAG_SHELL, FLAG_NEAR, FLAG_MISS, FLAG_NEWFLUID, FLAG_MULTI = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20
 STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CUDA',
-          -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -7: 'LBM_ERR_STATE'}
+          -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -6: 'LBM_ERR_TIMEOUT', -7: 'LBM_ERR_STATE'}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
            'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
            'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore', 'lbm_sample_density',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
-           'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error',
+           'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_launch_count',
+           'lbm_last_error',
            'lbm_destroy')
 
 c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -99,6 +100,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_profile_read.argtypes = [c_void_p, dp, P(ctypes.c_longlong)]
     lib.lbm_map_spheres_noalloc.argtypes = [P(LbmGrid), c_double, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p]
+    lib.lbm_fp64_fma_rate.argtypes = [c_int, dp]
     lib.lbm_launch_count.argtypes = [c_void_p]
     lib.lbm_launch_count.restype = ctypes.c_longlong
     lib.lbm_last_error.argtypes = [c_void_p]
@@ -353,6 +355,13 @@ def lbm_map_spheres_noalloc(grid, shell_width, pos, radius, flags, owner):
                                                       c_void_p(pos.data_ptr()), c_void_p(radius.data_ptr()),
                                                       c_void_p(flags.data_ptr()), c_void_p(owner.data_ptr()),
                                                       c_void_p(stream)))
+
+
+def lbm_fp64_fma_rate(iters=4096):
+    """Measured float64 FMA throughput of the current device in TFLOP/s."""
+    out = c_double(0.0)
+    _check(load_library().lbm_fp64_fma_rate(int(iters), ctypes.byref(out)))
+    return out.value
 
 
 def lbm_launch_count(ctx):

@@ -153,7 +153,12 @@ def test_calls_on_a_null_context_fail_cleanly(lib):
     for name in lbmdem.EXPORTS:
         assert name in calls or name in (
             'lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
-            'lbm_map_spheres_noalloc', 'lbm_launch_count', 'lbm_last_error', 'lbm_destroy'), name
+            'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_launch_count', 'lbm_last_error',
+            'lbm_destroy'), name
+    # the float64 throughput probe checks its arguments before any CUDA call
+    out = ctypes.c_double(0.0)
+    assert lib.lbm_fp64_fma_rate(0, ctypes.byref(out)) == -1
+    assert lib.lbm_fp64_fma_rate(10, None) == -1
 
 
 def test_create_in_arena_and_mapping_entry_reject_bad_arguments(lib):

@@ -58,7 +58,7 @@ def test_whole_job_value_counts_every_rank():
 def test_recorded_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
     csrc = tmp_path / 'paper_2003_01490_gb300' / 'csrc'
     csrc.mkdir(parents=True)
-    for f in ('stream_collide.cu', 'links.cuh', 'common.cuh'):
+    for f in ('stream_collide.cu', 'stream_collide_staged.cu', 'sc_common.cuh', 'links.cuh', 'common.cuh'):
         (csrc / f).write_text('// ' + f + '\n')
     (tmp_path / 'profiles').mkdir()
     monkeypatch.setattr(bench, 'ROOT', str(tmp_path))

@@ -61,3 +61,14 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
 
     bench.run_reference(Args(), rank=1, world=2)
     assert capsys.readouterr().out == ''
+
+
+def test_bench_refuses_a_rank_count_other_than_gpus():
+    # launched with WORLD_SIZE ranks that differ from --gpus: exit non-zero
+    # before any work instead of silently timing fewer replicas
+    import subprocess
+    env = dict(os.environ, WORLD_SIZE='1', RANK='0', LOCAL_RANK='0')
+    r = subprocess.run([sys.executable, os.path.join(ROOT, 'bench.py'), '--gpus', '2', '--steps', '1'],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode != 0
+    assert '--gpus 2 but WORLD_SIZE=1' in r.stderr
