@@ -24,6 +24,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# many concurrent streams (batched and served forms): let CUDA map them onto
+# its 32 hardware work queues instead of the default 8 (read at CUDA start)
+os.environ.setdefault('CUDA_DEVICE_MAX_CONNECTIONS', '32')
 
 L2_BYTES = 129e6
 FALLBACK_HBM_GBS = 6800.0
@@ -551,26 +554,28 @@ def run_reference(args, rank, world):
 
 
 def measure_batched(n_inst, steps_divisor, storage, rank, world, local):
-    """Many small independent boxes: every instance has its own context and
-    CUDA stream, and all of them advance concurrently (steady-state steps are
-    graph launches). Returns the aggregate MLUPS over all instances and the
-    same work run one instance at a time (the plain per-job loop)."""
+    """Many small independent boxes. The batched form: all instances in one
+    batch (lbm_batch_*), one CUDA graph per step with the dense kernels of all
+    active instances in one persistent launch, its launch shape picked by the
+    autotuner (tune.py); every instance runs its own step count (a finished
+    instance drops out of the batch). Beside it the plain per-job loop: the
+    same instances one at a time, lbm_step() per job. Both timed regions cover
+    every step of every instance (the first step of each instance runs on its
+    own in both)."""
     import torch
     from paper_2003_01490_gb300 import lbmdem as L
-    from paper_2003_01490_gb300 import workloads
+    from paper_2003_01490_gb300 import tune, workloads
     inst = workloads.batched(n=n_inst, seed=20030149 + 1000 * rank, storage=storage,
                              steps_divisor=steps_divisor)
     work = sum(w['shape'][0] * w['shape'][1] * w['shape'][2] * w['steps'] for w in inst)
+    cells = [w['shape'][0] * w['shape'][1] * w['shape'][2] for w in inst]
 
     def build():
         ctxs = []
         for w in inst:
-            st = torch.cuda.Stream()
-            with torch.cuda.stream(st):
-                ctx = make_context(w)
-                add_spheres(ctx, w)
-                L.lbm_step(ctx, 3)   # warm-up: first step and the graph captures
-            ctxs.append((ctx, st))
+            ctx = make_context(w)
+            add_spheres(ctx, w)
+            ctxs.append(ctx)
         torch.cuda.synchronize()
         return ctxs
 
@@ -579,47 +584,78 @@ def measure_batched(n_inst, steps_divisor, storage, rank, world, local):
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for (ctx, st), w in zip(ctxs, inst):
-        with torch.cuda.stream(st):
-            L.lbm_step(ctx, w['steps'])
-        st.synchronize()
+    for ctx, w in zip(ctxs, inst):
+        L.lbm_step(ctx, w['steps'])
+    torch.cuda.synchronize()
     t_seq = allreduce_max(time.perf_counter() - t0, world)
+    for ctx in ctxs:
+        L.lbm_sync(ctx)
     del ctxs
     torch.cuda.synchronize()
-    # all instances concurrently, queued in rounds of `chunk` steps
+    # autotune the number of concurrent batches and their launch shape on
+    # instances of the same shapes
     ctxs = build()
-    launches0 = sum(L.lbm_launch_count(c) for c, _ in ctxs)
-    left = [w['steps'] for w in inst]
-    chunk = 25
+    for ctx in ctxs:
+        L.lbm_step(ctx, 1)
+    best = tune.tune_batched(ctxs, storage)
+    del ctxs
+    torch.cuda.synchronize()
+    # the batched form
+    ctxs = build()
+    launches0 = sum(L.lbm_launch_count(c) for c in ctxs)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    while any(left):
-        for k, (ctx, st) in enumerate(ctxs):
-            if left[k]:
-                n = min(chunk, left[k])
-                with torch.cuda.stream(st):
-                    L.lbm_step(ctx, n)
-                left[k] -= n
+    for ctx in ctxs:
+        L.lbm_step(ctx, 1)
+    G = best['groups']
+    groups = tune.make_groups(ctxs, G)
+    segments = 0
+    for g, (b, _) in enumerate(groups):
+        L.lbm_batch_set_launch(b, -1, best['tile_bx'], best['zchunk'], best['blocks_per_sm'])
+        # every batch runs its own instances' step counts; a finished instance
+        # leaves its batch (all queued without waiting)
+        left = [w['steps'] - 1 for w in inst[g::G]]
+        for i, l in enumerate(left):
+            if l == 0:
+                L.lbm_batch_set_active(b, i, 0)
+        while any(left):
+            n = min(l for l in left if l > 0)
+            L.lbm_batch_step(b, n)
+            segments += 1
+            for i in range(len(left)):
+                if left[i] > 0:
+                    left[i] -= n
+                    if left[i] == 0:
+                        L.lbm_batch_set_active(b, i, 0)
     torch.cuda.synchronize()
     t_bat = allreduce_max(time.perf_counter() - t0, world)
     clk = clocks.stop()
-    for ctx, _ in ctxs:
-        L.lbm_sync(ctx)
-    launches = sum(L.lbm_launch_count(c) for c, _ in ctxs) - launches0
-    del ctxs
+    launches = sum(L.lbm_launch_count(c) for c in ctxs) - launches0
+    n_capt, capt_ms = 0, 0.0
+    for b, _ in groups:
+        L.lbm_batch_sync(b)
+        launches += L.lbm_batch_launch_count(b)
+        c_, m_ = L.lbm_batch_capture_stats(b)
+        n_capt += c_
+        capt_ms += m_
+    del groups, ctxs
     torch.cuda.synchronize()
-    cells = [w['shape'][0] * w['shape'][1] * w['shape'][2] for w in inst]
     return {
         'value': round(world * work / t_bat / 1e6, 1), 'unit': 'MLUPS',
         'workload': 'batched: %d sphere-wall boxes, sides 32-96 (s x s x 2s), %d-%d cells, steps 2000-10000 / %d, %s'
                     % (len(inst), min(cells), max(cells), steps_divisor, storage),
-        'cell_updates': int(work), 'steps': sum(w['steps'] for w in inst), 'streams': len(inst),
+        'cell_updates': int(work), 'steps': sum(w['steps'] for w in inst), 'instances': len(inst),
+        'form': '%d concurrent batches (one stream each); per batch and step one CUDA graph with the dense '
+                'kernels of its active instances in one persistent launch and their DEM steps in one launch; '
+                '%d segments (an instance leaves its batch when its steps are done)' % (G, segments),
+        'launch_shape': {k: best[k] for k in ('groups', 'tile_bx', 'zchunk', 'blocks_per_sm', 'source')},
+        'graph_captures': {'count': n_capt, 'host_ms': round(capt_ms, 1)},
         'l2': 'working set %.1f GB of PDFs > 129 MB L2' % (sum(cells) * 2 * 19 * 4 / 1e9),
         'sequential': {'value': round(world * work / t_seq / 1e6, 1), 'unit': 'MLUPS',
-                       'kind': 'the same instances one at a time (plain per-job loop)'},
+                       'kind': 'the same instances one at a time (plain per-job loop, lbm_step per job)'},
         'wall_s': {'batched': round(t_bat, 3), 'sequential': round(t_seq, 3)},
         'clocks': clk, 'gpu_launches': int(launches)}
 
@@ -632,8 +668,9 @@ def run_batched(args, rank, world, local):
         'steps': r['steps'], 'warmup': 3, 'ms_per_step': None,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': storage, 'data': 'synthetic',
-        'config': {'workload': r['workload'], 'cell_updates': r['cell_updates'], 'streams': r['streams'],
-                   'l2': r['l2'], 'parallelism': 'replicas' if world > 1 else 'single GPU'},
+        'config': {'workload': r['workload'], 'cell_updates': r['cell_updates'], 'instances': r['instances'],
+                   'form': r['form'], 'launch_shape': r['launch_shape'], 'l2': r['l2'],
+                   'parallelism': 'replicas' if world > 1 else 'single GPU'},
         'sequential': r['sequential'], 'wall_s': r['wall_s'], 'clocks': r['clocks'],
         'gpu_launches': r['gpu_launches'],
     }

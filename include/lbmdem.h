@@ -294,6 +294,69 @@ lbm_status lbm_map_spheres_noalloc(const lbm_grid *grid, double shell_width, int
  * message is returned by lbm_last_error(NULL). */
 lbm_status lbm_fp64_fma_rate(int iters, double *tflops_out);
 
+/* ------------------------------------------------------------------ batches
+ * A batch advances many independent contexts (instances: boxes of any size,
+ * their own relaxation and particle parameters) in lock step, one CUDA graph
+ * per step: each instance's boundary, finalisation and mapping kernels stay
+ * per instance (on parallel branches of the graph); the DEM steps of all
+ * instances with at most 32 particles run as one launch (a block each), and the
+ * dense kernels of all active instances run as ONE persistent launch over a
+ * table of work items (instance, tile, chunk of z planes), whose tile width and
+ * chunk depth are set per instance (lbm_batch_set_launch; tune.py picks them
+ * by timing). Every instance computes exactly what lbm_step() computes for it
+ * alone (same arithmetic per cell; the per-particle sums of the 4- and 2-byte
+ * formats are exact integer sums, so the results are bit-identical with the
+ * same tile and chunk). The method of the paper has no batches; this is the
+ * library's way of running many of its simulations at once (Algorithm 1 per
+ * instance and step).
+ *
+ * lbm_batch_create(ctxs, n, cuda_stream, out): n >= 1 distinct contexts of
+ *   one storage format. The batch queues its graph launches on cuda_stream (a
+ *   cudaStream_t; NULL = the first context's stream); when that differs from a
+ *   context's stream, each lbm_batch_step() call is ordered after the work
+ *   already queued on the contexts' streams and before work queued on them
+ *   later (events), so several batches over disjoint contexts can run
+ *   concurrently on their own streams. The batch borrows the contexts:
+ *   destroy the batch before them.
+ *   Errors: LBM_ERR_INVALID, LBM_ERR_CUDA (message by lbm_batch_last_error(NULL)).
+ * lbm_batch_set_launch(b, instance, tile_bx, zchunk, blocks_per_sm): launch
+ *   shape of the batched dense kernel for one instance (instance = -1: all):
+ *   tile width tile_bx in x (0 automatic: the narrowest of 32, 64, 128 that
+ *   covers the box width, else 32, 64 or 128; 256 / tile_bx rows),
+ *   zchunk z planes per work item (0 automatic = 16), and blocks_per_sm
+ *   resident blocks per multiprocessor for the whole launch (0 automatic:
+ *   4, 2 for float64). Synchronises the stream and drops the captured graphs.
+ * lbm_batch_set_active(b, instance, active): whether the instance takes part
+ *   in the following lbm_batch_step() calls (finished instances are
+ *   deactivated; an inactive instance's state is not touched).
+ * lbm_batch_step(b, n_steps): queue n_steps steps of every active instance on
+ *   the stream (asynchronous). Each active instance must have stepped at least
+ *   once with lbm_step() (the first step sets up the DEM state), must not have
+ *   a pending motion switch and must not be under phase timing
+ *   (LBM_ERR_STATE). A graph is captured the first time each combination of
+ *   active set, launch shape and buffer parities occurs and replayed after.
+ * lbm_batch_sync(b): wait for the stream; returns the first device error of
+ *   an instance (as lbm_sync()).
+ * lbm_batch_launch_count(b): launches of the batched kernels so far (the
+ *   persistent dense kernel and the one launch per step that runs the DEM of
+ *   every instance with at most 32 particles; the other kernels are counted by
+ *   each instance's lbm_launch_count()).
+ * lbm_batch_capture_stats(b, captures, capture_ms): graphs captured so far and
+ *   the host time spent capturing and instantiating them (either pointer may
+ *   be NULL).
+ * lbm_batch_destroy(b): releases the batch (not its contexts). NULL is a no-op.
+ */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *cuda_stream, lbm_batch **out);
+lbm_status lbm_batch_set_launch(lbm_batch *b, int instance, int tile_bx, int zchunk, int blocks_per_sm);
+lbm_status lbm_batch_set_active(lbm_batch *b, int instance, int active);
+lbm_status lbm_batch_step(lbm_batch *b, int n_steps);
+lbm_status lbm_batch_sync(lbm_batch *b);
+long long lbm_batch_launch_count(const lbm_batch *b);
+lbm_status lbm_batch_capture_stats(const lbm_batch *b, int *captures, double *capture_ms);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Number of kernel launches this context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);
 

@@ -2,6 +2,8 @@
 // management, device memory layout, particle insertion and the per-step
 // launch sequence of Algorithm 1 (Sec. 4.2).
 #include <algorithm>
+#include <chrono>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -765,9 +767,29 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
     return check_status(ctx);
 }
 
-// One time step of Algorithm 1 queued on stream sm; updates the host-side
-// state (buffer parities, launch count) as the launches are queued.
-lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
+// One time step of Algorithm 1 queued on stream sm, in two parts around the
+// dense kernel: enqueue_pre queues everything before it (the fluid body force;
+// on the side stream the missing links and the DEM neighbour lists) and fills
+// the dense kernel's parameters; enqueue_post queues everything after it (the
+// force finalisation, the DEM, the mapping and the refill) and updates the
+// host-side state (buffer parities, launch count). A batch queues the dense
+// kernels of all its instances as one launch between the two parts.
+struct StepState {
+    LbmStepParams lp{};
+    bool side = false;
+    bool first = false;
+    bool move = false;
+    bool dem = false;
+    // a batch runs the one-block DEM steps of all its instances as one launch:
+    // enqueue_post then leaves this instance's to the batch (defer_dem) and
+    // records what the launch needs
+    bool defer_dem = false;
+    bool dem_deferred = false;
+    DemParams dem_p{};
+    int dem_hcur = 0, dem_nsub = 0;
+};
+
+lbm_status enqueue_pre(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& ss) {
     const lbm_relax& r = ctx->relax;
     const lbm_dem& d = ctx->dem;
     const double s_nu = 1.0 / r.tau;
@@ -779,6 +801,9 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     const bool init_dem = dem && (first || ctx->dem_restart);
     ctx->dem_restart = false;
     if (first) ctx->stepped = true;
+    ss.first = first;
+    ss.move = move;
+    ss.dem = dem;
     if (init_dem) {
         // the force of the first Velocity-Verlet position update at the current
         // state (F(t = 0) on the first step, where the averaged fluid force is
@@ -794,7 +819,8 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     }
     // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
     CK(prof_mark(ctx));
-    LbmStepParams lp{};
+    LbmStepParams& lp = ss.lp;
+    lp = LbmStepParams{};
     lp.storage = ctx->storage;
     lp.src = ctx->f[ctx->cur];
     lp.dst = ctx->f[1 - ctx->cur];
@@ -827,6 +853,7 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     // which read only the positions the dense kernel reads too; finalize
     // waits for both streams
     const bool side = lp.missing_links || dem;
+    ss.side = side;
     if (side) {
         CK(cudaEventRecord(ctx->ev_fork, sm));
         CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
@@ -845,7 +872,24 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
         CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
     }
     CK(prof_mark(ctx));
-    launch_stream_collide(lp, sm);
+    return LBM_OK;
+}
+
+lbm_status enqueue_post_a(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& ss);
+lbm_status enqueue_post_b(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, const StepState& ss);
+
+lbm_status enqueue_post(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& ss) {
+    lbm_status st = enqueue_post_a(ctx, dp, sm, ss);
+    return st != LBM_OK ? st : enqueue_post_b(ctx, dp, sm, ss);
+}
+
+// after the dense kernel: force finalisation and the DEM (Algorithm 1,
+// lines 4-10)
+lbm_status enqueue_post_a(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& ss) {
+    const lbm_relax& r = ctx->relax;
+    const lbm_dem& d = ctx->dem;
+    const double s_nu = 1.0 / r.tau;
+    const bool first = ss.first, move = ss.move, dem = ss.dem, side = ss.side;
     CK(prof_mark(ctx));
     if (side) CK(cudaStreamWaitEvent(sm, ctx->ev_join, 0));
     FinalizeParams fpp{};
@@ -859,9 +903,16 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     if (move) {
         if (dem && ctx->P.n <= DEM_ONE_BLOCK_MAX) {
             // Algorithm 1, lines 4-10, in one block: few particles
-            launch_dem_step_one_block(dp, ctx->hcur, d.n_sub, sm);
+            if (ss.defer_dem) {
+                ss.dem_deferred = true;
+                ss.dem_p = dp;
+                ss.dem_hcur = ctx->hcur;
+                ss.dem_nsub = d.n_sub;
+            } else {
+                launch_dem_step_one_block(dp, ctx->hcur, d.n_sub, sm);
+                ctx->launches += 1;
+            }
             if (d.n_sub & 1) ctx->hcur = 1 - ctx->hcur;
-            ctx->launches += 1;
         } else if (dem) {
             // Algorithm 1, lines 4-10: DEM subcycles
             launch_dem_position(dp, sm);
@@ -884,6 +935,16 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
             launch_prescribed_move(ctx->P, ctx->g, sm);
             ctx->launches += 1;
         }
+    }
+    return LBM_OK;
+}
+
+// the mapping update and refill (Algorithm 1, line 11) and the host-side
+// step state
+lbm_status enqueue_post_b(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, const StepState& ss) {
+    (void)dp;
+    const double s_nu = 1.0 / ctx->relax.tau;
+    if (ss.move) {
         CK(prof_mark(ctx));
         // Algorithm 1, line 11: mapping update and refill
         lbm_status st = remap(ctx, sm);
@@ -912,6 +973,14 @@ lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
     if (ctx->profiling) ctx->prof_steps += 1;
     ctx->cur = 1 - ctx->cur;
     return LBM_OK;
+}
+
+lbm_status enqueue_step(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm) {
+    StepState ss;
+    lbm_status st = enqueue_pre(ctx, dp, sm, ss);
+    if (st != LBM_OK) return st;
+    launch_stream_collide(ss.lp, sm);
+    return enqueue_post(ctx, dp, sm, ss);
 }
 
 // Steady-state steps (after the first, profiling off) run as CUDA graphs: the
@@ -1296,6 +1365,375 @@ void lbm_destroy(lbm_ctx* ctx) {
     destroy_handles(ctx);
     if (ctx->own_memory && ctx->base) cudaFree(ctx->base);
     delete ctx;
+}
+
+// ====================================================================== batches
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    std::vector<int> active;
+    std::vector<int> tile_bx, zchunk;   // per instance, 0: automatic
+    int blocks_per_sm = 0;              // 0: automatic
+    int storage = 1;
+    int num_sms = 152;
+    int config_version = 0;
+    cudaStream_t stream = nullptr;      // the stream the batch's steps run on
+    std::vector<cudaStream_t> ctx_streams;   // the distinct streams of the contexts
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t capture = nullptr;     // private stream the steps are captured on
+    std::vector<cudaStream_t> inst;     // one capture stream per instance
+    std::vector<cudaEvent_t> ev_pre, ev_mid, ev_post;
+    cudaEvent_t ev_fork = nullptr, ev_dense = nullptr, ev_dem = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        void* d_args = nullptr;
+        int4* d_items = nullptr;
+        void* d_dem = nullptr;             // one-block DEM steps of the instances, one entry each
+        int n_items = 0;
+        int n_dem = 0;
+        std::vector<long long> launches;   // kernel launches per instance in one step
+        std::vector<int> hcur_after;       // history parity per instance after the step
+    };
+    // one captured step per (configuration, per instance: inactive, or buffer and history parities)
+    std::map<std::vector<int>, Graph> graphs;
+    long long launches = 0;             // launches of the batched dense kernel
+    int captures = 0;                   // graphs captured so far
+    double capture_ms = 0.0;            // host time spent capturing and instantiating them
+    std::string err;
+};
+
+namespace {
+
+lbm_status batch_fail(lbm_batch* b, lbm_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    set_global_error(msg);
+    return s;
+}
+
+#define BCK(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return batch_fail(b, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void batch_clear_graphs(lbm_batch* b) {
+    for (auto& kv : b->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.d_args) cudaFree(kv.second.d_args);
+        if (kv.second.d_items) cudaFree(kv.second.d_items);
+        if (kv.second.d_dem) cudaFree(kv.second.d_dem);
+    }
+    b->graphs.clear();
+}
+
+int batch_zchunk(const lbm_batch* b, int i) {
+    const int z = b->zchunk[i];
+    return z > 0 ? z : 16;
+}
+// the batched kernel's tiles are 32, 64 or 128 cells wide (threads map to
+// cells by masks and shifts): the narrowest that covers the box, at most 128
+int batch_tile_bx(const lbm_batch* b, int i) {
+    const int t = b->tile_bx[i];
+    const int nx = b->ctx[i]->g.n[0];
+    return t > 0 ? t : (nx > 64 ? 128 : (nx > 32 ? 64 : 32));
+}
+
+// work items of the active instances, interleaved across instances so that
+// concurrently running blocks spread over them
+std::vector<int4> batch_items(const lbm_batch* b) {
+    std::vector<std::vector<int4>> per(b->ctx.size());
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        if (!b->active[i]) continue;
+        const Geom& g = b->ctx[i]->g;
+        const int bx = batch_tile_bx(b, (int)i), by = 256 / bx, zc = batch_zchunk(b, (int)i);
+        for (int z0 = 0; z0 < g.n[2]; z0 += zc)
+            for (int y0 = 0; y0 < g.n[1]; y0 += by)
+                for (int x0 = 0; x0 < g.n[0]; x0 += bx) per[i].push_back(make_int4((int)i, x0, y0, z0));
+    }
+    std::vector<int4> out;
+    for (size_t k = 0;; ++k) {
+        bool any = false;
+        for (auto& v : per)
+            if (k < v.size()) {
+                out.push_back(v[k]);
+                any = true;
+            }
+        if (!any) break;
+    }
+    return out;
+}
+
+// capture one step of every active instance: per instance its work before
+// the dense kernel on its own stream, then one persistent dense launch over
+// all of them, per instance the force finalisation, one launch of the
+// one-block DEM steps of all instances with few particles, and per instance
+// the mapping and refill
+lbm_status batch_capture(lbm_batch* b, lbm_batch::Graph& G) {
+    const size_t n = b->ctx.size();
+    const size_t ab = batch_args_bytes(b->storage);
+    const size_t db = dem_batch_entry_bytes();
+    const std::vector<int4> items = batch_items(b);
+    G.n_items = (int)items.size();
+    BCK(cudaMalloc(&G.d_args, ab * n));
+    BCK(cudaMalloc(&G.d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
+    BCK(cudaMalloc(&G.d_dem, db * n));
+    std::vector<unsigned char> host(ab * n, 0), host_dem(db * n, 0);
+    std::vector<StepState> ss(n);
+    std::vector<DemParams> dp(n);
+    std::vector<long long> l0(n);
+    std::vector<int> cur0(n), h0(n);
+    for (size_t i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        l0[i] = c->launches;
+        cur0[i] = c->cur;
+        h0[i] = c->hcur;
+        dp[i] = dem_params(c);
+    }
+    cudaGraph_t g = nullptr;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->capture);
+    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
+        if (!b->active[i]) continue;
+        e = cudaStreamWaitEvent(b->inst[i], b->ev_fork, 0);
+        if (e == cudaSuccess) st = enqueue_pre(b->ctx[i], dp[i], b->inst[i], ss[i]);
+        if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_pre[i], b->inst[i]);
+        if (e == cudaSuccess && st == LBM_OK) e = cudaStreamWaitEvent(b->capture, b->ev_pre[i], 0);
+        if (st == LBM_OK) fill_batch_args(ss[i].lp, batch_tile_bx(b, (int)i), batch_zchunk(b, (int)i), &host[ab * i]);
+    }
+    if (e == cudaSuccess && st == LBM_OK && G.n_items > 0) {
+        const int bps = b->blocks_per_sm > 0 ? b->blocks_per_sm : (b->storage == 0 ? 2 : 4);
+        const int grid = std::min(G.n_items, bps * b->num_sms);
+        launch_stream_collide_batch(b->storage, G.d_args, G.d_items, G.n_items, grid, b->capture);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_dense, b->capture);
+    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
+        if (!b->active[i]) continue;
+        e = cudaStreamWaitEvent(b->inst[i], b->ev_dense, 0);
+        ss[i].defer_dem = true;
+        if (e == cudaSuccess) st = enqueue_post_a(b->ctx[i], dp[i], b->inst[i], ss[i]);
+        if (e == cudaSuccess && st == LBM_OK && ss[i].dem_deferred) {
+            fill_dem_batch_entry(ss[i].dem_p, ss[i].dem_hcur, ss[i].dem_nsub, &host_dem[db * G.n_dem]);
+            G.n_dem += 1;
+            e = cudaEventRecord(b->ev_mid[i], b->inst[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->ev_mid[i], 0);
+        }
+    }
+    if (e == cudaSuccess && st == LBM_OK && G.n_dem > 0) {
+        launch_dem_step_batch(G.d_dem, G.n_dem, b->storage != LBM_STORE_F64, b->capture);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_dem, b->capture);
+    }
+    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
+        if (!b->active[i]) continue;
+        if (ss[i].dem_deferred) e = cudaStreamWaitEvent(b->inst[i], b->ev_dem, 0);
+        if (e == cudaSuccess) st = enqueue_post_b(b->ctx[i], dp[i], b->inst[i], ss[i]);
+        if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_post[i], b->inst[i]);
+        if (e == cudaSuccess && st == LBM_OK) e = cudaStreamWaitEvent(b->capture, b->ev_post[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+    if (e == cudaSuccess) e = e2;
+    // the capture ran nothing: keep the host-side state changes of one step
+    // for the replays and undo them here
+    G.launches.assign(n, 0);
+    G.hcur_after.assign(n, 0);
+    for (size_t i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        G.launches[i] = c->launches - l0[i];
+        G.hcur_after[i] = c->hcur;
+        c->launches = l0[i];
+        c->cur = cur0[i];
+        c->hcur = h0[i];
+    }
+    if (e == cudaSuccess && st == LBM_OK) e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != LBM_OK) return batch_fail(b, st, "a step of an instance could not be queued: " + b->ctx[0]->err);
+    BCK(e);
+    BCK(cudaMemcpy(G.d_args, host.data(), host.size(), cudaMemcpyHostToDevice));
+    if (G.n_items > 0)
+        BCK(cudaMemcpy(G.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    if (G.n_dem > 0) BCK(cudaMemcpy(G.d_dem, host_dem.data(), db * G.n_dem, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* cuda_stream, lbm_batch** out) {
+    lbm_batch* b = nullptr;
+    if (!ctxs || n < 1 || !out) return batch_fail(b, LBM_ERR_INVALID, "lbm_batch_create: ctxs, n >= 1 and out required");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return batch_fail(b, LBM_ERR_INVALID, "lbm_batch_create: NULL context");
+        if (ctxs[i]->storage != ctxs[0]->storage)
+            return batch_fail(b, LBM_ERR_INVALID, "lbm_batch_create: all instances need one storage format");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return batch_fail(b, LBM_ERR_INVALID, "lbm_batch_create: a context appears twice");
+    }
+    b = new lbm_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->active.assign(n, 1);
+    b->tile_bx.assign(n, 0);
+    b->zchunk.assign(n, 0);
+    b->storage = ctxs[0]->storage;
+    b->num_sms = ctxs[0]->num_sms;
+    b->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctxs[0]->stream;
+    for (int i = 0; i < n; ++i)
+        if (std::find(b->ctx_streams.begin(), b->ctx_streams.end(), ctxs[i]->stream) == b->ctx_streams.end())
+            b->ctx_streams.push_back(ctxs[i]->stream);
+    b->inst.assign(n, nullptr);
+    b->ev_pre.assign(n, nullptr);
+    b->ev_mid.assign(n, nullptr);
+    b->ev_post.assign(n, nullptr);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_dense, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_dem, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->inst[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_pre[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_mid[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_post[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        cudaGetLastError();
+        return batch_fail(nullptr, LBM_ERR_CUDA, std::string("lbm_batch_create: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_launch(lbm_batch* b, int instance, int tile_bx, int zchunk, int blocks_per_sm) {
+    if (!b) return batch_fail(b, LBM_ERR_INVALID, "batch is NULL");
+    if (instance < -1 || instance >= (int)b->ctx.size())
+        return batch_fail(b, LBM_ERR_INVALID, "instance out of range (-1 = all)");
+    if (!(tile_bx == 0 || tile_bx == 32 || tile_bx == 64 || tile_bx == 128))
+        return batch_fail(b, LBM_ERR_INVALID, "tile_bx must be 0 (automatic), 32, 64 or 128");
+    if (zchunk < 0 || zchunk > 4096) return batch_fail(b, LBM_ERR_INVALID, "zchunk must be in 0 .. 4096");
+    if (blocks_per_sm < 0 || blocks_per_sm > 8) return batch_fail(b, LBM_ERR_INVALID, "blocks_per_sm must be in 0 .. 8");
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (instance < 0 || (int)i == instance) {
+            b->tile_bx[i] = tile_bx;
+            b->zchunk[i] = zchunk;
+        }
+    b->blocks_per_sm = blocks_per_sm;
+    BCK(cudaStreamSynchronize(b->stream));
+    batch_clear_graphs(b);
+    b->config_version += 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_active(lbm_batch* b, int instance, int active) {
+    if (!b) return batch_fail(b, LBM_ERR_INVALID, "batch is NULL");
+    if (instance < 0 || instance >= (int)b->ctx.size()) return batch_fail(b, LBM_ERR_INVALID, "instance out of range");
+    b->active[instance] = active ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
+    if (!b) return batch_fail(b, LBM_ERR_INVALID, "batch is NULL");
+    if (n_steps < 0) return batch_fail(b, LBM_ERR_INVALID, "n_steps must be >= 0");
+    bool any = false;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        if (!b->active[i]) continue;
+        const lbm_ctx* c = b->ctx[i];
+        if (!c->stepped || c->dem_restart || c->profiling)
+            return batch_fail(b, LBM_ERR_STATE,
+                              "lbm_batch_step: every active instance must have stepped once on its own, "
+                              "without a pending motion switch or phase timing");
+        any = true;
+    }
+    if (!any || n_steps == 0) return LBM_OK;
+    // the steps start after the work queued on the contexts' streams and that
+    // work resumes after them
+    const bool foreign = b->ctx_streams.size() != 1 || b->ctx_streams[0] != b->stream;
+    if (foreign)
+        for (cudaStream_t cs : b->ctx_streams) {
+            BCK(cudaEventRecord(b->ev_in, cs));
+            BCK(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+        }
+    for (int step = 0; step < n_steps; ++step) {
+        std::vector<int> key{b->config_version};
+        for (size_t i = 0; i < b->ctx.size(); ++i)
+            key.push_back(b->active[i] ? 2 * b->ctx[i]->cur + b->ctx[i]->hcur : -1);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            lbm_batch::Graph G;
+            const auto t0 = std::chrono::steady_clock::now();
+            lbm_status st = batch_capture(b, G);
+            b->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            b->captures += 1;
+            if (st != LBM_OK) {
+                if (G.exec) cudaGraphExecDestroy(G.exec);
+                if (G.d_args) cudaFree(G.d_args);
+                if (G.d_items) cudaFree(G.d_items);
+                if (G.d_dem) cudaFree(G.d_dem);
+                return st;
+            }
+            it = b->graphs.emplace(key, G).first;
+        }
+        const lbm_batch::Graph& G = it->second;
+        BCK(cudaGraphLaunch(G.exec, b->stream));
+        b->launches += (G.n_items > 0 ? 1 : 0) + (G.n_dem > 0 ? 1 : 0);
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            if (!b->active[i]) continue;
+            lbm_ctx* c = b->ctx[i];
+            c->launches += G.launches[i];
+            c->hcur = G.hcur_after[i];
+            c->cur = 1 - c->cur;
+        }
+    }
+    if (foreign) {
+        BCK(cudaEventRecord(b->ev_out, b->stream));
+        for (cudaStream_t cs : b->ctx_streams) BCK(cudaStreamWaitEvent(cs, b->ev_out, 0));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    if (!b) return batch_fail(b, LBM_ERR_INVALID, "batch is NULL");
+    BCK(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        lbm_status st = check_status(b->ctx[i]);
+        if (st != LBM_OK) return batch_fail(b, st, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    return LBM_OK;
+}
+
+long long lbm_batch_launch_count(const lbm_batch* b) { return b ? b->launches : 0; }
+
+lbm_status lbm_batch_capture_stats(const lbm_batch* b, int* captures, double* capture_ms) {
+    if (!b) return batch_fail(nullptr, LBM_ERR_INVALID, "batch is NULL");
+    if (captures) *captures = b->captures;
+    if (capture_ms) *capture_ms = b->capture_ms;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_clear_graphs(b);
+    for (auto s : b->inst)
+        if (s) cudaStreamDestroy(s);
+    for (auto ev : b->ev_pre)
+        if (ev) cudaEventDestroy(ev);
+    for (auto ev : b->ev_mid)
+        if (ev) cudaEventDestroy(ev);
+    for (auto ev : b->ev_post)
+        if (ev) cudaEventDestroy(ev);
+    if (b->ev_dem) cudaEventDestroy(b->ev_dem);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_dense) cudaEventDestroy(b->ev_dense);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
 }
 
 }  // extern "C"

@@ -14,6 +14,8 @@
 // particle keeps its own copy of the tangential spring of every active
 // contact (double buffered per subcycle). Up to 32 particles run a whole
 // step's subcycles in one block.
+#include <cstring>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -626,11 +628,11 @@ __device__ void integrate_particle(const DemParams& p, int ip, const T (&sum)[6]
 
 
 template <typename T>
-__device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int hin, int hout, int init, int last) {
+__device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int hin, int hout, int init, int last, int pblock) {
     const Particles& P = p.P;
     const int tid = threadIdx.x;
     const int pl = tid >> 2, sub = tid & 3;   // pass 1: particle of the block, lane of its group
-    const int i = blockIdx.x * PPB + pl;
+    const int i = pblock * PPB + pl;
     __shared__ unsigned short s_queue[PPB * NBR_CAP];   // pl << 5 | slot
     __shared__ int s_off[PPB + 1];
     __shared__ T s_res[PAIR_CHUNK][6];
@@ -696,7 +698,7 @@ __device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int h
         if (e < total) {
             const int q = s_queue[e];
             const int ep = q >> 5, k = q & 31;
-            const int ei = blockIdx.x * PPB + ep;
+            const int ei = pblock * PPB + ep;
             const int j = P.nbr[ei * NBR_CAP + k];
             Vec3<T> F, Tq, dnew;
             bool contact;
@@ -724,7 +726,7 @@ __device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int h
     // work of the block spread over the four schedulers)
     if ((tid & 31) < PPB / 4) {
         const int pl3 = (tid >> 5) * (PPB / 4) + (tid & 31);
-        const int ip = blockIdx.x * PPB + pl3;
+        const int ip = pblock * PPB + pl3;
         if (ip < P.n) {
             T sum[6];
 #pragma unroll
@@ -739,7 +741,7 @@ __device__ __forceinline__ void subcycle_body(const DemParams& p, int cur, int h
 // update (Eq. (38)) and the next position update (Eq. (37))
 template <typename T>
 __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cur, int init, int last) {
-    subcycle_body<T>(p, cur, p.hin, p.hout, init, last);
+    subcycle_body<T>(p, cur, p.hin, p.hout, init, last, blockIdx.x);
 }
 
 // All subcycles of a step in one block when the particles fit in it (at most
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(128) dem_step_one_block_kernel(const DemParams
     __syncthreads();
     int cur = 0;
     for (int s = 0; s < n_sub; ++s) {
-        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == n_sub - 1);
+        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == n_sub - 1, 0);
         __syncthreads();
         hcur = 1 - hcur;
         cur = 1 - cur;
@@ -770,6 +772,66 @@ __global__ void __launch_bounds__(128) dem_step_one_block_kernel(const DemParams
             P.omfs[0][k] = P.omfs[1][k];
         }
     }
+}
+
+// The one-block DEM steps of many instances in one launch: block b runs the
+// step of entry b of the table (its parameters, history parity and subcycle
+// count), exactly as dem_step_one_block_kernel does for one instance.
+struct DemBatchEntry {
+    DemParams p;
+    int hcur, n_sub;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) dem_step_batch_kernel(const DemBatchEntry* __restrict__ table) {
+    __shared__ __align__(16) DemBatchEntry e;
+    constexpr int WORDS = (int)(sizeof(DemBatchEntry) / 4);
+    static_assert(sizeof(DemBatchEntry) % 4 == 0, "entry copied in words");
+    const int* src = reinterpret_cast<const int*>(table + blockIdx.x);
+    int* dst = reinterpret_cast<int*>(&e);
+    for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    const DemParams& p = e.p;
+    const int tid = threadIdx.x;
+    int hcur = e.hcur;
+    if (tid < p.P.n) position_update(p, tid);
+    __syncthreads();
+    int cur = 0;
+    for (int s = 0; s < e.n_sub; ++s) {
+        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == e.n_sub - 1, 0);
+        __syncthreads();
+        hcur = 1 - hcur;
+        cur = 1 - cur;
+    }
+    if (cur == 1) {
+        const Particles& P = p.P;
+        for (int k = tid; k < 3 * P.n; k += blockDim.x) {
+            P.xs[0][k] = P.xs[1][k];
+            P.us[0][k] = P.us[1][k];
+            P.oms[0][k] = P.oms[1][k];
+            P.xfs[0][k] = P.xfs[1][k];
+            P.ufs[0][k] = P.ufs[1][k];
+            P.omfs[0][k] = P.omfs[1][k];
+        }
+    }
+}
+
+size_t dem_batch_entry_bytes() { return sizeof(DemBatchEntry); }
+
+void fill_dem_batch_entry(const DemParams& p, int hcur, int n_sub, void* out) {
+    DemBatchEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.p = p;
+    e.hcur = hcur;
+    e.n_sub = n_sub;
+    std::memcpy(out, &e, sizeof(e));
+}
+
+void launch_dem_step_batch(const void* d_table, int count, int pair_f32, cudaStream_t st) {
+    if (count <= 0) return;
+    const DemBatchEntry* t = static_cast<const DemBatchEntry*>(d_table);
+    if (pair_f32) dem_step_batch_kernel<float><<<count, 128, 0, st>>>(t);
+    else dem_step_batch_kernel<double><<<count, 128, 0, st>>>(t);
 }
 
 void launch_dem_step_one_block(const DemParams& p, int hcur, int n_sub, cudaStream_t st) {

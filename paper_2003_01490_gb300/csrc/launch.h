@@ -30,6 +30,8 @@ struct LbmStepParams {
     double* accel_d;                 // out: fluid body force of the step [3]
     float* accel_f;
     int use_staged;                  // 1: the dense kernel with bulk-copy staging where it applies
+    int tile_bx;                     // x extent of the dense kernel's tile (0: automatic)
+    int zchunk;                      // z planes per block of the dense kernel (0: automatic)
     int staged_zchunk;               // z planes per work item of the staged kernel (0: automatic)
 };
 // BC_ACCEL: the fluid body force of the step; BC_LINKS: the missing links
@@ -38,6 +40,14 @@ void launch_boundary(const LbmStepParams& p, cudaStream_t st, int mode);
 void launch_stream_collide(const LbmStepParams& p, cudaStream_t st);
 // kernel attributes on the current device (before any launch or capture)
 cudaError_t prepare_stream_collide(int storage);
+// the dense kernels of many boxes in one persistent launch: per instance one
+// argument block (batch_args_bytes(storage) bytes, filled by fill_batch_args)
+// in device memory, and a table of work items (instance, x0, y0, z0)
+size_t batch_args_bytes(int storage);
+void fill_batch_args(const LbmStepParams& p, int tile_bx, int zchunk, void* out);
+int default_tile_bx(int nx);
+void launch_stream_collide_batch(int storage, const void* d_args, const int4* d_items, int n_items, int grid,
+                                 cudaStream_t st);
 // the dense kernel with bulk-copy staging of the pulls (4- and 2-byte formats)
 bool staged_applicable(const LbmStepParams& p);
 void launch_stream_collide_staged(const LbmStepParams& p, cudaStream_t st);
@@ -146,6 +156,10 @@ struct DemParams {
     DemConsts<float> kf;
     int* status;
 };
+// the one-block DEM steps of many instances in one launch (batches)
+size_t dem_batch_entry_bytes();
+void fill_dem_batch_entry(const DemParams& p, int hcur, int n_sub, void* out);
+void launch_dem_step_batch(const void* d_table, int count, int pair_f32, cudaStream_t st);
 void launch_bins(const DemParams& p, cudaStream_t st);
 void launch_neighbours(const DemParams& p, cudaStream_t st);
 void launch_dem_position(const DemParams& p, cudaStream_t st);

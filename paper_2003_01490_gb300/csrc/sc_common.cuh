@@ -23,6 +23,7 @@ struct SCArgs {
     const T* __restrict__ accel;     // [3]
     int* status;
     int zchunk;                      // z planes per block
+    int bx;                          // x extent of a block's tile (a multiple of 32; 256 / bx rows)
     // particles (for the links)
     int np;
     const int* __restrict__ owner;   // particle of a solid cell, -1 for fluid
@@ -54,6 +55,7 @@ void fill_sc_args(const LbmStepParams& p, SCArgs<S, T>& a) {
     a.accel = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)p.accel_d : (const void*)p.accel_f);
     a.status = p.status;
     a.zchunk = 0;
+    a.bx = 128;
     a.np = p.P.n;
     a.owner = p.owner;
     a.px = p.P.x;

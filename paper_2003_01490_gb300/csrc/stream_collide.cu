@@ -30,6 +30,8 @@
 // in integers; the remainder is summed per warp in float32 and per particle
 // in 64-bit fixed point (scale 2^32) through integer atomics. No float64
 // arithmetic runs per cell or link on the float32 path.
+#include <cstring>
+
 #include "sc_common.cuh"
 
 // minimum resident blocks per SM requested for the kernel with 4-byte or
@@ -85,28 +87,35 @@ __device__ __forceinline__ void store_sums(Acc<T>& acc, int* s_key, T (*s_sum)[2
     for (int c = 0; c < 6; ++c) s_sum[c][tid] = acc.f[c];
 }
 
-// One block per (x, y) tile of 256 cells and a chunk of zchunk (<= LBM_SC_ZCHUNK)
-// consecutive z planes, marched in order: the links a warp meets in
-// consecutive rows mostly belong to the same spheres, so a lane's force sums
-// (kept in shared memory between rows) rarely change particle and the warp
-// commits them once per chunk. Cell indices are 32-bit (the library limits
-// boxes to 2^31 - 2^24 cells); each PDF array q starts at src + q N.
-template <typename S, typename T>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : LBM_SC_MIN_BLOCKS) stream_collide_kernel(const SCArgs<S, T> a) {
+// One tile of bx x (256 / bx) cells in (x, y) from (x0, y0), planes z_begin
+// .. z_end - 1 marched in order: the links a warp meets in consecutive rows
+// mostly belong to the same spheres, so a lane's force sums (kept in shared
+// memory between rows) rarely change particle and the warp commits them once
+// per tile. Thread tid of the block's 256 handles column x0 + tid % bx, row
+// y0 + tid / bx (warps hold 32 consecutive tids). Cell indices are 32-bit
+// (the library limits boxes to 2^31 - 2^24 cells); each PDF array q starts at
+// src + q N. s_qi holds the link codes qinfo(q).
+// A single-box launch has blocks of (bx, 256 / bx) threads and takes its tile
+// from the block index (BATCH false: x0, y0 unused); the batched launch has
+// blocks of 256 threads and passes the tile.
+template <typename S, typename T, bool BATCH>
+__device__ __forceinline__ void sc_tile(const SCArgs<S, T>& a, int x0, int y0, int z_begin, int z_end, int bx,
+                                        unsigned char* sc_smem, const int* s_qi) {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    // bx is 32, 64 or 128
+    const int tid = BATCH ? (int)threadIdx.x : (int)(threadIdx.x + blockDim.x * threadIdx.y);
+    const int x = BATCH ? x0 + (tid & (bx - 1)) : (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = BATCH ? y0 + (tid >> (bx == 128 ? 7 : (bx == 64 ? 6 : 5)))
+                        : (int)(blockIdx.y * blockDim.y + threadIdx.y);
     const bool valid = x < nx && y < ny;
     const int plane = nx * ny;
     const long long N = a.g.ncells;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;   // warps hold 32 consecutive tids
     // dynamic shared memory (sc_smem_bytes): PDFs of the cells of warps with
     // links [q][thread]; per lane the particle of its open force sums (-1:
     // none), the open float sums (F, T) and the exact integer sums (float32
     // path, two 16-bit halves per word); per warp the link entries q | lane << 8
-    extern __shared__ __align__(16) unsigned char sc_smem[];
     T (*s_f)[256] = reinterpret_cast<T (*)[256]>(sc_smem);
     T (*s_sum)[256] = reinterpret_cast<T (*)[256]>(sc_smem + Q * 256 * sizeof(T));
     int (*s_int)[256] = reinterpret_cast<int (*)[256]>(sc_smem + (Q + 6) * 256 * sizeof(T));
@@ -114,14 +123,6 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     unsigned short (*s_queue)[32 * (Q - 1)] =
         reinterpret_cast<unsigned short (*)[32 * (Q - 1)]>(reinterpret_cast<unsigned char*>(s_key) + 256 * 4);
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
-    __shared__ int s_qi[Q];
-    if (tid < Q) {
-        constexpr int QI[Q] = {qinfo(0), qinfo(1), qinfo(2), qinfo(3), qinfo(4), qinfo(5), qinfo(6),
-                               qinfo(7), qinfo(8), qinfo(9), qinfo(10), qinfo(11), qinfo(12), qinfo(13),
-                               qinfo(14), qinfo(15), qinfo(16), qinfo(17), qinfo(18)};
-        s_qi[tid] = QI[tid];
-    }
-    __syncthreads();
     s_key[tid] = -1;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -130,8 +131,6 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     }
     bool open = false;   // warp-uniform: some lane of the warp holds sums
 
-    const int z_begin = blockIdx.z * a.zchunk;
-    const int z_end = min(nz, z_begin + a.zchunk);
     // the 19 pulls of cell (x, y, zz) with periodic wrap (walls are handled
     // below), issued only for a fluid cell
     auto pull_row = [&](int zz, bool fluid_zz, T (&g)[Q]) {
@@ -241,6 +240,56 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : 
     }
 }
 
+
+// link codes of the directions into shared memory (before the first tile)
+__device__ __forceinline__ void load_qinfo(int* s_qi) {
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    if (t < Q) {
+        constexpr int QI[Q] = {qinfo(0), qinfo(1), qinfo(2), qinfo(3), qinfo(4), qinfo(5), qinfo(6),
+                               qinfo(7), qinfo(8), qinfo(9), qinfo(10), qinfo(11), qinfo(12), qinfo(13),
+                               qinfo(14), qinfo(15), qinfo(16), qinfo(17), qinfo(18)};
+        s_qi[t] = QI[t];
+    }
+}
+
+// One box: block (bx, 256 / bx) tiles from blockIdx.x, blockIdx.y, a chunk of
+// a.zchunk planes from blockIdx.z.
+template <typename S, typename T>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : LBM_SC_MIN_BLOCKS)
+    stream_collide_kernel(const SCArgs<S, T> a) {
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    __shared__ int s_qi[Q];
+    load_qinfo(s_qi);
+    __syncthreads();
+    const int z_begin = blockIdx.z * a.zchunk;
+    sc_tile<S, T, false>(a, 0, 0, z_begin, min(a.g.n[2], z_begin + a.zchunk), (int)blockDim.x, sc_smem, s_qi);
+}
+
+// Many boxes in one persistent launch: block b takes the work items b,
+// b + gridDim.x, ... of the table (instance, x0, y0, z0), copies the
+// arguments of the item's instance into shared memory and runs its tile
+// (a.bx x 256 / a.bx cells, a.zchunk planes from z0).
+template <typename S, typename T>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? LBM_SC_MIN_BLOCKS_F64 : LBM_SC_MIN_BLOCKS)
+    stream_collide_batch_kernel(const SCArgs<S, T>* __restrict__ args, const int4* __restrict__ items, int n_items) {
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    __shared__ int s_qi[Q];
+    __shared__ __align__(16) SCArgs<S, T> s_a;
+    load_qinfo(s_qi);
+    constexpr int WORDS = (int)(sizeof(SCArgs<S, T>) / 4);
+    static_assert(sizeof(SCArgs<S, T>) % 4 == 0, "argument block copied in words");
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 item = items[it];
+        __syncthreads();                 // the previous tile is done with s_a
+        const int* src = reinterpret_cast<const int*>(args + item.x);
+        int* dst = reinterpret_cast<int*>(&s_a);
+        for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        sc_tile<S, T, true>(s_a, item.y, item.z, item.w, min(s_a.g.n[2], item.w + s_a.zchunk), s_a.bx, sc_smem,
+                            s_qi);
+    }
+}
+
 // bytes of dynamic shared memory of the kernel (256 threads)
 template <typename T>
 constexpr size_t sc_smem_bytes() {
@@ -254,16 +303,69 @@ void launch_stream_collide_t(const LbmStepParams& p, cudaStream_t st) {
     fill_sc_args<S, T>(p, a);
     const int nx = p.g.n[0];
     int bx = nx >= LBM_SC_BX ? LBM_SC_BX : ((nx + 31) / 32) * 32;
+    if (p.tile_bx > 0) bx = p.tile_bx;
     int by = 256 / bx;
+    a.bx = bx;
     dim3 block(bx, by, 1);
     const int bxy = ((nx + bx - 1) / bx) * ((p.g.n[1] + by - 1) / by);
     // at least 4 blocks per SM where the box allows, else shorter chunks
     const long long want = 4LL * (p.num_sms > 0 ? p.num_sms : 152);
     int zc = (int)((long long)bxy * p.g.n[2] / want);
     a.zchunk = zc < 1 ? 1 : (zc > LBM_SC_ZCHUNK ? LBM_SC_ZCHUNK : zc);
+    if (p.zchunk > 0) a.zchunk = p.zchunk;
     dim3 grid((nx + bx - 1) / bx, (p.g.n[1] + by - 1) / by, (p.g.n[2] + a.zchunk - 1) / a.zchunk);
     constexpr size_t smem = sc_smem_bytes<T>();
     stream_collide_kernel<S, T><<<grid, block, smem, st>>>(a);
+}
+
+// ------------------------------------------------------------ batched launch
+
+template <typename S>
+static void fill_batch_args_t(const LbmStepParams& p, int tile_bx, int zchunk, void* out) {
+    using T = typename Store<S>::T;
+    SCArgs<S, T> a;
+    fill_sc_args<S, T>(p, a);
+    a.bx = tile_bx;
+    a.zchunk = zchunk;
+    std::memcpy(out, &a, sizeof(a));
+}
+
+size_t batch_args_bytes(int storage) {
+    switch (storage) {
+        case 0: return sizeof(SCArgs<double, double>);
+        case 1: return sizeof(SCArgs<float, float>);
+        case 2: return sizeof(SCArgs<__half, float>);
+        default: return sizeof(SCArgs<__nv_bfloat16, float>);
+    }
+}
+
+void fill_batch_args(const LbmStepParams& p, int tile_bx, int zchunk, void* out) {
+    switch (p.storage) {
+        case 0: fill_batch_args_t<double>(p, tile_bx, zchunk, out); break;
+        case 1: fill_batch_args_t<float>(p, tile_bx, zchunk, out); break;
+        case 2: fill_batch_args_t<__half>(p, tile_bx, zchunk, out); break;
+        default: fill_batch_args_t<__nv_bfloat16>(p, tile_bx, zchunk, out); break;
+    }
+}
+
+int default_tile_bx(int nx) { return nx >= LBM_SC_BX ? LBM_SC_BX : ((nx + 31) / 32) * 32; }
+
+template <typename S>
+static void launch_batch_t(const void* d_args, const int4* d_items, int n_items, int grid, cudaStream_t st) {
+    using T = typename Store<S>::T;
+    constexpr size_t smem = sc_smem_bytes<T>();
+    stream_collide_batch_kernel<S, T>
+        <<<grid, 256, smem, st>>>(static_cast<const SCArgs<S, T>*>(d_args), d_items, n_items);
+}
+
+void launch_stream_collide_batch(int storage, const void* d_args, const int4* d_items, int n_items, int grid,
+                                 cudaStream_t st) {
+    switch (storage) {
+        case 0: launch_batch_t<double>(d_args, d_items, n_items, grid, st); break;
+        case 1: launch_batch_t<float>(d_args, d_items, n_items, grid, st); break;
+        case 2: launch_batch_t<__half>(d_args, d_items, n_items, grid, st); break;
+        default: launch_batch_t<__nv_bfloat16>(d_args, d_items, n_items, grid, st); break;
+    }
 }
 
 template <typename S>
@@ -272,7 +374,11 @@ cudaError_t prepare_t() {
     constexpr size_t smem = sc_smem_bytes<T>();
     if (smem <= 48 * 1024) return cudaSuccess;
     // float64 storage: above the default dynamic shared memory limit
-    return cudaFuncSetAttribute(stream_collide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(stream_collide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(stream_collide_batch_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
 }
 
 cudaError_t prepare_stream_collide(int storage) {

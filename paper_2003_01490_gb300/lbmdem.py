@@ -29,7 +29,9 @@ EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create
            'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore', 'lbm_sample_density',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
-           'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_launch_count',
+           'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_batch_create',
+           'lbm_batch_set_launch', 'lbm_batch_set_active', 'lbm_batch_step', 'lbm_batch_sync',
+           'lbm_batch_launch_count', 'lbm_batch_capture_stats', 'lbm_batch_last_error', 'lbm_batch_destroy', 'lbm_launch_count',
            'lbm_last_error',
            'lbm_destroy')
 
@@ -101,6 +103,18 @@ def load_library(path=LIB_PATH):
     lib.lbm_map_spheres_noalloc.argtypes = [P(LbmGrid), c_double, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p]
     lib.lbm_fp64_fma_rate.argtypes = [c_int, dp]
+    lib.lbm_batch_create.argtypes = [P(c_void_p), c_int, c_void_p, P(c_void_p)]
+    lib.lbm_batch_set_launch.argtypes = [c_void_p, c_int, c_int, c_int, c_int]
+    lib.lbm_batch_set_active.argtypes = [c_void_p, c_int, c_int]
+    lib.lbm_batch_step.argtypes = [c_void_p, c_int]
+    lib.lbm_batch_sync.argtypes = [c_void_p]
+    lib.lbm_batch_capture_stats.argtypes = [c_void_p, P(c_int), dp]
+    lib.lbm_batch_launch_count.argtypes = [c_void_p]
+    lib.lbm_batch_launch_count.restype = ctypes.c_longlong
+    lib.lbm_batch_last_error.argtypes = [c_void_p]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    lib.lbm_batch_destroy.argtypes = [c_void_p]
+    lib.lbm_batch_destroy.restype = None
     lib.lbm_launch_count.argtypes = [c_void_p]
     lib.lbm_launch_count.restype = ctypes.c_longlong
     lib.lbm_last_error.argtypes = [c_void_p]
@@ -108,7 +122,8 @@ def load_library(path=LIB_PATH):
     lib.lbm_destroy.argtypes = [c_void_p]
     lib.lbm_destroy.restype = None
     for name in EXPORTS:
-        if name not in ('lbm_launch_count', 'lbm_last_error', 'lbm_destroy'):
+        if name not in ('lbm_launch_count', 'lbm_last_error', 'lbm_destroy', 'lbm_batch_launch_count',
+                        'lbm_batch_last_error', 'lbm_batch_destroy'):
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -362,6 +377,65 @@ def lbm_fp64_fma_rate(iters=4096):
     out = c_double(0.0)
     _check(load_library().lbm_fp64_fma_rate(int(iters), ctypes.byref(out)))
     return out.value
+
+
+class LbmBatch:
+    """Handle of a batch of contexts (see lbm_batch_create); keeps its contexts
+    alive and releases the batch before them."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+
+    def __del__(self):
+        if getattr(self, 'handle', None):
+            load_library().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+
+def _bcheck(status, b=None):
+    if status != 0:
+        msg = load_library().lbm_batch_last_error(b.handle if b is not None else None).decode()
+        raise LbmError(status, msg)
+
+
+def lbm_batch_create(ctxs, stream=None):
+    """One batch over the contexts (one storage format). stream: a torch CUDA
+    stream the batch runs on (None: the contexts' stream, the current one when
+    they were created)."""
+    arr = (c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    h = c_void_p()
+    st = c_void_p(stream.cuda_stream) if stream is not None else None
+    _bcheck(load_library().lbm_batch_create(arr, len(ctxs), st, ctypes.byref(h)))
+    return LbmBatch(h, ctxs)
+
+
+def lbm_batch_set_launch(b, instance=-1, tile_bx=0, zchunk=0, blocks_per_sm=0):
+    _bcheck(load_library().lbm_batch_set_launch(b.handle, int(instance), int(tile_bx), int(zchunk),
+                                                int(blocks_per_sm)), b)
+
+
+def lbm_batch_set_active(b, instance, active):
+    _bcheck(load_library().lbm_batch_set_active(b.handle, int(instance), int(bool(active))), b)
+
+
+def lbm_batch_step(b, n_steps):
+    _bcheck(load_library().lbm_batch_step(b.handle, int(n_steps)), b)
+
+
+def lbm_batch_sync(b):
+    _bcheck(load_library().lbm_batch_sync(b.handle), b)
+
+
+def lbm_batch_capture_stats(b):
+    """(graphs captured, host ms spent capturing and instantiating them)."""
+    n, ms = c_int(0), c_double(0.0)
+    _bcheck(load_library().lbm_batch_capture_stats(b.handle, ctypes.byref(n), ctypes.byref(ms)), b)
+    return n.value, ms.value
+
+
+def lbm_batch_launch_count(b):
+    return int(load_library().lbm_batch_launch_count(b.handle))
 
 
 def lbm_launch_count(ctx):

@@ -154,7 +154,20 @@ def test_calls_on_a_null_context_fail_cleanly(lib):
         assert name in calls or name in (
             'lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
             'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_launch_count', 'lbm_last_error',
-            'lbm_destroy'), name
+            'lbm_destroy') or name.startswith('lbm_batch_'), name
+    # batch calls on a NULL batch, and batch creation without contexts, fail
+    # before any CUDA call
+    assert lib.lbm_batch_create(None, 0, None, None) == -1
+    h = ctypes.c_void_p()
+    assert lib.lbm_batch_create((ctypes.c_void_p * 1)(None), 1, None, ctypes.byref(h)) == -1 and not h.value
+    assert lib.lbm_batch_set_launch(None, -1, 0, 0, 0) == -1
+    assert lib.lbm_batch_set_active(None, 0, 1) == -1
+    assert lib.lbm_batch_step(None, 1) == -1
+    assert lib.lbm_batch_sync(None) == -1
+    assert lib.lbm_batch_launch_count(None) == 0
+    assert lib.lbm_batch_capture_stats(None, None, None) == -1
+    assert lib.lbm_batch_last_error(None).decode()
+    lib.lbm_batch_destroy(None)
     # the float64 throughput probe checks its arguments before any CUDA call
     out = ctypes.c_double(0.0)
     assert lib.lbm_fp64_fma_rate(0, ctypes.byref(out)) == -1
