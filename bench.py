@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument('--shape', default=None, help='NXxNYxNZ of the suspension box (default 256x256x512)')
     ap.add_argument('--particles', type=int, default=None, help='sphere count (default: 27 %% solids)')
     ap.add_argument('--e2e-steps', type=int, default=200)
+    ap.add_argument('--trace-file', default=None, help='served: write the arrival trace (JSON) here')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-configs', action='store_true',
@@ -429,9 +430,8 @@ def dense_roofline(m, storage, workload_name):
     share = {k: round(v / sum(phases.values()), 4) for k, v in phases.items()} if sum(phases.values()) else {}
     roofline = {'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': peak, 'unit': 'GB/s',
                 'frac': round(achieved / peak, 4), 'traffic': traffic,
-                'kernel': ('stream_collide_kernel' if storage == 'f64' else 'stream_collide_staged_kernel') +
-                          ' (pull stream with the particle links: CLI condition and momentum exchange; wall '
-                          'bounce-back; TRT+aB collision)',
+                'kernel': 'stream_collide_kernel (pull stream with the particle links: CLI condition and '
+                          'momentum exchange; wall bounce-back; TRT+aB collision)',
                 'kernel_ms_per_launch': round(k_ms, 5), 'alg_bytes_per_launch': int(alg_bytes),
                 'links_per_launch': int(n_links), 'link_bytes_per_launch': int(n_links * 2 * es),
                 'peak_source': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
@@ -678,20 +678,53 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def measure_served(n_jobs, steps_divisor, rank, local):
-    """A seeded stream of jobs (Poisson arrivals; sphere-wall and suspension
-    cubes of 32^3 to 128^3) served with continuous batching in float16 and in
-    float32 storage, and the plain float32 FIFO loop, all on the same trace:
-    float16-served against float32-served isolates the precision gain,
-    float32-served against the float32 FIFO loop the concurrency gain."""
+def measure_served(n_jobs, steps_divisor, rank, local, max_side=256, trace_file=None):
+    """The served form: a seeded stream of independent jobs (half sphere-wall
+    collisions, half periodic suspensions; cubes of 32^3 to max_side^3 cells,
+    0-2000 spheres of D = 8-16, 1000-20000 steps divided by steps_divisor)
+    with Poisson arrivals, served with continuous batching (admission by a
+    memory budget of 0.8 of the free device memory). The arrival rate follows
+    Little's law from a calibration pass: the aggregate throughput R (cell
+    updates per second) of the first jobs served all at once, and
+    lambda = 0.9 R / (mean work per job), i.e. arrivals at 90 % of the
+    capacity the GPU showed. The same trace is served in float16 and in
+    float32 storage and run by the plain float32 FIFO loop: float16-served
+    against float32-served isolates the precision gain, float32-served against
+    the float32 FIFO loop the concurrency gain at equal accuracy."""
     import torch
-    from paper_2003_01490_gb300 import serve, workloads
-    jobs = workloads.served(n=n_jobs, seed=20030149 + 1000 * rank, storage='f16', steps_divisor=steps_divisor)
+    from paper_2003_01490_gb300 import lbmdem as L, serve, workloads
+    gap0 = 0.004
+    jobs = workloads.served(n=n_jobs, seed=20030149 + 1000 * rank, storage='f16', steps_divisor=steps_divisor,
+                            max_side=max_side, gap=gap0)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    out = {'workload': 'served: %d jobs, Poisson arrivals (mean gap 4 ms), sphere-wall and suspension '
-                       'cubes 32^3-128^3, steps 1000-20000 / %d' % (len(jobs), steps_divisor),
-           'budget_bytes': budget}
+    work = [j['shape'][0] * j['shape'][1] * j['shape'][2] * j['steps'] for j in jobs]
+    mean_work = sum(work) / len(work)
+    # calibration: the first min(16, n) jobs all at once, float16
+    k = min(16, len(jobs))
+    cal = [dict(j, arrival=0.0) for j in jobs[:k]]
+    t0 = time.perf_counter()
+    serve.serve(cal, budget)
+    R = sum(work[:k]) / (time.perf_counter() - t0)
+    lam = 0.9 * R / mean_work
+    # the same Poisson draws with mean gap 1 / lambda
+    scale = (1.0 / lam) / gap0
+    for j in jobs:
+        j['arrival'] *= scale
+    mean_bytes = sum(serve.job_bytes(j) for j in jobs) / len(jobs)
+    if trace_file:
+        with open(trace_file, 'w') as fh:
+            json.dump([{k_: (list(v) if isinstance(v, tuple) else v) for k_, v in j.items()
+                        if k_ in ('name', 'shape', 'periodic', 'steps', 'arrival', 'tau')} for j in jobs], fh)
+    out = {'workload': 'served: %d jobs (a stated tenth of the 2000-job stream when n = 200), Poisson arrivals, '
+                       'sphere-wall and suspension cubes 32^3-%d^3 with 0-2000 spheres of D 8-16, steps 1000-20000 / %d'
+                       % (len(jobs), max_side, steps_divisor),
+           'budget_bytes': budget, 'cell_updates': int(sum(work)),
+           'arrival_rate': {'jobs_per_s': round(lam, 3), 'rule': "Little's law: 0.9 x calibrated throughput / "
+                            "mean work per job", 'calibrated_mlups': round(R / 1e6, 1),
+                            'mean_cell_updates_per_job': round(mean_work),
+                            'resident_jobs_for_0.8_of_memory': round(budget / mean_bytes, 1)},
+           'trace_file': trace_file}
     for key, storage, fn in (('served_f16', 'f16', 'serve'), ('served_f32', 'f32', 'serve'),
                              ('fifo_f32', 'f32', 'fifo')):
         js = [dict(j, storage=storage) for j in jobs]
@@ -700,21 +733,22 @@ def measure_served(n_jobs, steps_divisor, rank, local):
         rec = serve.serve(js, budget) if fn == 'serve' else serve.fifo(js)
         clk = clocks.stop()
         out[key] = dict(serve.summary(rec), clocks=clk)
+        torch.cuda.synchronize()
     return out
 
 
 def run_served(args, rank, world, local):
-    n = args.instances if '--instances' in sys.argv else 48
+    n = args.instances if '--instances' in sys.argv else 200
     div = args.steps_divisor if '--steps-divisor' in sys.argv else 50
-    r = measure_served(n, div, rank, local)
+    r = measure_served(n, div, rank, local, trace_file=args.trace_file)
     s_srv = r['served_f16']
     line = {
         'metric': 'MLUPS', 'value': s_srv['mlups'], 'unit': 'MLUPS', 'n_gpus': world,
         'steps': None, 'warmup': 0, 'ms_per_step': None,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f16', 'data': 'synthetic',
-        'config': {'workload': r['workload'], 'budget_bytes': r['budget_bytes'],
-                   'parallelism': 'replicas' if world > 1 else 'single GPU'},
+        'config': {'workload': r['workload'], 'budget_bytes': r['budget_bytes'], 'arrival_rate': r['arrival_rate'],
+                   'cell_updates': r['cell_updates'], 'parallelism': 'replicas' if world > 1 else 'single GPU'},
         'served': s_srv, 'served_f32': r['served_f32'], 'fifo_f32': r['fifo_f32'], 'clocks': s_srv['clocks'],
     }
     if rank == 0:
@@ -751,7 +785,7 @@ def measure_configs(args, rank, world, local):
     except Exception as ex:
         out['batched'] = {'error': str(ex)[:300]}
     try:
-        out['served'] = measure_served(48, 50, rank, local)
+        out['served'] = measure_served(100, 100, rank, local)
     except Exception as ex:
         out['served'] = {'error': str(ex)[:300]}
     return out
