@@ -19,3 +19,43 @@ def test_shear_drag_lift_at_half_resolution():
     assert res['converged']
     assert abs(res['C_D'] / 34.44 - 1) < 0.02
     assert abs(res['C_L'] / 2.30 - 1) < 0.03
+
+
+def test_stokes_array_drag_is_independent_of_tau_for_trt_not_for_srt():
+    # Sec. 2.4: the normalised drag of a fixed sphere in a periodic simple
+    # cubic array (C_ref = 2.842) does not depend on the relaxation time with
+    # TRT (magic 3/16) and TRT+aB, and does with SRT. Here at D = 10 in a 20^3
+    # box (half the paper's resolution), float64, run to steady state.
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no GPU')
+    from paper_2003_01490_gb300 import validation
+    C = {}
+    for model in ('TRT', 'TRT+aB'):
+        for tau in (0.55, 0.8, 1.5):
+            r = validation.stokes_array(tau, model=model, D=10.0)
+            assert r['converged']
+            C[model, tau] = r['C']
+    for tau in (0.55, 1.5):
+        C['SRT', tau] = validation.stokes_array(tau, model='SRT', D=10.0)['C']
+    print(C)
+    for model in ('TRT', 'TRT+aB'):
+        vals = [C[model, t] for t in (0.55, 0.8, 1.5)]
+        assert (max(vals) - min(vals)) / min(vals) < 1e-3
+        assert abs(vals[0] / 2.842 - 1) < 0.03
+    assert abs(C['SRT', 0.55] / C['SRT', 1.5] - 1) > 0.01
+
+
+def test_sphere_wall_rebound_height_st27_half_resolution():
+    # Sec. 4.4, St = 27, n_sub = 10: the sphere approaches the bottom wall with
+    # its prescribed settling velocity, is released to the DEM one diameter
+    # above it and bounces; the paper's rebound height over ten starts is
+    # H_r = 0.3269-0.3276 (mean 0.3274) at D = 20. Here at D = 10.
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no GPU')
+    from paper_2003_01490_gb300 import validation
+    r = validation.sphere_wall_rebound(n_sub=10, D=10.0)
+    print(r)
+    assert r['contact_step'] is not None
+    assert abs(r['H_r'] / 0.3274 - 1) < 0.05
