@@ -30,3 +30,18 @@ def test_first_checkpoint_of_the_stored_trajectory_is_reproduced():
     assert np.abs(sim.X - ref[:, :3]).max() <= 1e-12 * np.abs(ref[:, :3]).max()
     assert np.abs(sim.U - ref[:, 3:]).max() <= 1e-12 * np.abs(ref[:, 3:]).max()
     assert np.allclose(gen.field_stats(sim), stats, rtol=1e-10, atol=0)
+
+
+def test_sphere_wall_golden_is_the_oracle_as_it_stands():
+    # the first steps of tests/golden/sphere_wall_2000.npz, recomputed: the
+    # stored trajectory is what the oracle computes (bit for bit on this host)
+    import numpy as np
+    sys.path.insert(0, os.path.join(HERE, 'golden'))
+    import make_long_runs
+    from cases import build_oracle
+    gold = np.load(os.path.join(HERE, 'golden', 'sphere_wall_2000.npz'))['states']
+    sim = build_oracle(make_long_runs.sphere_wall_case())
+    for k in range(5):
+        sim.step()
+        got = np.concatenate([sim.X[0], sim.U[0], sim.Om[0], sim.Ffp[0], sim.Tfp[0]])
+        assert np.allclose(got, gold[k], rtol=1e-13, atol=1e-16), k
