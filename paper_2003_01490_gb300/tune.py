@@ -132,7 +132,7 @@ def time_groups(groups, steps):
     return (time.perf_counter() - t0) * 1e3
 
 
-def tune_batched(ctxs, storage, steps=4, groups=(1, 2, 4, 8, 16), use_cache=True):
+def tune_batched(ctxs, storage, steps=4, groups=(1, 2, 4, 8, 16, 32, 64), use_cache=True):
     """Number of concurrent batches and the launch shape for running `ctxs`
     (every one stepped once already): first the group count with the
     automatic shape, then the shape for that count. The contexts advance by

@@ -5,6 +5,7 @@ generators. Run from the repository root:
     python tests/golden/make_long_runs.py sphere-wall            # minutes
     python tests/golden/make_long_runs.py suspension [SCRATCH]   # hours, two processes
     python tests/golden/make_long_runs.py floor [SCRATCH]        # floor from what exists
+    python tests/golden/make_long_runs.py storage [SCRATCH]      # hours, four processes
 
 The suspension runs save their results after each of the field steps, so
 the step-1000 comparison exists long before step 5000 is reached; `floor`
@@ -25,6 +26,15 @@ oracle run from the same inputs, with particle 0 displaced by 1e-12 along x,
 gives the predictability floor (the divergence of two float64 runs that
 differ by 1e-12 in one input, Algorithm 1 being chaotic in a dense
 suspension) -> suspension_64x64x128_floor.txt.
+
+storage: the same suspension over 1000 steps, four oracle runs at once: the
+float64 reference, saved with rho - 1 (not rho) so that density deviations of
+1e-5 keep their digits -> suspension_64x64x128_1000.npz; and three runs whose
+stored post-collision PDFs are rounded after every step to the storage
+formats of the precision forms (f - w rounded to nearest in float32; float16
+and bfloat16 from that float32 value) -> the storage floor
+suspension_64x64x128_storage_floor.txt: the error that storing f - w in that
+format causes by itself, whatever the arithmetic around it.
 """
 import multiprocessing as mp
 import os
@@ -41,6 +51,9 @@ sys.path.insert(0, os.path.join(ROOT, 'tests'))
 SPHERE_WALL = os.path.join(HERE, 'sphere_wall_2000.npz')
 SUSPENSION = os.path.join(HERE, 'suspension_64x64x128_5000.npz')
 FLOOR = os.path.join(HERE, 'suspension_64x64x128_floor.txt')
+SUSPENSION_1000 = os.path.join(HERE, 'suspension_64x64x128_1000.npz')
+STORAGE_FLOOR = os.path.join(HERE, 'suspension_64x64x128_storage_floor.txt')
+STORAGE_FORMATS = ('f32', 'f16', 'bf16')
 SUSP_FIELD_STEPS = (1000, 5000)
 SUSP_STATE_EVERY = 100
 PERTURBATION = 1e-12
@@ -108,6 +121,90 @@ def _suspension_run(perturb, out):
             os.replace(tmp, out)
 
 
+def round_storage(v, fmt):
+    """v rounded to the storage format: float32 (nearest even), float16 and
+    bfloat16 (nearest even, from the float32 value)."""
+    v32 = np.asarray(v, np.float64).astype(np.float32)
+    if fmt == 'f32':
+        return v32.astype(np.float64)
+    if fmt == 'f16':
+        return v32.astype(np.float16).astype(np.float64)
+    bits = v32.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _storage_run(fmt, out):
+    """1000 oracle steps; fmt None keeps float64, else the fluid cells'
+    post-collision PDFs are stored as w + round(f - w) after every step."""
+    os.environ['OMP_NUM_THREADS'] = '1'
+    from cases import build_oracle
+    from oracle.d3q19 import W
+    sim = build_oracle(suspension_case())
+    w = W.reshape(19, 1)
+    states = {}
+    t0 = time.time()
+    for step in range(1, 1001):
+        sim.step()
+        if fmt is not None:
+            fluid = sim.owner < 0
+            sim.ft[:, fluid] = w + round_storage(sim.ft[:, fluid] - w, fmt)
+        if step % SUSP_STATE_EVERY == 0:
+            states[step] = np.concatenate([sim.X, sim.U, sim.Om], axis=1)
+            print('suspension (%s storage) step %d (%.0f s)' % (fmt or 'f64', step, time.time() - t0), flush=True)
+    rho, u = sim.fields()
+    steps = sorted(states)
+    tmp = out + '.tmp.npz'
+    np.savez_compressed(tmp, state_steps=np.array(steps), states=np.array([states[k] for k in steps]),
+                        drho_1000=np.where(sim.owner < 0, rho - 1.0, 0.0).astype(np.float32),
+                        u_1000=u.astype(np.float32), solid_1000=sim.owner >= 0)
+    os.replace(tmp, out)
+
+
+def run_storage(scratch):
+    ctx = mp.get_context('spawn')
+    jobs = [(None, SUSPENSION_1000)] + [(f, os.path.join(scratch, 'suspension_storage_%s.npz' % f))
+                                        for f in STORAGE_FORMATS]
+    procs = [ctx.Process(target=_storage_run, args=j) for j in jobs]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join()
+        if p.exitcode != 0:
+            raise SystemExit('oracle run failed')
+    write_storage_floor(scratch)
+
+
+def write_storage_floor(scratch):
+    a = np.load(SUSPENSION_1000)
+    shape = suspension_case()['shape']
+    lines = ['# storage floor of the 64x64x128 suspension (150 spheres D=12) at step 1000: the float64',
+             '# oracle with its fluid PDFs stored as w + round(f - w) in the format after every step,',
+             '# against the plain float64 oracle. Relative L2 of u, of rho and of rho-1 over cells fluid in',
+             '# both runs, relative L2 of the positions, RMS position distance / D, relative L2 of the',
+             '# particle velocities.',
+             '# format step rel_u rel_rho rel_rho-1 rel_pos rms_pos/D rel_vel']
+    for fmt in STORAGE_FORMATS:
+        path = os.path.join(scratch, 'suspension_storage_%s.npz' % fmt)
+        if not os.path.exists(path):
+            continue
+        b = np.load(path)
+        both = ~a['solid_1000'] & ~b['solid_1000']
+        da, db = a['drho_1000'].astype(np.float64), b['drho_1000'].astype(np.float64)
+        ru = rel_l2(b['u_1000'], a['u_1000'], both)
+        rr = rel_l2(1.0 + db, 1.0 + da, both)
+        rr1 = rel_l2(db, da, both)
+        k = list(a['state_steps']).index(1000)
+        xa, xb = a['states'][k][:, :3], b['states'][k][:, :3]
+        rp, dp = position_error(xb, xa, shape, 12.0)
+        ua, ub = a['states'][k][:, 3:6], b['states'][k][:, 3:6]
+        rv = float(np.linalg.norm(ub - ua) / np.linalg.norm(ua))
+        lines.append('%s 1000 %.6e %.6e %.6e %.6e %.6e %.6e' % (fmt, ru, rr, rr1, rp, dp, rv))
+    with open(STORAGE_FLOOR, 'w') as fh:
+        fh.write('\n'.join(lines) + '\n')
+    print('\n'.join(lines))
+
+
 def rel_l2(a, b, mask):
     a = np.asarray(a, np.float64)[..., mask]
     b = np.asarray(b, np.float64)[..., mask]
@@ -169,9 +266,10 @@ def main():
     what = sys.argv[1] if len(sys.argv) > 1 else ''
     if what == 'sphere-wall':
         run_sphere_wall()
-    elif what in ('suspension', 'floor'):
+    elif what in ('suspension', 'floor', 'storage', 'storage-floor'):
         scratch = sys.argv[2] if len(sys.argv) > 2 else HERE
-        (run_suspension if what == 'suspension' else write_floor)(scratch)
+        {'suspension': run_suspension, 'floor': write_floor, 'storage': run_storage,
+         'storage-floor': write_storage_floor}[what](scratch)
     else:
         raise SystemExit(__doc__)
 
