@@ -175,6 +175,19 @@ lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *
                                   double *omega, double *force_hyd, double *torque_hyd,
                                   int *n_out);
 
+/* The same read-out without waiting: queues the copies on the context's stream
+ * (after every step queued so far) and returns. The values are in the buffers
+ * once lbm_sync() or another synchronising call returns; the buffers must stay
+ * valid until then, and page-locked buffers let the copies run while the host
+ * queues further steps. Reading in this way after every step of a loop costs
+ * no host wait per step. Device errors of the steps are reported by
+ * lbm_sync(). force_hyd / torque_hyd pass through the context's scratch buffer
+ * (LBM_ERR_CAPACITY if 6 n doubles exceed it; it holds 4 min(cells, 2^22)).
+ * Errors: LBM_ERR_INVALID (NULL ctx, n_cap too small), LBM_ERR_CUDA. */
+lbm_status lbm_get_particle_state_async(lbm_ctx *ctx, int n_cap, double *pos, double *vel,
+                                        double *omega, double *force_hyd, double *torque_hyd,
+                                        int *n_out);
+
 /* Switch how particles move from the next step on (mode as lbm_dem.fixed_particles:
  * 0 DEM, 1 fixed, 2 prescribed motion), e.g. to release a sphere whose
  * approach velocity was prescribed (Sec. 4.4 turns the prescribed settling

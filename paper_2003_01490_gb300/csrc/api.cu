@@ -1083,6 +1083,34 @@ lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* 
     return check_status(ctx);
 }
 
+lbm_status lbm_get_particle_state_async(lbm_ctx* ctx, int n_cap, double* pos, double* vel, double* omega,
+                                        double* force_hyd, double* torque_hyd, int* n_out) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    const int n = ctx->P.n;
+    if (n_out) *n_out = n;
+    if (n_cap < n && (pos || vel || omega || force_hyd || torque_hyd))
+        return fail(ctx, LBM_ERR_INVALID, "n_cap smaller than the particle count");
+    if (n == 0) return LBM_OK;
+    if ((force_hyd || torque_hyd) && 6LL * n > 4LL * ctx->scratch_cells)
+        return fail(ctx, LBM_ERR_CAPACITY, "more particles than the scratch buffer holds forces and torques for");
+    cudaStream_t sm = ctx->stream;
+    if (pos) CK(cudaMemcpyAsync(pos, ctx->P.x, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    if (vel) CK(cudaMemcpyAsync(vel, ctx->P.u, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    if (omega) CK(cudaMemcpyAsync(omega, ctx->P.om, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    if (force_hyd || torque_hyd) {
+        // split [n][6] into F and T blocks in the scratch buffer (later users
+        // of the scratch buffer are ordered after these copies on the stream)
+        launch_fp_split(ctx->P.fp, ctx->scratch, n, sm);
+        CK(cudaGetLastError());
+        ctx->launches += 1;
+        if (force_hyd) CK(cudaMemcpyAsync(force_hyd, ctx->scratch, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+        if (torque_hyd)
+            CK(cudaMemcpyAsync(torque_hyd, ctx->scratch + 3 * (size_t)n, 24 * (size_t)n, cudaMemcpyDeviceToHost,
+                               sm));
+    }
+    return LBM_OK;
+}
+
 // ------------------------------------------------------------ checkpoints
 
 // a checkpoint: this header, the host-side insertion copies (fixed size for

@@ -861,4 +861,19 @@ void launch_state_copy(const Particles& P, cudaStream_t st) {
     state_copy_kernel<<<(3 * P.n + 255) / 256, 256, 0, st>>>(P);
 }
 
+// F^fp and T^fp of each particle ([n][6]) into two blocks [n][3] | [n][3],
+// the layout of the host read-out
+__global__ void fp_split_kernel(const double* __restrict__ fp, double* __restrict__ out, int n) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= 6LL * n) return;
+    const long long i = k / 6;
+    const int c = (int)(k - 6 * i);
+    out[(c < 3 ? 0 : 3LL * n) + 3 * i + (c < 3 ? c : c - 3)] = fp[k];
+}
+
+void launch_fp_split(const double* fp, double* out, int n, cudaStream_t st) {
+    if (n <= 0) return;
+    fp_split_kernel<<<(int)((6LL * n + 255) / 256), 256, 0, st>>>(fp, out, n);
+}
+
 }  // namespace lbmdem

@@ -169,6 +169,7 @@ void launch_dem_subcycle(const DemParams& p, int cur, int init, int last, cudaSt
 constexpr int DEM_ONE_BLOCK_MAX = 32;
 void launch_dem_step_one_block(const DemParams& p, int hcur, int n_sub, cudaStream_t st);
 void launch_state_copy(const Particles& P, cudaStream_t st);
+void launch_fp_split(const double* fp, double* out, int n, cudaStream_t st);
 void launch_view_update(const Particles& P, cudaStream_t st);
 void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st);
 

@@ -25,7 +25,8 @@ STATUS = {0: 'LBM_OK', -1: 'LBM_ERR_INVALID', -2: 'LBM_ERR_OOM', -3: 'LBM_ERR_CU
           -4: 'LBM_ERR_UNSTABLE', -5: 'LBM_ERR_CAPACITY', -6: 'LBM_ERR_TIMEOUT', -7: 'LBM_ERR_STATE'}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create_in_arena',
-           'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_set_particle_velocity',
+           'lbm_add_spheres', 'lbm_step', 'lbm_get_particle_state', 'lbm_get_particle_state_async',
+           'lbm_set_particle_velocity',
            'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore', 'lbm_sample_density',
            'lbm_get_fields',
            'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_add_spheres.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_step.argtypes = [c_void_p, c_int]
     lib.lbm_get_particle_state.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
+    lib.lbm_get_particle_state_async.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp, P(c_int)]
     lib.lbm_set_particle_velocity.argtypes = [c_void_p, c_int, dp, dp]
     lib.lbm_set_motion.argtypes = [c_void_p, c_int]
     lib.lbm_sample_density.argtypes = [c_void_p, c_int, dp, dp]
@@ -291,6 +293,29 @@ def lbm_get_particle_state(ctx, out=None):
     _check(lib.lbm_get_particle_state(ctx.handle, n, *[_dptr(res[k]) for k in keys], None),
            ctx.handle)
     return res
+
+
+def lbm_get_particle_state_async(ctx, out):
+    """Queue copies of the particle state into the arrays of ``out`` (keys
+    pos, vel, omega, force_hyd, torque_hyd, any subset; C-contiguous float64
+    with n x 3 entries, page-locked for the copies to overlap host work) and
+    return without waiting; the values are there once lbm_sync(ctx) returns.
+    The arrays must stay alive until then."""
+    lib = load_library()
+    n = c_int(0)
+    _check(lib.lbm_get_particle_state_async(ctx.handle, 0, None, None, None, None, None, ctypes.byref(n)),
+           ctx.handle)
+    n = n.value
+    keys = ('pos', 'vel', 'omega', 'force_hyd', 'torque_hyd')
+    ptrs = []
+    for k in keys:
+        a = out.get(k)
+        if a is not None:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags['C_CONTIGUOUS']
+                    and a.size >= 3 * n):
+                raise ValueError('%s: expected a C-contiguous float64 array of %d x 3 values' % (k, n))
+        ptrs.append(_dptr(a))
+    _check(lib.lbm_get_particle_state_async(ctx.handle, n, *ptrs, None), ctx.handle)
 
 
 def lbm_get_fields(ctx):

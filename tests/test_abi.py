@@ -132,6 +132,7 @@ def test_calls_on_a_null_context_fail_cleanly(lib):
         'lbm_step': (None, 1),
         'lbm_sync': (None,),
         'lbm_get_particle_state': (None, 0, dp, dp, dp, dp, dp, ctypes.byref(n)),
+        'lbm_get_particle_state_async': (None, 0, dp, dp, dp, dp, dp, ctypes.byref(n)),
         'lbm_set_particle_velocity': (None, 0, dp, dp),
         'lbm_set_motion': (None, 0),
         'lbm_checkpoint_bytes': (None, ctypes.byref(size)),

@@ -247,3 +247,29 @@ def test_density_probe_interpolates_a_linear_field_exactly(L):
     pts = np.random.default_rng(3).uniform([0.5, 0.0, 0.0], [nx - 0.5, ny, nz], size=(50, 3))
     got = L.lbm_sample_density(ctx, pts)
     assert np.abs(got - (1.0 + 1e-3 * (pts[:, 0] - 0.5))).max() < 1e-6
+
+
+def test_async_particle_state_read_out_equals_the_synchronous_one(L):
+    # one read-out queued after every step into page-locked buffers (later
+    # copies overwrite earlier ones in stream order); after lbm_sync the
+    # buffers hold the state of the last step, equal to the synchronous
+    # read-out of a twin context; a buffer of the wrong size is refused
+    import torch
+    case = checkpoint_case()
+    a, b = build_gpu(case), build_gpu(case)
+    n = len(case['spheres']['radius'])
+    keys = ('pos', 'vel', 'omega', 'force_hyd', 'torque_hyd')
+    pinned = {k: torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy() for k in keys}
+    for _ in range(12):
+        L.lbm_step(a, 1)
+        L.lbm_get_particle_state_async(a, pinned)
+    L.lbm_sync(a)
+    L.lbm_step(b, 12)
+    ref = L.lbm_get_particle_state(b)
+    for k in keys:
+        assert np.array_equal(pinned[k], ref[k]), k
+    # only some of the arrays
+    L.lbm_get_particle_state_async(a, {'vel': pinned['vel']})
+    L.lbm_sync(a)
+    with pytest.raises(ValueError):
+        L.lbm_get_particle_state_async(a, {'pos': np.zeros((n, 2))})
