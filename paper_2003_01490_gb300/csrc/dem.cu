@@ -747,31 +747,126 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
 // All subcycles of a step in one block when the particles fit in it (at most
 // PPB): the first position update, n_sub subcycles separated by block
 // barriers (each reads the positions and velocities the previous one wrote),
-// and the copy back into buffer 0 after an odd count. Launch latency, not
-// arithmetic, sets the time of a few-particle DEM step.
+// and the copy back into buffer 0 after an odd count. The particles' state
+// stays in shared memory for the whole step: the block loads it once, points
+// the particle arrays of its (shared) parameter copy at the staged arrays, runs
+// the subcycles there -- the code of the multi-block path, reaching shared
+// memory through generic pointers -- and writes back what the step changed.
+// Neighbour lists, pair springs and the particle views stay in global memory.
+// Latency, not arithmetic, sets the time of a few-particle DEM step, so each
+// dependent global round trip saved per subcycle counts.
+struct DemStage {
+    double x[2][3 * PPB], u[2][3 * PPB], om[2][3 * PPB];
+    float xf[2][3 * PPB], uf[2][3 * PPB], omf[2][3 * PPB];
+    double F_prev[3 * PPB], T_prev[3 * PPB], ext[3 * PPB], fbar[6 * PPB];
+    double hm[PPB], hI[PPB], R[PPB], m[PPB];
+    double whist[2][18 * PPB];
+    unsigned char wact[2][6 * PPB];
+};
+
+// sp: the step's parameters in shared memory (n <= PPB particles); g receives
+// the global particle arrays
 template <typename T>
-__global__ void __launch_bounds__(128) dem_step_one_block_kernel(const DemParams p, int hcur, int n_sub) {
+__device__ void dem_step_block(DemParams& sp, Particles& g, DemStage& st, int hcur, int n_sub) {
     const int tid = threadIdx.x;
-    if (tid < p.P.n) position_update(p, tid);
+    const int n = sp.P.n;
+    if (tid == 0) g = sp.P;
+    __syncthreads();
+    for (int k = tid; k < 3 * n; k += blockDim.x) {
+        st.x[0][k] = g.x[k];
+        st.u[0][k] = g.u[k];
+        st.om[0][k] = g.om[k];
+        st.xf[0][k] = g.xf[k];
+        st.uf[0][k] = g.ufs[0][k];
+        st.omf[0][k] = g.omfs[0][k];
+        st.F_prev[k] = g.F_prev[k];
+        st.T_prev[k] = g.T_prev[k];
+        st.ext[k] = g.ext[k];
+    }
+    for (int k = tid; k < 6 * n; k += blockDim.x) {
+        st.fbar[k] = g.fbar[k];
+        st.wact[0][k] = g.wact[0][k];
+        st.wact[1][k] = g.wact[1][k];
+    }
+    for (int k = tid; k < 18 * n; k += blockDim.x) {
+        st.whist[0][k] = g.whist[0][k];
+        st.whist[1][k] = g.whist[1][k];
+    }
+    for (int k = tid; k < n; k += blockDim.x) {
+        st.hm[k] = g.hm[k];
+        st.hI[k] = g.hI[k];
+        st.R[k] = g.R[k];
+        st.m[k] = g.m[k];
+    }
+    if (tid == 0) {
+        Particles& P = sp.P;
+        P.x = P.xs[0] = st.x[0];
+        P.xs[1] = st.x[1];
+        P.u = P.us[0] = st.u[0];
+        P.us[1] = st.u[1];
+        P.om = P.oms[0] = st.om[0];
+        P.oms[1] = st.om[1];
+        P.xf = P.xfs[0] = st.xf[0];
+        P.xfs[1] = st.xf[1];
+        for (int h = 0; h < 2; ++h) {
+            P.ufs[h] = st.uf[h];
+            P.omfs[h] = st.omf[h];
+            P.whist[h] = st.whist[h];
+            P.wact[h] = st.wact[h];
+        }
+        P.F_prev = st.F_prev;
+        P.T_prev = st.T_prev;
+        P.ext = st.ext;
+        P.fbar = st.fbar;
+        P.hm = st.hm;
+        P.hI = st.hI;
+        P.R = st.R;
+        P.m = st.m;
+    }
+    __syncthreads();
+    if (tid < n) position_update(sp, tid);
     __syncthreads();
     int cur = 0;
     for (int s = 0; s < n_sub; ++s) {
-        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == n_sub - 1, 0);
+        subcycle_body<T>(sp, cur, hcur, 1 - hcur, 0, s == n_sub - 1, 0);
         __syncthreads();
         hcur = 1 - hcur;
         cur = 1 - cur;
     }
-    if (cur == 1) {
-        const Particles& P = p.P;
-        for (int k = tid; k < 3 * P.n; k += blockDim.x) {
-            P.xs[0][k] = P.xs[1][k];
-            P.us[0][k] = P.us[1][k];
-            P.oms[0][k] = P.oms[1][k];
-            P.xfs[0][k] = P.xfs[1][k];
-            P.ufs[0][k] = P.ufs[1][k];
-            P.omfs[0][k] = P.omfs[1][k];
-        }
+    // the state after the last subcycle is in buffer cur; buffer 0 of the
+    // global arrays receives it
+    for (int k = tid; k < 3 * n; k += blockDim.x) {
+        g.x[k] = st.x[cur][k];
+        g.u[k] = st.u[cur][k];
+        g.om[k] = st.om[cur][k];
+        g.xf[k] = st.xf[cur][k];
+        g.ufs[0][k] = st.uf[cur][k];
+        g.omfs[0][k] = st.omf[cur][k];
+        g.F_prev[k] = st.F_prev[k];
+        g.T_prev[k] = st.T_prev[k];
     }
+    for (int k = tid; k < 6 * n; k += blockDim.x) {
+        g.wact[0][k] = st.wact[0][k];
+        g.wact[1][k] = st.wact[1][k];
+    }
+    for (int k = tid; k < 18 * n; k += blockDim.x) {
+        g.whist[0][k] = st.whist[0][k];
+        g.whist[1][k] = st.whist[1][k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) dem_step_one_block_kernel(const DemParams p, int hcur, int n_sub) {
+    __shared__ __align__(16) DemParams sp;
+    __shared__ __align__(16) Particles g;
+    __shared__ __align__(16) DemStage st;
+    constexpr int WORDS = (int)(sizeof(DemParams) / 4);
+    static_assert(sizeof(DemParams) % 4 == 0, "parameters copied in words");
+    const int* src = reinterpret_cast<const int*>(&p);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    dem_step_block<T>(sp, g, st, hcur, n_sub);
 }
 
 // The one-block DEM steps of many instances in one launch: block b runs the
@@ -785,35 +880,15 @@ struct DemBatchEntry {
 template <typename T>
 __global__ void __launch_bounds__(128) dem_step_batch_kernel(const DemBatchEntry* __restrict__ table) {
     __shared__ __align__(16) DemBatchEntry e;
+    __shared__ __align__(16) Particles g;
+    __shared__ __align__(16) DemStage st;
     constexpr int WORDS = (int)(sizeof(DemBatchEntry) / 4);
     static_assert(sizeof(DemBatchEntry) % 4 == 0, "entry copied in words");
     const int* src = reinterpret_cast<const int*>(table + blockIdx.x);
     int* dst = reinterpret_cast<int*>(&e);
     for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    const DemParams& p = e.p;
-    const int tid = threadIdx.x;
-    int hcur = e.hcur;
-    if (tid < p.P.n) position_update(p, tid);
-    __syncthreads();
-    int cur = 0;
-    for (int s = 0; s < e.n_sub; ++s) {
-        subcycle_body<T>(p, cur, hcur, 1 - hcur, 0, s == e.n_sub - 1, 0);
-        __syncthreads();
-        hcur = 1 - hcur;
-        cur = 1 - cur;
-    }
-    if (cur == 1) {
-        const Particles& P = p.P;
-        for (int k = tid; k < 3 * P.n; k += blockDim.x) {
-            P.xs[0][k] = P.xs[1][k];
-            P.us[0][k] = P.us[1][k];
-            P.oms[0][k] = P.oms[1][k];
-            P.xfs[0][k] = P.xfs[1][k];
-            P.ufs[0][k] = P.ufs[1][k];
-            P.omfs[0][k] = P.omfs[1][k];
-        }
-    }
+    dem_step_block<T>(e.p, g, st, e.hcur, e.n_sub);
 }
 
 size_t dem_batch_entry_bytes() { return sizeof(DemBatchEntry); }

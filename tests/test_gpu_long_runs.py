@@ -11,18 +11,21 @@
   carry the differences along, see test_gpu_parity.py); 2000 steps with a
   stiff contact (T_c = 32 steps) amplify them further, so the bounds sit at
   1e-9 (fields, trajectory) -- still seven orders below the float32 path.
-* The 64 x 64 x 128 suspension (150 spheres of D = 12) in float32 at steps
-  1000 and 5000 against the predictability floor: the divergence of two
-  float64 oracle runs whose inputs differ by 1e-12 in one position
-  (tests/golden/suspension_64x64x128_floor.txt). Where that floor lies below
-  the float32 targets (relative L2 1e-6 on velocity and density, 1e-5 on
-  positions) the targets are asserted; where chaos has amplified the 1e-12
-  perturbation above them, no implementation can be held to them and the
-  error is bounded by the floor instead (a float32 run is a perturbation of
-  ~1e-7 per value, so its divergence is compared with 1e5 times the floor).
+* The 64 x 64 x 128 suspension (150 spheres of D = 12) at step 1000 (and
+  5000 where the oracle run has reached it) against two floors, both from
+  float64 oracle runs (tests/golden/make_long_runs.py, oracle only):
+  - the predictability floor: the divergence of two runs whose inputs differ
+    by 1e-12 in one position (suspension_64x64x128_floor.txt);
+  - the storage floor: the divergence caused by storing f - w in the format
+    alone, the oracle's PDFs rounded to it after every step
+    (suspension_64x64x128_storage_floor.txt).
+  Where both floors lie below the float32 targets (relative L2 1e-6 on
+  velocity and density, 1e-5 on positions) the targets are asserted; where a
+  floor lies above a target no implementation storing that format can meet
+  it, and the error is held to a small multiple of the floor (the kernels
+  also round their arithmetic, which the storage floor leaves out).
 * The precision forms (float16 / bfloat16 storage of f - w) on the same
-  suspension, errors reported at steps 1000 and 5000 beside the floor.
-Expected values come from tests/golden/make_long_runs.py (oracle only).
+  suspension, errors against their storage floors.
 """
 import os
 
@@ -103,16 +106,18 @@ def test_sphere_wall_collision_over_its_2000_steps_f64(L):
 
 # ------------------------------------------------------------ suspension at 1000 / 5000 steps
 
-def load_floor():
-    rows = {}
-    p = os.path.join(GOLDEN, 'suspension_64x64x128_floor.txt')
+def load_rows(name, keyed_by_format=False):
+    p = os.path.join(GOLDEN, name)
     if not os.path.exists(p):
-        pytest.skip('predictability floor not stored yet (tests/golden/make_long_runs.py suspension)')
+        pytest.skip('%s not stored yet (tests/golden/make_long_runs.py)' % name)
+    rows = {}
     for line in open(p):
         if line.startswith('#') or not line.strip():
             continue
         v = line.split()
-        rows[int(v[0])] = dict(zip(('u', 'rho', 'rho1', 'pos', 'pos_d', 'vel'), map(float, v[1:])))
+        key = (v[0], int(v[1])) if keyed_by_format else int(v[0])
+        vals = v[2:] if keyed_by_format else v[1:]
+        rows[key] = dict(zip(('u', 'rho', 'rho1', 'pos', 'pos_d', 'vel'), map(float, vals)))
     return rows
 
 
@@ -123,70 +128,89 @@ def suspension_case(storage):
                 spheres=spheres(w['pos'], w['radius'], w['density'], w['vel'], w['omega']), dem=w['dem'])
 
 
-def suspension_errors(L, storage):
-    """Errors against the oracle at each field step the golden file holds."""
-    path = os.path.join(GOLDEN, 'suspension_64x64x128_5000.npz')
-    if not os.path.exists(path):
-        pytest.skip('oracle run not stored yet (tests/golden/make_long_runs.py suspension)')
-    gold = np.load(path)
-    steps = [s for s in (1000, 5000) if 'u_%d' % s in gold.files]
-    assert steps, 'golden file without field steps'
+def errors_against(L, ctx, gold, step):
+    """Errors of the context's state against an oracle file at `step`: fields
+    over cells fluid on both sides (rho - 1 from the file's float32 rho - 1,
+    or from its float32 rho where only that is stored), particle state with
+    periodic images."""
     shape = np.array([64.0, 64.0, 128.0])
+    st = L.lbm_get_particle_state(ctx)
+    rho, u, flags = L.lbm_get_fields(ctx)
+    both = ((flags & L.FLAG_SOLID) == 0) & ~gold['solid_%d' % step]
+    if 'drho_%d' % step in gold.files:
+        d_ref = gold['drho_%d' % step].astype(np.float64)
+    else:
+        d_ref = gold['rho_%d' % step].astype(np.float64) - 1.0
+    k = list(gold['state_steps']).index(step)
+    xr = gold['states'][k][:, :3]
+    d = st['pos'] - xr
+    d -= shape * np.round(d / shape)
+    return dict(u=rel_l2(u, gold['u_%d' % step], both), rho=rel_l2(rho, 1.0 + d_ref, both),
+                rho1=rel_l2(rho - 1.0, d_ref, both),
+                pos=float(np.sqrt((d * d).sum() / (xr * xr).sum())),
+                pos_d=float(np.sqrt((d * d).sum(1).mean()) / 12.0),
+                vel=rel_l2(st['vel'], gold['states'][k][:, 3:6]))
+
+
+def report(label, e, floors):
+    keys = ('u', 'rho', 'rho1', 'pos', 'pos_d', 'vel')
+    print('%s: ' % label + ', '.join('%s %.2e' % (k, e[k]) for k in keys))
+    for name, f in floors.items():
+        print('    %s floor: ' % name + ', '.join('%s %.2e' % (k, f[k]) for k in keys))
+
+
+def run_to_1000(L, storage):
+    path = os.path.join(GOLDEN, 'suspension_64x64x128_1000.npz')
+    if not os.path.exists(path):
+        pytest.skip('oracle run not stored yet (tests/golden/make_long_runs.py storage)')
+    gold = np.load(path)
     ctx = build_gpu(suspension_case(storage))
-    done = 0
-    out = {}
-    for step in steps:
-        L.lbm_step(ctx, step - done)
-        done = step
-        st = L.lbm_get_particle_state(ctx)
-        rho, u, flags = L.lbm_get_fields(ctx)
-        both = ((flags & L.FLAG_SOLID) == 0) & ~gold['solid_%d' % step]
-        k = list(gold['state_steps']).index(step)
-        xr = gold['states'][k][:, :3]
-        d = st['pos'] - xr
-        d -= shape * np.round(d / shape)
-        out[step] = dict(u=rel_l2(u, gold['u_%d' % step], both), rho=rel_l2(rho, gold['rho_%d' % step], both),
-                         rho1=rel_l2(rho - 1.0, gold['rho_%d' % step].astype(np.float64) - 1.0, both),
-                         pos=float(np.sqrt((d * d).sum() / (xr * xr).sum())),
-                         pos_d=float(np.sqrt((d * d).sum(1).mean()) / 12.0),
-                         vel=rel_l2(st['vel'], gold['states'][k][:, 3:6]))
-    return out
+    L.lbm_step(ctx, 1000)
+    return ctx, errors_against(L, ctx, gold, 1000)
 
 
-def report(storage, errs, floor):
-    for step, e in errs.items():
-        f = floor.get(step, {})
-        print('%s step %d: u %.2e (floor %.2e), rho %.2e (floor %.2e), rho-1 %.2e (floor %.2e), '
-              'positions %.2e (floor %.2e), RMS position / D %.2e, particle velocities %.2e (floor %.2e)'
-              % (storage, step, e['u'], f.get('u', np.nan), e['rho'], f.get('rho', np.nan), e['rho1'],
-                 f.get('rho1', np.nan), e['pos'], f.get('pos', np.nan), e['pos_d'], e['vel'],
-                 f.get('vel', np.nan)))
+# a kernel error above its storage floor: float32 arithmetic and float32
+# link geometry add rounding of the same order as the storage itself
+ARITH_FACTOR = 4.0
 
 
-def test_reduced_suspension_f32_at_1000_and_5000_steps_against_the_floor(L):
-    floor = load_floor()
-    errs = suspension_errors(L, 'f32')
-    report('f32', errs, floor)
-    for step, e in errs.items():
-        f = floor[step]
-        for key, tol in (('u', 1e-6), ('rho', 1e-6), ('pos', 1e-5)):
-            if f[key] < tol:
-                assert e[key] < tol, (step, key, e[key], f[key])
-            else:
-                assert e[key] < 1e5 * f[key], (step, key, e[key], f[key])
-
-
-# errors of the 16-bit forms measured on GB300 (step: u, rho - 1, RMS position / D);
-# the test bounds sit at ten times these
-PRECISION_BOUNDS = {'f16': {1000: (2e-2, 2e-2, 1e-3), 5000: (1e-1, 1e-1, 1e-2)},
-                    'bf16': {1000: (2e-1, 2e-1, 1e-2), 5000: (1.0, 1.0, 1e-1)}}
+def test_reduced_suspension_f32_at_1000_steps_against_the_floors(L):
+    chaos = load_rows('suspension_64x64x128_floor.txt')[1000]
+    storage = load_rows('suspension_64x64x128_storage_floor.txt', keyed_by_format=True)[('f32', 1000)]
+    _, e = run_to_1000(L, 'f32')
+    report('f32 step 1000', e, {'predictability': chaos, 'f32 storage': storage})
+    # the float32 copies of rho in the predictability runs resolve no density
+    # difference below 6e-8: that floor's rho columns are not used
+    for key, tol in (('u', 1e-6), ('rho', 1e-6), ('pos', 1e-5)):
+        floor = storage[key] if key.startswith('rho') else max(storage[key], chaos[key])
+        if floor < tol:
+            assert e[key] < tol, (key, e[key], floor)
+        else:
+            assert e[key] < ARITH_FACTOR * floor, (key, e[key], floor)
 
 
 @pytest.mark.parametrize('storage', ['f16', 'bf16'])
-def test_precision_form_errors_at_1000_and_5000_steps(L, storage):
-    floor = load_floor()
-    errs = suspension_errors(L, storage)
-    report(storage, errs, floor)
-    for step, e in errs.items():
-        bu, br, bx = PRECISION_BOUNDS[storage][step]
-        assert e['u'] < bu and e['rho1'] < br and e['pos_d'] < bx
+def test_precision_form_errors_at_1000_steps_against_their_storage_floor(L, storage):
+    floor = load_rows('suspension_64x64x128_storage_floor.txt', keyed_by_format=True)[(storage, 1000)]
+    _, e = run_to_1000(L, storage)
+    report('%s step 1000' % storage, e, {storage + ' storage': floor})
+    for key in ('u', 'rho1', 'pos_d', 'vel'):
+        assert e[key] < ARITH_FACTOR * floor[key], (key, e[key], floor[key])
+
+
+def test_reduced_suspension_f32_at_5000_steps_against_the_predictability_floor(L):
+    path = os.path.join(GOLDEN, 'suspension_64x64x128_5000.npz')
+    if not os.path.exists(path) or 'u_5000' not in np.load(path).files:
+        pytest.skip('oracle run has not reached step 5000 (tests/golden/make_long_runs.py suspension)')
+    gold = np.load(path)
+    chaos = load_rows('suspension_64x64x128_floor.txt')[5000]
+    ctx = build_gpu(suspension_case('f32'))
+    L.lbm_step(ctx, 5000)
+    e = errors_against(L, ctx, gold, 5000)
+    report('f32 step 5000', e, {'predictability': chaos})
+    # a float32 run is a perturbation of ~1e-7 of every value, the floor's of
+    # 1e-12 of one position: where chaos has amplified the latter beyond the
+    # targets, the former is held to 1e5 times it
+    for key, tol in (('u', 1e-6), ('pos', 1e-5)):
+        if chaos[key] >= tol:
+            assert e[key] < 1e5 * chaos[key], (key, e[key], chaos[key])
