@@ -250,6 +250,15 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes);
 /* Wait for all queued work and report device-side errors (sticky). */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
+/* Queue the context's later work on another stream of the same device
+ * (NULL: the legacy default stream). Waits for the work queued so far on the
+ * old stream first. Contexts that share a stream run one after another; a
+ * batch (lbm_batch_create) orders its steps after the streams its contexts
+ * had when it was created, so move contexts before creating their batch.
+ * Errors: LBM_ERR_INVALID (NULL ctx), LBM_ERR_STATE (phase timing on),
+ * LBM_ERR_CUDA, and device errors of the finished work (as lbm_sync). */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
 /* Device timing of lbm_step() by phase, with CUDA events recorded on the
  * context stream between the launches of each step. Phases: 0 the boundary
  * kernel (particle links, Eqs. (14)-(17), and missing links), 1 the dense

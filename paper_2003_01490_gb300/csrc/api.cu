@@ -789,6 +789,40 @@ struct StepState {
     int dem_hcur = 0, dem_nsub = 0;
 };
 
+// parameters of the step's boundary and dense kernels from the context state
+void fill_step_params(const lbm_ctx* ctx, LbmStepParams& lp) {
+    const lbm_relax& r = ctx->relax;
+    const lbm_dem& d = ctx->dem;
+    const double s_nu = 1.0 / r.tau;
+    lp = LbmStepParams{};
+    lp.storage = ctx->storage;
+    lp.src = ctx->f[ctx->cur];
+    lp.dst = ctx->f[1 - ctx->cur];
+    lp.flags = ctx->flags;
+    lp.owner = ctx->owner;
+    lp.g = ctx->g;
+    lp.s_plus = s_nu;
+    lp.s_minus = s_minus_of(s_nu, r.magic);
+    lp.s_b_shell = s_b_of(s_nu, r.lambda_b_shell);
+    lp.s_b_bulk = s_b_of(s_nu, r.lambda_b_bulk);
+    lp.bulk_corr = r.lambda_b_bulk != 1.0;
+    for (int a = 0; a < 3; ++a) {
+        lp.a_user[a] = ctx->a_user[a];
+        lp.ext_total[a] = ctx->ext_total[a];
+    }
+    lp.n_solid = ctx->n_solid;
+    lp.counterforce = d.fluid_counterforce && ctx->P.n > 0;
+    lp.P = ctx->P;
+    lp.missing_links = d.missing_links && ctx->P.n > 0;
+    lp.status = ctx->status;
+    lp.miss_list = ctx->miss_list;
+    lp.miss_count = ctx->miss_count;
+    lp.miss_cap = ctx->miss_cap;
+    lp.num_sms = ctx->num_sms;
+    lp.accel_d = ctx->accel;
+    lp.accel_f = ctx->accel_f;
+}
+
 lbm_status enqueue_pre(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& ss) {
     const lbm_relax& r = ctx->relax;
     const lbm_dem& d = ctx->dem;
@@ -820,33 +854,7 @@ lbm_status enqueue_pre(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepState& 
     // Algorithm 1, lines 1-3: boundary conditions, interaction force, LBM step
     CK(prof_mark(ctx));
     LbmStepParams& lp = ss.lp;
-    lp = LbmStepParams{};
-    lp.storage = ctx->storage;
-    lp.src = ctx->f[ctx->cur];
-    lp.dst = ctx->f[1 - ctx->cur];
-    lp.flags = ctx->flags;
-    lp.owner = ctx->owner;
-    lp.g = ctx->g;
-    lp.s_plus = s_nu;
-    lp.s_minus = s_minus_of(s_nu, r.magic);
-    lp.s_b_shell = s_b_of(s_nu, r.lambda_b_shell);
-    lp.s_b_bulk = s_b_of(s_nu, r.lambda_b_bulk);
-    lp.bulk_corr = r.lambda_b_bulk != 1.0;
-    for (int a = 0; a < 3; ++a) {
-        lp.a_user[a] = ctx->a_user[a];
-        lp.ext_total[a] = ctx->ext_total[a];
-    }
-    lp.n_solid = ctx->n_solid;
-    lp.counterforce = d.fluid_counterforce && ctx->P.n > 0;
-    lp.P = ctx->P;
-    lp.missing_links = d.missing_links && ctx->P.n > 0;
-    lp.status = ctx->status;
-    lp.miss_list = ctx->miss_list;
-    lp.miss_count = ctx->miss_count;
-    lp.miss_cap = ctx->miss_cap;
-    lp.num_sms = ctx->num_sms;
-    lp.accel_d = ctx->accel;
-    lp.accel_f = ctx->accel_f;
+    fill_step_params(ctx, lp);
     launch_boundary(lp, sm, BC_ACCEL);
     // beside the dense kernel, on the side stream: the missing links (their
     // sums commute with the dense kernel's) and the DEM's neighbour lists,
@@ -1048,6 +1056,14 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
     }
     CK(cudaGetLastError());
     return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+    if (ctx->profiling) return fail(ctx, LBM_ERR_STATE, "lbm_set_stream: phase timing is on");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return check_status(ctx);
 }
 
 lbm_status lbm_sync(lbm_ctx* ctx) {
@@ -1419,6 +1435,8 @@ struct lbm_batch {
         void* d_dem = nullptr;             // one-block DEM steps of the instances, one entry each
         int n_items = 0;
         int n_dem = 0;
+        void* d_gang = nullptr;            // parameter tables and block offsets of the gang launches
+        int gang_launches = 0;             // gang launches in one step (0: per-instance branches)
         std::vector<long long> launches;   // kernel launches per instance in one step
         std::vector<int> hcur_after;       // history parity per instance after the step
     };
@@ -1451,6 +1469,7 @@ void batch_clear_graphs(lbm_batch* b) {
         if (kv.second.d_args) cudaFree(kv.second.d_args);
         if (kv.second.d_items) cudaFree(kv.second.d_items);
         if (kv.second.d_dem) cudaFree(kv.second.d_dem);
+        if (kv.second.d_gang) cudaFree(kv.second.d_gang);
     }
     b->graphs.clear();
 }
@@ -1586,6 +1605,178 @@ lbm_status batch_capture(lbm_batch* b, lbm_batch::Graph& G) {
     return LBM_OK;
 }
 
+// Whether the step of every active instance can run as gang launches: its
+// particles (if any) are held fixed or moved by the DEM in one block.
+bool batch_gang_ok(const lbm_batch* b) {
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        if (!b->active[i]) continue;
+        const lbm_ctx* c = b->ctx[i];
+        if (c->P.n == 0) continue;
+        if (c->dem.fixed_particles == 2) return false;
+        if (c->dem.fixed_particles == 0 && c->P.n > DEM_ONE_BLOCK_MAX) return false;
+    }
+    return true;
+}
+
+// The parameter tables of one kind of gang launch: one block per instance
+// that takes part, the prefix sums of their block counts.
+struct GangTable {
+    std::vector<unsigned char> bytes;
+    std::vector<int> off{0};
+    size_t elem = 0;
+    int count() const { return (int)off.size() - 1; }
+    int blocks() const { return off.back(); }
+    void add(const void* params, int blocks) {
+        const size_t at = bytes.size();
+        bytes.resize(at + elem);
+        std::memcpy(bytes.data() + at, params, elem);
+        off.push_back(off.back() + blocks);
+    }
+};
+
+// Capture one step of every active instance as gang launches (each per-step
+// kernel once for all instances; the dense kernels in one persistent launch,
+// the DEM steps in one launch), in the order of a single instance's step:
+// fluid body force and missing links, neighbour bins and lists, dense kernel,
+// force finalisation, DEM, counters, tile scatter, mapping, refill.
+lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
+    const size_t n = b->ctx.size();
+    const size_t ab = batch_args_bytes(b->storage);
+    const size_t db = dem_batch_entry_bytes();
+    const std::vector<int4> items = batch_items(b);
+    G.n_items = (int)items.size();
+    std::vector<unsigned char> host(ab * n, 0), host_dem(db * n, 0);
+    GangTable bc, zb, bins, nbr, fin, zc, scat, map, ref;
+    bc.elem = bc_args_bytes();
+    zb.elem = zc.elem = sizeof(ZeroSpan);
+    bins.elem = nbr.elem = sizeof(DemParams);
+    fin.elem = sizeof(FinalizeParams);
+    scat.elem = map.elem = sizeof(MapParams);
+    ref.elem = sizeof(RefillParams);
+    G.launches.assign(n, 0);
+    G.hcur_after.assign(n, 0);
+    for (size_t i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        G.hcur_after[i] = c->hcur;
+        if (!b->active[i]) continue;
+        const lbm_dem& d = c->dem;
+        const int np = c->P.n;
+        const bool move = np > 0 && d.fixed_particles != 1;
+        const bool dem = move && d.fixed_particles == 0;
+        LbmStepParams lp;
+        fill_step_params(c, lp);
+        std::vector<unsigned char> bca(bc.elem, 0);
+        fill_bc_args(lp, bca.data());
+        bc.add(bca.data(), lp.missing_links ? 4 : 1);
+        fill_batch_args(lp, batch_tile_bx(b, (int)i), batch_zchunk(b, (int)i), &host[ab * i]);
+        DemParams dp = dem_params(c);
+        if (dem) {
+            const ZeroSpan z{c->P.bin_count, dp.nbins[0] * dp.nbins[1] * dp.nbins[2], 0};
+            zb.add(&z, (z.words + 127) / 128 < 64 ? (z.words + 127) / 128 : 64);
+            bins.add(&dp, (np + 127) / 128);
+            nbr.add(&dp, (32 * np + 127) / 128);
+        }
+        if (np > 0) {
+            FinalizeParams fp{};
+            fp.P = c->P;
+            fp.use_fixed = c->storage != LBM_STORE_F64;
+            fp.first_step = 0;
+            fp.averaging = d.force_averaging;
+            fin.add(&fp, (np + 127) / 128);
+        }
+        if (dem) {
+            fill_dem_batch_entry(dp, c->hcur, d.n_sub, &host_dem[db * G.n_dem]);
+            G.n_dem += 1;
+            if (d.n_sub & 1) G.hcur_after[i] = 1 - c->hcur;
+        }
+        if (move) {
+            // n_solid and the missing-link and refill counts (16 bytes)
+            const ZeroSpan z{reinterpret_cast<int*>(c->n_solid), 4, 0};
+            zc.add(&z, 1);
+            const MapParams mp = map_params(c);
+            scat.add(&mp, (32 * np + 127) / 128);
+            map.add(&mp, (int)c->ntiles);
+            RefillParams rp{};
+            rp.storage = c->storage;
+            rp.f = c->f[1 - c->cur];
+            rp.flags = c->flags;
+            rp.list_owner = c->refill_owner;
+            rp.g = c->g;
+            rp.P = c->P;
+            rp.list = c->refill_list;
+            rp.count = c->refill_count;
+            rp.cap = c->refill_cap;
+            rp.s_nu = 1.0 / c->relax.tau;
+            rp.accel = c->accel;
+            ref.add(&rp, 4);
+        }
+    }
+    // one device buffer: the tables, then their offsets (16-byte aligned pieces)
+    GangTable* tabs[9] = {&bc, &zb, &bins, &nbr, &fin, &zc, &scat, &map, &ref};
+    size_t total = 0;
+    size_t at_tab[9], at_off[9];
+    for (int k = 0; k < 9; ++k) {
+        at_tab[k] = total;
+        total += (tabs[k]->bytes.size() + 15) & ~size_t(15);
+        at_off[k] = total;
+        total += (sizeof(int) * tabs[k]->off.size() + 15) & ~size_t(15);
+    }
+    BCK(cudaMalloc(&G.d_args, ab * n));
+    BCK(cudaMalloc(&G.d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
+    BCK(cudaMalloc(&G.d_dem, db * n));
+    BCK(cudaMalloc(&G.d_gang, std::max<size_t>(total, 16)));
+    std::vector<unsigned char> gang(std::max<size_t>(total, 16), 0);
+    for (int k = 0; k < 9; ++k) {
+        if (!tabs[k]->bytes.empty()) std::memcpy(gang.data() + at_tab[k], tabs[k]->bytes.data(), tabs[k]->bytes.size());
+        std::memcpy(gang.data() + at_off[k], tabs[k]->off.data(), sizeof(int) * tabs[k]->off.size());
+    }
+    char* dg = static_cast<char*>(G.d_gang);
+    auto T = [&](int k) { return static_cast<const void*>(dg + at_tab[k]); };
+    auto O = [&](int k) { return reinterpret_cast<const int*>(dg + at_off[k]); };
+    cudaGraph_t g = nullptr;
+    const cudaStream_t cs = b->capture;
+    int launches = 0;
+    auto gl = [&](int k) { return tabs[k]->count() > 0 ? 1 : 0; };
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        launch_boundary_gang(b->storage, T(0), O(0), bc.count(), bc.blocks(), BC_ACCEL | BC_LINKS, cs);
+        launch_gang(GANG_ZERO, T(1), O(1), zb.count(), zb.blocks(), cs);
+        launch_gang(GANG_BINS, T(2), O(2), bins.count(), bins.blocks(), cs);
+        launch_gang(GANG_NEIGHBOURS, T(3), O(3), nbr.count(), nbr.blocks(), cs);
+        launches += gl(0) + gl(1) + gl(2) + gl(3);
+        if (G.n_items > 0) {
+            const int bps = b->blocks_per_sm > 0 ? b->blocks_per_sm : (b->storage == 0 ? 2 : 4);
+            const int grid = std::min(G.n_items, bps * b->num_sms);
+            launch_stream_collide_batch(b->storage, G.d_args, G.d_items, G.n_items, grid, cs);
+            launches += 1;
+        }
+        launch_gang(GANG_FINALIZE, T(4), O(4), fin.count(), fin.blocks(), cs);
+        launches += gl(4);
+        if (G.n_dem > 0) {
+            launch_dem_step_batch(G.d_dem, G.n_dem, b->storage != LBM_STORE_F64, cs);
+            launches += 1;
+        }
+        launch_gang(GANG_ZERO, T(5), O(5), zc.count(), zc.blocks(), cs);
+        launch_map_gang(GANG_SCATTER, b->storage, T(6), O(6), scat.count(), scat.blocks(), cs);
+        launch_map_gang(GANG_MAP, b->storage, T(7), O(7), map.count(), map.blocks(), cs);
+        launch_map_gang(GANG_REFILL, b->storage, T(8), O(8), ref.count(), ref.blocks(), cs);
+        launches += gl(5) + gl(6) + gl(7) + gl(8);
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    G.gang_launches = launches;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    BCK(e);
+    BCK(cudaMemcpy(G.d_args, host.data(), host.size(), cudaMemcpyHostToDevice));
+    if (G.n_items > 0)
+        BCK(cudaMemcpy(G.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    if (G.n_dem > 0) BCK(cudaMemcpy(G.d_dem, host_dem.data(), db * G.n_dem, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(G.d_gang, gang.data(), gang.size(), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 }  // namespace
 
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* cuda_stream, lbm_batch** out) {
@@ -1692,7 +1883,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
         if (it == b->graphs.end()) {
             lbm_batch::Graph G;
             const auto t0 = std::chrono::steady_clock::now();
-            lbm_status st = batch_capture(b, G);
+            lbm_status st = batch_gang_ok(b) ? batch_capture_gang(b, G) : batch_capture(b, G);
             b->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             b->captures += 1;
             if (st != LBM_OK) {
@@ -1700,13 +1891,14 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
                 if (G.d_args) cudaFree(G.d_args);
                 if (G.d_items) cudaFree(G.d_items);
                 if (G.d_dem) cudaFree(G.d_dem);
+                if (G.d_gang) cudaFree(G.d_gang);
                 return st;
             }
             it = b->graphs.emplace(key, G).first;
         }
         const lbm_batch::Graph& G = it->second;
         BCK(cudaGraphLaunch(G.exec, b->stream));
-        b->launches += (G.n_items > 0 ? 1 : 0) + (G.n_dem > 0 ? 1 : 0);
+        b->launches += G.gang_launches > 0 ? G.gang_launches : (G.n_items > 0 ? 1 : 0) + (G.n_dem > 0 ? 1 : 0);
         for (size_t i = 0; i < b->ctx.size(); ++i) {
             if (!b->active[i]) continue;
             lbm_ctx* c = b->ctx[i];

@@ -16,7 +16,10 @@
 // The particle links themselves (CLI condition of Eq. (14), momentum exchange
 // of Eq. (15)) are handled inside the dense stream/collide kernel, which finds
 // them from the marker that solid cells hold in their PDF slots.
+#include <cstring>
+
 #include "common.cuh"
+#include "gang.cuh"
 #include "launch.h"
 #include "links.cuh"
 
@@ -121,10 +124,11 @@ __device__ __forceinline__ void missing_links(const BcArgs<S>& a, long long idx,
 // mode BC_ACCEL: one thread forms the fluid body force of the step; mode
 // BC_LINKS: the missing-link terms 2 w_q c_q of Sec. 2.2 and their torques, one
 // thread per listed solid cell, committed per warp
+// (block bx of a grid of gx blocks)
 template <typename S>
-__global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mode) {
+__device__ __forceinline__ void boundary_body(const BcArgs<S>& a, int mode, int bx, int gx) {
     using T = typename Store<S>::T;
-    if ((mode & BC_ACCEL) && blockIdx.x == 0 && threadIdx.x == 0) {
+    if ((mode & BC_ACCEL) && bx == 0 && threadIdx.x == 0) {
         double acc3[3] = {a.a_user[0], a.a_user[1], a.a_user[2]};
         if (a.counterforce) {
             const double nf = (double)(a.g.ncells - (long long)(*a.n_solid));
@@ -138,8 +142,8 @@ __global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mo
     if (!(mode & BC_LINKS) || !a.missing_links) return;
     const Sinks sk{a.acc_d, a.acc_i, a.acc_k, a.status};
     const int mcount = min(*a.miss_count, a.miss_cap);
-    const int stride = (int)(gridDim.x * blockDim.x);
-    for (int base = (int)(blockIdx.x * blockDim.x); base < mcount; base += stride) {
+    const int stride = (int)(gx * blockDim.x);
+    for (int base = (int)(bx * blockDim.x); base < mcount; base += stride) {
         const int k = base + threadIdx.x;
         Acc<T> acc;
         if (k < mcount) missing_links<S, T>(a, (long long)a.miss[k], acc, sk);
@@ -148,8 +152,21 @@ __global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mo
 }
 
 template <typename S>
-void launch_boundary_t(const LbmStepParams& p, cudaStream_t st, int mode) {
-    BcArgs<S> b;
+__global__ void __launch_bounds__(128) boundary_kernel(const BcArgs<S> a, int mode) {
+    boundary_body<S>(a, mode, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) boundary_gang_kernel(const BcArgs<S>* __restrict__ table,
+                                                            const int* __restrict__ off, int n, int mode) {
+    __shared__ __align__(16) BcArgs<S> a;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, a);
+    boundary_body<S>(a, mode, (int)blockIdx.x - off[i], off[i + 1] - off[i]);
+}
+
+template <typename S>
+void fill_bc_args_t(const LbmStepParams& p, BcArgs<S>& b) {
     b.flags = p.flags;
     b.owner = p.owner;
     b.g = p.g;
@@ -174,8 +191,36 @@ void launch_boundary_t(const LbmStepParams& p, cudaStream_t st, int mode) {
     b.n_solid = p.n_solid;
     b.accel_d = p.accel_d;
     b.accel_f = p.accel_f;
+}
+
+template <typename S>
+void launch_boundary_t(const LbmStepParams& p, cudaStream_t st, int mode) {
+    BcArgs<S> b;
+    fill_bc_args_t<S>(p, b);
     const int blocks = (mode & BC_LINKS) && p.missing_links ? 8 * (p.num_sms > 0 ? p.num_sms : 1) : 1;
     boundary_kernel<S><<<blocks, 128, 0, st>>>(b, mode);
+}
+
+size_t bc_args_bytes() { return sizeof(BcArgs<float>); }
+
+void fill_bc_args(const LbmStepParams& p, void* out) {
+    // the argument block does not depend on the storage format
+    static_assert(sizeof(BcArgs<float>) == sizeof(BcArgs<double>), "one layout for all formats");
+    BcArgs<float> b;
+    std::memset(&b, 0, sizeof(b));
+    fill_bc_args_t<float>(p, b);
+    std::memcpy(out, &b, sizeof(b));
+}
+
+void launch_boundary_gang(int storage, const void* table, const int* off, int n, int blocks, int mode,
+                          cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return;
+    switch (storage) {
+        case 0: boundary_gang_kernel<double><<<blocks, 128, 0, st>>>(static_cast<const BcArgs<double>*>(table), off, n, mode); break;
+        case 1: boundary_gang_kernel<float><<<blocks, 128, 0, st>>>(static_cast<const BcArgs<float>*>(table), off, n, mode); break;
+        case 2: boundary_gang_kernel<__half><<<blocks, 128, 0, st>>>(static_cast<const BcArgs<__half>*>(table), off, n, mode); break;
+        default: boundary_gang_kernel<__nv_bfloat16><<<blocks, 128, 0, st>>>(static_cast<const BcArgs<__nv_bfloat16>*>(table), off, n, mode); break;
+    }
 }
 
 void launch_boundary(const LbmStepParams& p, cudaStream_t st, int mode) {

@@ -17,6 +17,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "gang.cuh"
 #include "launch.h"
 
 namespace lbmdem {
@@ -117,8 +118,8 @@ void launch_view_update(const Particles& P, cudaStream_t st) {
 // per particle: the step's hydrodynamic force and torque (Eqs. (16)-(17)) from
 // the float64 or fixed-point link sums and the exact integer missing-link
 // sums, their two-step average (Sec. 4.2), and the accumulators cleared
-__global__ void finalize_kernel(const FinalizeParams p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void finalize_body(const FinalizeParams& p, int bx) {
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
     double exact[6] = {0, 0, 0, 0, 0, 0};
     if (p.use_fixed) {
@@ -162,6 +163,15 @@ __global__ void finalize_kernel(const FinalizeParams p) {
     }
 }
 
+__global__ void finalize_kernel(const FinalizeParams p) { finalize_body(p, (int)blockIdx.x); }
+
+__global__ void finalize_gang_kernel(const FinalizeParams* __restrict__ table, const int* __restrict__ off, int n) {
+    __shared__ __align__(16) FinalizeParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    finalize_body(sp, (int)blockIdx.x - off[i]);
+}
+
 void launch_finalize(const FinalizeParams& p, cudaStream_t st) {
     if (p.P.n == 0) return;
     finalize_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
@@ -176,8 +186,8 @@ __device__ __forceinline__ int bin_coord(float x, float bs, int nb) {
 
 // particles into uniform bins no smaller than the largest interaction reach,
 // for the neighbour search of the lubrication and contact pairs (Secs. 3.1, 4.1)
-__global__ void bin_fill_kernel(const DemParams p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bin_fill_body(const DemParams& p, int bx) {
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= p.P.n) return;
     int b[3];
     for (int d = 0; d < 3; ++d) b[d] = bin_coord(p.P.xf[3 * i + d], (float)p.binsize[d], p.nbins[d]);
@@ -193,6 +203,15 @@ __global__ void bin_fill_kernel(const DemParams p) {
     else atomicOr(p.status, ST_BIN_OVERFLOW);
 }
 
+__global__ void bin_fill_kernel(const DemParams p) { bin_fill_body(p, (int)blockIdx.x); }
+
+__global__ void bin_fill_gang_kernel(const DemParams* __restrict__ table, const int* __restrict__ off, int n) {
+    __shared__ __align__(16) DemParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    bin_fill_body(sp, (int)blockIdx.x - off[i]);
+}
+
 void launch_bins(const DemParams& p, cudaStream_t st) {
     if (p.P.n == 0) return;
     bin_fill_kernel<<<(p.P.n + 127) / 128, 128, 0, st>>>(p);
@@ -200,9 +219,9 @@ void launch_bins(const DemParams& p, cudaStream_t st) {
 
 // one warp per particle: lane k tests entry k of each of the 27 bins around it
 // (a bin holds at most BIN_CAP = 32 particles); hits are appended in bin order
-__global__ void neighbour_kernel(const DemParams p) {
+__device__ __forceinline__ void neighbour_body(const DemParams& p, int bx) {
     static_assert(BIN_CAP == 32, "one lane per bin entry");
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = (bx * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= p.P.n) return;   // warp-uniform
     const unsigned FULL = 0xffffffffu;
@@ -253,6 +272,15 @@ __global__ void neighbour_kernel(const DemParams p) {
         }
         p.P.nbr_count[i] = cnt;
     }
+}
+
+__global__ void neighbour_kernel(const DemParams p) { neighbour_body(p, (int)blockIdx.x); }
+
+__global__ void neighbour_gang_kernel(const DemParams* __restrict__ table, const int* __restrict__ off, int n) {
+    __shared__ __align__(16) DemParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    neighbour_body(sp, (int)blockIdx.x - off[i]);
 }
 
 void launch_neighbours(const DemParams& p, cudaStream_t st) {
@@ -944,6 +972,32 @@ __global__ void fp_split_kernel(const double* __restrict__ fp, double* __restric
     const long long i = k / 6;
     const int c = (int)(k - 6 * i);
     out[(c < 3 ? 0 : 3LL * n) + 3 * i + (c < 3 ? c : c - 3)] = fp[k];
+}
+
+// words set to zero, per instance a span (the counters a step starts from)
+__global__ void zero_gang_kernel(const ZeroSpan* __restrict__ table, const int* __restrict__ off, int n) {
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    const ZeroSpan z = table[i];
+    const int bx = (int)blockIdx.x - off[i], gx = off[i + 1] - off[i];
+    for (int k = bx * blockDim.x + threadIdx.x; k < z.words; k += gx * blockDim.x) z.p[k] = 0;
+}
+
+void launch_gang(int kind, const void* table, const int* off, int n, int blocks, cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return;
+    switch (kind) {
+        case GANG_FINALIZE:
+            finalize_gang_kernel<<<blocks, 128, 0, st>>>(static_cast<const FinalizeParams*>(table), off, n);
+            break;
+        case GANG_BINS:
+            bin_fill_gang_kernel<<<blocks, 128, 0, st>>>(static_cast<const DemParams*>(table), off, n);
+            break;
+        case GANG_NEIGHBOURS:
+            neighbour_gang_kernel<<<blocks, 128, 0, st>>>(static_cast<const DemParams*>(table), off, n);
+            break;
+        default:
+            zero_gang_kernel<<<blocks, 128, 0, st>>>(static_cast<const ZeroSpan*>(table), off, n);
+            break;
+    }
 }
 
 void launch_fp_split(const double* fp, double* out, int n, cudaStream_t st) {

@@ -170,6 +170,22 @@ constexpr int DEM_ONE_BLOCK_MAX = 32;
 void launch_dem_step_one_block(const DemParams& p, int hcur, int n_sub, cudaStream_t st);
 void launch_state_copy(const Particles& P, cudaStream_t st);
 void launch_fp_split(const double* fp, double* out, int n, cudaStream_t st);
+
+// Gang launches (gang.cuh): one launch of a per-step kernel for many
+// instances; table holds n parameter blocks in device memory, off the n + 1
+// prefix sums of their block counts (blocks = off[n]).
+enum { GANG_FINALIZE = 1, GANG_BINS, GANG_NEIGHBOURS, GANG_ZERO, GANG_SCATTER, GANG_MAP, GANG_REFILL };
+struct ZeroSpan {
+    int* p;        // words set to zero
+    int words;
+    int pad;
+};
+void launch_gang(int kind, const void* table, const int* off, int n, int blocks, cudaStream_t st);
+void launch_map_gang(int kind, int storage, const void* table, const int* off, int n, int blocks, cudaStream_t st);
+size_t bc_args_bytes();
+void fill_bc_args(const LbmStepParams& p, void* out);
+void launch_boundary_gang(int storage, const void* table, const int* off, int n, int blocks, int mode,
+                          cudaStream_t st);
 void launch_view_update(const Particles& P, cudaStream_t st);
 void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st);
 

@@ -17,6 +17,7 @@
 // next step reads. A cell that turns solid gets the NaN marker in all its PDF
 // slots of both buffers.
 #include "common.cuh"
+#include "gang.cuh"
 #include "launch.h"
 
 // minimum resident mapping blocks per SM (a register cap)
@@ -70,8 +71,8 @@ __device__ int axis_tiles(int np, const int (&a)[2], const int (&b)[2], int tsiz
 }
 
 // one warp per particle; the lanes share out the tiles of its box
-__global__ void tile_scatter_kernel(const MapParams p) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void tile_scatter_body(const MapParams& p, int bx) {
+    const int i = (bx * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= p.P.n) return;   // warp-uniform
     const double r = p.P.R[i] + fmax(p.shell_width, 1.4142135623730951) + 0.02;
@@ -101,6 +102,15 @@ __global__ void tile_scatter_kernel(const MapParams p) {
         if (slot < TILE_CAP) p.tile_list[t * TILE_CAP + slot] = i;
         else atomicOr(p.status, ST_TILE_OVERFLOW);
     }
+}
+
+__global__ void tile_scatter_kernel(const MapParams p) { tile_scatter_body(p, (int)blockIdx.x); }
+
+__global__ void tile_scatter_gang_kernel(const MapParams* __restrict__ table, const int* __restrict__ off, int n) {
+    __shared__ __align__(16) MapParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    tile_scatter_body(sp, (int)blockIdx.x - off[i]);
 }
 
 void launch_tile_scatter(const MapParams& p, cudaStream_t st) {
@@ -162,7 +172,8 @@ __device__ __forceinline__ float short_axis_image(float n, float g, int L) {
 // integer part formed first, so no float32 intermediate is larger than the
 // offset itself. Each warp first drops the candidates that cannot reach its
 // brick.
-__global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __grid_constant__ MapParams p) {
+// (tile bx, by, bz of the box)
+__device__ __forceinline__ void map_body(const MapParams& p, int bx, int by, int bz) {
     static_assert(TILE_X == 32 && TILE_Y == 4, "four 8x4 column bricks per tile");
     __shared__ float4 cn[TILE_CAP];
     __shared__ float4 ca[TILE_CAP];
@@ -170,10 +181,10 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     __shared__ unsigned int s_cnt[4];          // per warp: missing-link cells
     __shared__ unsigned int s_solid[4];
     __shared__ unsigned int s_base;
-    const long long t = ((long long)blockIdx.z * p.ntile[1] + blockIdx.y) * p.ntile[0] + blockIdx.x;
+    const long long t = ((long long)bz * p.ntile[1] + by) * p.ntile[0] + bx;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lx = 8 * warp + (lane & 7), ly = lane >> 3;
-    const int org[3] = {(int)blockIdx.x * TILE_X, (int)blockIdx.y * TILE_Y, (int)blockIdx.z * TILE_Z};
+    const int org[3] = {bx * TILE_X, by * TILE_Y, bz * TILE_Z};
     const int x = org[0] + lx, y = org[1] + ly;
     const int nx = p.g.n[0], ny = p.g.n[1], nz = p.g.n[2];
     const long long plane = (long long)nx * ny;
@@ -386,6 +397,21 @@ __global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __gr
     }
 }
 
+__global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS) map_kernel(const __grid_constant__ MapParams p) {
+    map_body(p, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+}
+
+// instance i's tiles are its blocks off[i] .. off[i + 1] - 1, x fastest
+__global__ void __launch_bounds__(128, LBM_MAP_MIN_BLOCKS / 2)
+    map_gang_kernel(const MapParams* __restrict__ table, const int* __restrict__ off, int n) {
+    __shared__ __align__(16) MapParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    const int b = (int)blockIdx.x - off[i];
+    const int t0 = sp.ntile[0], t1 = sp.ntile[1];
+    map_body(sp, b % t0, (b / t0) % t1, b / (t0 * t1));
+}
+
 void launch_map(const MapParams& p, cudaStream_t st) {
     dim3 grid(p.ntile[0], p.ntile[1], p.ntile[2]);
     map_kernel<<<grid, TILE_X * TILE_Y, 0, st>>>(p);
@@ -409,7 +435,7 @@ void launch_solid_markers(const MapParams& p, cudaStream_t st) {
 // densities and shares the axis neighbours' velocities, and lane q (0..18)
 // writes f_q of Eq. (18).
 template <typename S>
-__global__ void __launch_bounds__(128) refill_kernel(const RefillParams p) {
+__device__ __forceinline__ void refill_body(const RefillParams& p, int bx, int gx) {
     using T = typename Store<S>::T;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -420,8 +446,8 @@ __global__ void __launch_bounds__(128) refill_kernel(const RefillParams p) {
     const int nx = p.g.n[0], ny = p.g.n[1];
     const T ax = (T)p.accel[0], ay = (T)p.accel[1], az = (T)p.accel[2];
     constexpr unsigned long long PX = pack_dirs(0), PY = pack_dirs(1), PZ = pack_dirs(2);
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < count; k += warps) {   // warp-uniform
+    const int warps = gx * (blockDim.x >> 5);
+    for (int k = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); k < count; k += warps) {   // warp-uniform
         const long long idx = p.list[k];
         const int x = (int)(idx % nx);
         const int y = (int)((idx / nx) % ny);
@@ -520,6 +546,37 @@ __global__ void __launch_bounds__(128) refill_kernel(const RefillParams p) {
             // f_q - w_q written without forming f_q: w_q (rho_bar - 1) + ...
             const T dfq = w * (drb + T(3) * rb * cu + T(4.5) * second);
             Store<S>::store(fw + (long long)q * N + idx, dfq);
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) refill_kernel(const RefillParams p) {
+    refill_body<S>(p, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) refill_gang_kernel(const RefillParams* __restrict__ table,
+                                                          const int* __restrict__ off, int n) {
+    __shared__ __align__(16) RefillParams sp;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, sp);
+    refill_body<S>(sp, (int)blockIdx.x - off[i], off[i + 1] - off[i]);
+}
+
+void launch_map_gang(int kind, int storage, const void* table, const int* off, int n, int blocks, cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return;
+    if (kind == GANG_SCATTER) {
+        tile_scatter_gang_kernel<<<blocks, 128, 0, st>>>(static_cast<const MapParams*>(table), off, n);
+    } else if (kind == GANG_MAP) {
+        map_gang_kernel<<<blocks, TILE_X * TILE_Y, 0, st>>>(static_cast<const MapParams*>(table), off, n);
+    } else {
+        const RefillParams* t = static_cast<const RefillParams*>(table);
+        switch (storage) {
+            case 0: refill_gang_kernel<double><<<blocks, 128, 0, st>>>(t, off, n); break;
+            case 1: refill_gang_kernel<float><<<blocks, 128, 0, st>>>(t, off, n); break;
+            case 2: refill_gang_kernel<__half><<<blocks, 128, 0, st>>>(t, off, n); break;
+            default: refill_gang_kernel<__nv_bfloat16><<<blocks, 128, 0, st>>>(t, off, n); break;
         }
     }
 }

@@ -29,7 +29,7 @@ EXPORTS = ('lbm_default_params', 'lbm_required_bytes', 'lbm_create', 'lbm_create
            'lbm_set_particle_velocity',
            'lbm_set_motion', 'lbm_checkpoint_bytes', 'lbm_save', 'lbm_restore', 'lbm_sample_density',
            'lbm_get_fields',
-           'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_profile',
+           'lbm_get_owner', 'lbm_get_pdfs', 'lbm_set_pdfs', 'lbm_sync', 'lbm_set_stream', 'lbm_profile',
            'lbm_profile_read', 'lbm_map_spheres_noalloc', 'lbm_fp64_fma_rate', 'lbm_batch_create',
            'lbm_batch_set_launch', 'lbm_batch_set_active', 'lbm_batch_step', 'lbm_batch_sync',
            'lbm_batch_launch_count', 'lbm_batch_capture_stats', 'lbm_batch_last_error', 'lbm_batch_destroy', 'lbm_launch_count',
@@ -100,6 +100,7 @@ def load_library(path=LIB_PATH):
     lib.lbm_get_pdfs.argtypes = [c_void_p, dp]
     lib.lbm_set_pdfs.argtypes = [c_void_p, dp]
     lib.lbm_sync.argtypes = [c_void_p]
+    lib.lbm_set_stream.argtypes = [c_void_p, c_void_p]
     lib.lbm_profile.argtypes = [c_void_p, c_int]
     lib.lbm_profile_read.argtypes = [c_void_p, dp, P(ctypes.c_longlong)]
     lib.lbm_map_spheres_noalloc.argtypes = [P(LbmGrid), c_double, c_int, c_void_p, c_void_p, c_void_p,
@@ -272,6 +273,14 @@ def lbm_step(ctx, n_steps=1):
 
 def lbm_sync(ctx):
     _check(load_library().lbm_sync(ctx.handle), ctx.handle)
+
+
+def lbm_set_stream(ctx, stream=None):
+    """Queue the context's later work on `stream` (a torch.cuda.Stream; None:
+    PyTorch's current stream) after the work queued so far."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().lbm_set_stream(ctx.handle, c_void_p(st.cuda_stream)), ctx.handle)
 
 
 def lbm_get_particle_state(ctx, out=None):

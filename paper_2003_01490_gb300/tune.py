@@ -108,7 +108,9 @@ def tune_batch(batch, storage, steps=6, use_cache=True, restore=False, cands=Non
 
 
 def make_groups(ctxs, G):
-    """G batches over the contexts (round robin), each on its own stream."""
+    """G batches over the contexts (round robin), each on its own stream; the
+    contexts of a batch move to its stream first, so that no stream they
+    share orders one batch after another."""
     import torch
     groups = []
     for g in range(G):
@@ -116,6 +118,8 @@ def make_groups(ctxs, G):
         if not part:
             continue
         st = torch.cuda.Stream()
+        for c in part:
+            L.lbm_set_stream(c, st)
         groups.append((L.lbm_batch_create(part, stream=st), st))
     return groups
 

@@ -131,6 +131,7 @@ def test_calls_on_a_null_context_fail_cleanly(lib):
         'lbm_add_spheres': (None, 0, dp, dp, dp, dp, dp, None),
         'lbm_step': (None, 1),
         'lbm_sync': (None,),
+        'lbm_set_stream': (None, None),
         'lbm_get_particle_state': (None, 0, dp, dp, dp, dp, dp, ctypes.byref(n)),
         'lbm_get_particle_state_async': (None, 0, dp, dp, dp, dp, dp, ctypes.byref(n)),
         'lbm_set_particle_velocity': (None, 0, dp, dp),

@@ -82,13 +82,15 @@ def test_batch_equals_each_instance_alone(L, storage):
         L.lbm_batch_set_launch(b, i, bx, zc, 4)
     L.lbm_batch_step(b, steps - 1)
     L.lbm_batch_sync(b)
-    # per step one persistent dense launch and one launch of the DEM steps of
-    # all instances (each has at most 32 particles)
-    assert L.lbm_batch_launch_count(b) == 2 * (steps - 1)
     for i, ctx in enumerate(ctxs):
         got = state(L, ctx)
         for g, s_ in zip(got, solo[i]):
             assert np.array_equal(np.nan_to_num(g, nan=7.0), np.nan_to_num(s_, nan=7.0)), i
+    # every instance has at most 32 particles, so each step is 11 gang
+    # launches for all instances together: body force and missing links,
+    # bin reset, bins, neighbour lists, the persistent dense launch, force
+    # finalisation, the DEM steps, counter reset, tile scatter, mapping, refill
+    assert L.lbm_batch_launch_count(b) == 11 * (steps - 1)
 
 
 def test_float64_instance_in_a_batch_matches_the_oracle(L):
@@ -215,5 +217,40 @@ def test_two_batches_on_their_own_streams_equal_each_instance_alone(L):
     for b in batches:
         L.lbm_batch_sync(b)
     for i, ctx in enumerate(ctxs):      # read on the contexts' stream: ordered after the batches
+        for g, s_ in zip(state(L, ctx), solo[i]):
+            assert np.array_equal(np.nan_to_num(g, nan=7.0), np.nan_to_num(s_, nan=7.0)), i
+
+
+def test_contexts_moved_to_their_batch_streams_run_concurrently_and_equal_each_alone(L):
+    # tune.make_groups moves each batch's contexts onto its stream
+    # (lbm_set_stream), so the batches share no stream; the results stay those
+    # of each instance alone, and the contexts' later work follows the batches
+    import torch
+    from paper_2003_01490_gb300 import tune
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cases = [sphere_wall_case(32, 8.0, 4.0, 0.6, 'f32', 31), sphere_wall_case(40, 10.0, 2.0, 0.7, 'f32', 32),
+             sphere_wall_case(48, 12.0, 3.0, 0.6, 'f32', 33), sphere_wall_case(64, 14.0, 5.0, 0.65, 'f32', 34)]
+    steps = 25
+    solo = []
+    for c in cases:
+        ctx = build_gpu(c)
+        L.lbm_step(ctx, steps + 3)
+        solo.append(state(L, ctx))
+        del ctx
+    ctxs = [build_gpu(c) for c in cases]
+    for ctx in ctxs:
+        L.lbm_step(ctx, 1)
+    groups = tune.make_groups(ctxs, 2)
+    for g, (b, _) in enumerate(groups):
+        for i, c in enumerate(cases[g::2]):
+            bx, zc = solo_launch(c['shape'], sms)
+            L.lbm_batch_set_launch(b, i, bx, zc, 2)
+    for b, _ in groups:
+        L.lbm_batch_step(b, steps - 1)
+    for ctx in ctxs:                    # plain steps on the contexts' new streams
+        L.lbm_step(ctx, 3)
+    for b, _ in groups:
+        L.lbm_batch_sync(b)
+    for i, ctx in enumerate(ctxs):
         for g, s_ in zip(state(L, ctx), solo[i]):
             assert np.array_equal(np.nan_to_num(g, nan=7.0), np.nan_to_num(s_, nan=7.0)), i
