@@ -76,7 +76,10 @@ constexpr int ST_UNSTABLE = 1, ST_TILE_OVERFLOW = 2, ST_NBR_OVERFLOW = 4, ST_BIN
               ST_FIXED_OVERFLOW = 128, ST_TIMEOUT = 256;
 
 // capacities of the fixed-size device lists
-constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;   // mapping tile (512 cells)
+#ifndef LBM_TILE_Z
+#define LBM_TILE_Z 4
+#endif
+constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = LBM_TILE_Z;   // mapping tile (512 cells at depth 4)
 constexpr int TILE_CAP = 64;                          // candidate particles per tile
 constexpr int BIN_CAP = 32;                           // particles per DEM bin
 constexpr int NBR_CAP = 32;                           // neighbour candidates per particle

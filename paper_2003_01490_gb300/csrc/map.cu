@@ -16,6 +16,8 @@
 // missing links) go to the missing-link list that the boundary kernel of the
 // next step reads. A cell that turns solid gets the NaN marker in all its PDF
 // slots of both buffers.
+#include <type_traits>
+
 #include "common.cuh"
 #include "gang.cuh"
 #include "launch.h"
@@ -191,10 +193,12 @@ __device__ __forceinline__ void map_body(const MapParams& p, int bx, int by, int
     const bool valid_xy = x < nx && y < ny;
     const long long idx0 = (long long)org[2] * plane + (long long)y * nx + x;
     // previous flags of the column, loaded before the candidate tests
-    unsigned old4 = 0;
+    static_assert(TILE_Z <= 8, "previous flags of a column packed in one word");
+    using ZWord = typename std::conditional<(TILE_Z > 4), unsigned long long, unsigned>::type;
+    ZWord old4 = 0;
 #pragma unroll
     for (int j = 0; j < TILE_Z; ++j)
-        if (valid_xy && org[2] + j < nz) old4 |= (unsigned)p.flags[idx0 + j * plane] << (8 * j);
+        if (valid_xy && org[2] + j < nz) old4 |= (ZWord)p.flags[idx0 + j * plane] << (8 * j);
     const int c = p.tile_count[t];
     const int ncand = c < TILE_CAP ? c : TILE_CAP;
     if (tid < ncand) {
