@@ -175,14 +175,16 @@ lbm_status lbm_get_particle_state(lbm_ctx *ctx, int n_cap, double *pos, double *
                                   double *omega, double *force_hyd, double *torque_hyd,
                                   int *n_out);
 
-/* The same read-out without waiting: queues the copies on the context's stream
- * (after every step queued so far) and returns. The values are in the buffers
- * once lbm_sync() or another synchronising call returns; the buffers must stay
- * valid until then, and page-locked buffers let the copies run while the host
- * queues further steps. Reading in this way after every step of a loop costs
- * no host wait per step. Device errors of the steps are reported by
- * lbm_sync(). force_hyd / torque_hyd pass through the context's scratch buffer
- * (LBM_ERR_CAPACITY if 6 n doubles exceed it; it holds 4 min(cells, 2^22)).
+/* The same read-out without waiting: queues a device snapshot of the state
+ * after every step queued so far (on the context's stream) and its copy into
+ * the host buffers (on a read-out stream of the context, so the copy overlaps
+ * the steps queued after it), and returns. The values are in the buffers once
+ * lbm_sync() returns; the buffers must stay valid until then, and must be
+ * page-locked for the copies to run asynchronously. A later call's snapshot
+ * waits for the previous call's copies. Reading in this way after every step
+ * of a loop costs no host wait per step. The first call allocates the
+ * snapshot (15 doubles per particle of max_particles). Device errors of the
+ * steps are reported by lbm_sync().
  * Errors: LBM_ERR_INVALID (NULL ctx, n_cap too small), LBM_ERR_CUDA. */
 lbm_status lbm_get_particle_state_async(lbm_ctx *ctx, int n_cap, double *pos, double *vel,
                                         double *omega, double *force_hyd, double *torque_hyd,

@@ -66,6 +66,12 @@ struct lbm_ctx {
     // second stream for work beside the dense kernel, with its fork/join events
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // asynchronous particle-state read-out: a device snapshot taken on the
+    // context stream, copied to the host on its own stream
+    cudaStream_t readout_stream = nullptr;
+    cudaEvent_t ev_snap = nullptr, ev_read = nullptr;
+    double* snap = nullptr;        // [15 max_particles]: x, u, om, F, T blocks
+    bool read_pending = false;
     cudaGraphExec_t step_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};   // kernel launches in each graph
     int graph_hcur[2][2] = {{0, 0}, {0, 0}};            // history parity after each graph
@@ -102,6 +108,16 @@ void destroy_handles(lbm_ctx* ctx) {
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     ctx->capture_stream = ctx->side_stream = nullptr;
     ctx->ev_fork = ctx->ev_join = nullptr;
+    if (ctx->readout_stream) {
+        cudaStreamSynchronize(ctx->readout_stream);
+        cudaStreamDestroy(ctx->readout_stream);
+    }
+    if (ctx->ev_snap) cudaEventDestroy(ctx->ev_snap);
+    if (ctx->ev_read) cudaEventDestroy(ctx->ev_read);
+    if (ctx->snap) cudaFree(ctx->snap);
+    ctx->readout_stream = nullptr;
+    ctx->ev_snap = ctx->ev_read = nullptr;
+    ctx->snap = nullptr;
 }
 
 namespace {
@@ -1069,6 +1085,7 @@ lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream) {
 lbm_status lbm_sync(lbm_ctx* ctx) {
     if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->readout_stream) CK(cudaStreamSynchronize(ctx->readout_stream));
     return check_status(ctx);
 }
 
@@ -1099,6 +1116,10 @@ lbm_status lbm_get_particle_state(lbm_ctx* ctx, int n_cap, double* pos, double* 
     return check_status(ctx);
 }
 
+// The state is copied on the context stream into a device snapshot (x, u,
+// omega, and F, T split out of [n][6]), and from there to the host on the
+// read-out stream, so the host copies overlap the steps queued after them.
+// The next snapshot waits for the previous host copies.
 lbm_status lbm_get_particle_state_async(lbm_ctx* ctx, int n_cap, double* pos, double* vel, double* omega,
                                         double* force_hyd, double* torque_hyd, int* n_out) {
     if (!ctx) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
@@ -1106,24 +1127,37 @@ lbm_status lbm_get_particle_state_async(lbm_ctx* ctx, int n_cap, double* pos, do
     if (n_out) *n_out = n;
     if (n_cap < n && (pos || vel || omega || force_hyd || torque_hyd))
         return fail(ctx, LBM_ERR_INVALID, "n_cap smaller than the particle count");
-    if (n == 0) return LBM_OK;
-    if ((force_hyd || torque_hyd) && 6LL * n > 4LL * ctx->scratch_cells)
-        return fail(ctx, LBM_ERR_CAPACITY, "more particles than the scratch buffer holds forces and torques for");
-    cudaStream_t sm = ctx->stream;
-    if (pos) CK(cudaMemcpyAsync(pos, ctx->P.x, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
-    if (vel) CK(cudaMemcpyAsync(vel, ctx->P.u, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
-    if (omega) CK(cudaMemcpyAsync(omega, ctx->P.om, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
+    if (n == 0 || !(pos || vel || omega || force_hyd || torque_hyd)) return LBM_OK;
+    if (!ctx->readout_stream) {
+        CK(cudaMalloc(&ctx->snap, 15 * sizeof(double) * (size_t)std::max(ctx->max_particles, 1)));
+        CK(cudaStreamCreateWithFlags(&ctx->readout_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_snap, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_read, cudaEventDisableTiming));
+    }
+    cudaStream_t sm = ctx->stream, rs = ctx->readout_stream;
+    const size_t b3 = 24 * (size_t)n;
+    double* sx = ctx->snap;
+    double* su = sx + 3 * (size_t)n;
+    double* so = su + 3 * (size_t)n;
+    double* sf = so + 3 * (size_t)n;   // F block, then T block
+    if (ctx->read_pending) CK(cudaStreamWaitEvent(sm, ctx->ev_read, 0));
+    if (pos) CK(cudaMemcpyAsync(sx, ctx->P.x, b3, cudaMemcpyDeviceToDevice, sm));
+    if (vel) CK(cudaMemcpyAsync(su, ctx->P.u, b3, cudaMemcpyDeviceToDevice, sm));
+    if (omega) CK(cudaMemcpyAsync(so, ctx->P.om, b3, cudaMemcpyDeviceToDevice, sm));
     if (force_hyd || torque_hyd) {
-        // split [n][6] into F and T blocks in the scratch buffer (later users
-        // of the scratch buffer are ordered after these copies on the stream)
-        launch_fp_split(ctx->P.fp, ctx->scratch, n, sm);
+        launch_fp_split(ctx->P.fp, sf, n, sm);
         CK(cudaGetLastError());
         ctx->launches += 1;
-        if (force_hyd) CK(cudaMemcpyAsync(force_hyd, ctx->scratch, 24 * (size_t)n, cudaMemcpyDeviceToHost, sm));
-        if (torque_hyd)
-            CK(cudaMemcpyAsync(torque_hyd, ctx->scratch + 3 * (size_t)n, 24 * (size_t)n, cudaMemcpyDeviceToHost,
-                               sm));
     }
+    CK(cudaEventRecord(ctx->ev_snap, sm));
+    CK(cudaStreamWaitEvent(rs, ctx->ev_snap, 0));
+    if (pos) CK(cudaMemcpyAsync(pos, sx, b3, cudaMemcpyDeviceToHost, rs));
+    if (vel) CK(cudaMemcpyAsync(vel, su, b3, cudaMemcpyDeviceToHost, rs));
+    if (omega) CK(cudaMemcpyAsync(omega, so, b3, cudaMemcpyDeviceToHost, rs));
+    if (force_hyd) CK(cudaMemcpyAsync(force_hyd, sf, b3, cudaMemcpyDeviceToHost, rs));
+    if (torque_hyd) CK(cudaMemcpyAsync(torque_hyd, sf + 3 * (size_t)n, b3, cudaMemcpyDeviceToHost, rs));
+    CK(cudaEventRecord(ctx->ev_read, rs));
+    ctx->read_pending = true;
     return LBM_OK;
 }
 
