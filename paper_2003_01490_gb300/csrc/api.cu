@@ -788,21 +788,15 @@ lbm_status lbm_add_spheres(lbm_ctx* ctx, int n, const double* pos, const double*
 // on the side stream the missing links and the DEM neighbour lists) and fills
 // the dense kernel's parameters; enqueue_post queues everything after it (the
 // force finalisation, the DEM, the mapping and the refill) and updates the
-// host-side state (buffer parities, launch count). A batch queues the dense
-// kernels of all its instances as one launch between the two parts.
+// host-side state (buffer parities, launch count). A batch does not use
+// them: it captures the same kernels as gang launches over its instances
+// (batch_capture_gang).
 struct StepState {
     LbmStepParams lp{};
     bool side = false;
     bool first = false;
     bool move = false;
     bool dem = false;
-    // a batch runs the one-block DEM steps of all its instances as one launch:
-    // enqueue_post then leaves this instance's to the batch (defer_dem) and
-    // records what the launch needs
-    bool defer_dem = false;
-    bool dem_deferred = false;
-    DemParams dem_p{};
-    int dem_hcur = 0, dem_nsub = 0;
 };
 
 // parameters of the step's boundary and dense kernels from the context state
@@ -927,15 +921,8 @@ lbm_status enqueue_post_a(lbm_ctx* ctx, DemParams& dp, cudaStream_t sm, StepStat
     if (move) {
         if (dem && ctx->P.n <= DEM_ONE_BLOCK_MAX) {
             // Algorithm 1, lines 4-10, in one block: few particles
-            if (ss.defer_dem) {
-                ss.dem_deferred = true;
-                ss.dem_p = dp;
-                ss.dem_hcur = ctx->hcur;
-                ss.dem_nsub = d.n_sub;
-            } else {
-                launch_dem_step_one_block(dp, ctx->hcur, d.n_sub, sm);
-                ctx->launches += 1;
-            }
+            launch_dem_step_one_block(dp, ctx->hcur, d.n_sub, sm);
+            ctx->launches += 1;
             if (d.n_sub & 1) ctx->hcur = 1 - ctx->hcur;
         } else if (dem) {
             // Algorithm 1, lines 4-10: DEM subcycles
@@ -1459,9 +1446,6 @@ struct lbm_batch {
     std::vector<cudaStream_t> ctx_streams;   // the distinct streams of the contexts
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaStream_t capture = nullptr;     // private stream the steps are captured on
-    std::vector<cudaStream_t> inst;     // one capture stream per instance
-    std::vector<cudaEvent_t> ev_pre, ev_mid, ev_post;
-    cudaEvent_t ev_fork = nullptr, ev_dense = nullptr, ev_dem = nullptr;
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         void* d_args = nullptr;
@@ -1545,113 +1529,6 @@ std::vector<int4> batch_items(const lbm_batch* b) {
     return out;
 }
 
-// capture one step of every active instance: per instance its work before
-// the dense kernel on its own stream, then one persistent dense launch over
-// all of them, per instance the force finalisation, one launch of the
-// one-block DEM steps of all instances with few particles, and per instance
-// the mapping and refill
-lbm_status batch_capture(lbm_batch* b, lbm_batch::Graph& G) {
-    const size_t n = b->ctx.size();
-    const size_t ab = batch_args_bytes(b->storage);
-    const size_t db = dem_batch_entry_bytes();
-    const std::vector<int4> items = batch_items(b);
-    G.n_items = (int)items.size();
-    BCK(cudaMalloc(&G.d_args, ab * n));
-    BCK(cudaMalloc(&G.d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
-    BCK(cudaMalloc(&G.d_dem, db * n));
-    std::vector<unsigned char> host(ab * n, 0), host_dem(db * n, 0);
-    std::vector<StepState> ss(n);
-    std::vector<DemParams> dp(n);
-    std::vector<long long> l0(n);
-    std::vector<int> cur0(n), h0(n);
-    for (size_t i = 0; i < n; ++i) {
-        lbm_ctx* c = b->ctx[i];
-        l0[i] = c->launches;
-        cur0[i] = c->cur;
-        h0[i] = c->hcur;
-        dp[i] = dem_params(c);
-    }
-    cudaGraph_t g = nullptr;
-    lbm_status st = LBM_OK;
-    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->capture);
-    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
-        if (!b->active[i]) continue;
-        e = cudaStreamWaitEvent(b->inst[i], b->ev_fork, 0);
-        if (e == cudaSuccess) st = enqueue_pre(b->ctx[i], dp[i], b->inst[i], ss[i]);
-        if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_pre[i], b->inst[i]);
-        if (e == cudaSuccess && st == LBM_OK) e = cudaStreamWaitEvent(b->capture, b->ev_pre[i], 0);
-        if (st == LBM_OK) fill_batch_args(ss[i].lp, batch_tile_bx(b, (int)i), batch_zchunk(b, (int)i), &host[ab * i]);
-    }
-    if (e == cudaSuccess && st == LBM_OK && G.n_items > 0) {
-        const int bps = b->blocks_per_sm > 0 ? b->blocks_per_sm : (b->storage == 0 ? 2 : 4);
-        const int grid = std::min(G.n_items, bps * b->num_sms);
-        launch_stream_collide_batch(b->storage, G.d_args, G.d_items, G.n_items, grid, b->capture);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_dense, b->capture);
-    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
-        if (!b->active[i]) continue;
-        e = cudaStreamWaitEvent(b->inst[i], b->ev_dense, 0);
-        ss[i].defer_dem = true;
-        if (e == cudaSuccess) st = enqueue_post_a(b->ctx[i], dp[i], b->inst[i], ss[i]);
-        if (e == cudaSuccess && st == LBM_OK && ss[i].dem_deferred) {
-            fill_dem_batch_entry(ss[i].dem_p, ss[i].dem_hcur, ss[i].dem_nsub, &host_dem[db * G.n_dem]);
-            G.n_dem += 1;
-            e = cudaEventRecord(b->ev_mid[i], b->inst[i]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->ev_mid[i], 0);
-        }
-    }
-    if (e == cudaSuccess && st == LBM_OK && G.n_dem > 0) {
-        launch_dem_step_batch(G.d_dem, G.n_dem, b->storage != LBM_STORE_F64, b->capture);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaEventRecord(b->ev_dem, b->capture);
-    }
-    for (size_t i = 0; i < n && e == cudaSuccess && st == LBM_OK; ++i) {
-        if (!b->active[i]) continue;
-        if (ss[i].dem_deferred) e = cudaStreamWaitEvent(b->inst[i], b->ev_dem, 0);
-        if (e == cudaSuccess) st = enqueue_post_b(b->ctx[i], dp[i], b->inst[i], ss[i]);
-        if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(b->ev_post[i], b->inst[i]);
-        if (e == cudaSuccess && st == LBM_OK) e = cudaStreamWaitEvent(b->capture, b->ev_post[i], 0);
-    }
-    cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
-    if (e == cudaSuccess) e = e2;
-    // the capture ran nothing: keep the host-side state changes of one step
-    // for the replays and undo them here
-    G.launches.assign(n, 0);
-    G.hcur_after.assign(n, 0);
-    for (size_t i = 0; i < n; ++i) {
-        lbm_ctx* c = b->ctx[i];
-        G.launches[i] = c->launches - l0[i];
-        G.hcur_after[i] = c->hcur;
-        c->launches = l0[i];
-        c->cur = cur0[i];
-        c->hcur = h0[i];
-    }
-    if (e == cudaSuccess && st == LBM_OK) e = cudaGraphInstantiate(&G.exec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (st != LBM_OK) return batch_fail(b, st, "a step of an instance could not be queued: " + b->ctx[0]->err);
-    BCK(e);
-    BCK(cudaMemcpy(G.d_args, host.data(), host.size(), cudaMemcpyHostToDevice));
-    if (G.n_items > 0)
-        BCK(cudaMemcpy(G.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
-    if (G.n_dem > 0) BCK(cudaMemcpy(G.d_dem, host_dem.data(), db * G.n_dem, cudaMemcpyHostToDevice));
-    return LBM_OK;
-}
-
-// Whether the step of every active instance can run as gang launches: its
-// particles (if any) are held fixed or moved by the DEM in one block.
-bool batch_gang_ok(const lbm_batch* b) {
-    for (size_t i = 0; i < b->ctx.size(); ++i) {
-        if (!b->active[i]) continue;
-        const lbm_ctx* c = b->ctx[i];
-        if (c->P.n == 0) continue;
-        if (c->dem.fixed_particles == 2) return false;
-        if (c->dem.fixed_particles == 0 && c->P.n > DEM_ONE_BLOCK_MAX) return false;
-    }
-    return true;
-}
-
 // The parameter tables of one kind of gang launch: one block per instance
 // that takes part, the prefix sums of their block counts.
 struct GangTable {
@@ -1680,13 +1557,15 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
     const std::vector<int4> items = batch_items(b);
     G.n_items = (int)items.size();
     std::vector<unsigned char> host(ab * n, 0), host_dem(db * n, 0);
-    GangTable bc, zb, bins, nbr, fin, zc, scat, map, ref;
+    GangTable bc, zb, bins, nbr, fin, zc, scat, map, ref, pos, copy, pres;
+    std::vector<GangTable> sub;   // one table per subcycle of the multi-block DEM steps
     bc.elem = bc_args_bytes();
     zb.elem = zc.elem = sizeof(ZeroSpan);
     bins.elem = nbr.elem = sizeof(DemParams);
     fin.elem = sizeof(FinalizeParams);
     scat.elem = map.elem = sizeof(MapParams);
     ref.elem = sizeof(RefillParams);
+    pos.elem = copy.elem = pres.elem = sizeof(DemGangEntry);
     G.launches.assign(n, 0);
     G.hcur_after.assign(n, 0);
     for (size_t i = 0; i < n; ++i) {
@@ -1718,10 +1597,37 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
             fp.averaging = d.force_averaging;
             fin.add(&fp, (np + 127) / 128);
         }
-        if (dem) {
+        if (dem && np <= DEM_ONE_BLOCK_MAX) {
             fill_dem_batch_entry(dp, c->hcur, d.n_sub, &host_dem[db * G.n_dem]);
             G.n_dem += 1;
             if (d.n_sub & 1) G.hcur_after[i] = 1 - c->hcur;
+        } else if (dem) {
+            // the multi-block DEM step: first position update, n_sub
+            // subcycles (history parity and state buffer alternating), the
+            // copy back into buffer 0 after an odd count
+            DemGangEntry ge{};
+            ge.p = dp;
+            pos.add(&ge, (np + 127) / 128);
+            int hc = c->hcur, cur = 0;
+            for (int k = 0; k < d.n_sub; ++k) {
+                if ((int)sub.size() <= k) {
+                    sub.emplace_back();
+                    sub.back().elem = sizeof(DemGangEntry);
+                }
+                ge.p.hin = hc;
+                ge.p.hout = 1 - hc;
+                ge.cur = cur;
+                ge.last = k == d.n_sub - 1;
+                sub[k].add(&ge, (np + DEM_ONE_BLOCK_MAX - 1) / DEM_ONE_BLOCK_MAX);
+                hc = 1 - hc;
+                cur = 1 - cur;
+            }
+            if (cur == 1) copy.add(&ge, (3 * np + 127) / 128);
+            G.hcur_after[i] = hc;
+        } else if (move) {
+            DemGangEntry ge{};
+            ge.p = dp;
+            pres.add(&ge, (np + 127) / 128);
         }
         if (move) {
             // n_solid and the missing-link and refill counts (16 bytes)
@@ -1746,10 +1652,12 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
         }
     }
     // one device buffer: the tables, then their offsets (16-byte aligned pieces)
-    GangTable* tabs[9] = {&bc, &zb, &bins, &nbr, &fin, &zc, &scat, &map, &ref};
+    std::vector<GangTable*> tabs = {&bc, &zb, &bins, &nbr, &fin, &zc, &scat, &map, &ref, &pos, &copy, &pres};
+    for (auto& t : sub) tabs.push_back(&t);
+    const int nt = (int)tabs.size();
     size_t total = 0;
-    size_t at_tab[9], at_off[9];
-    for (int k = 0; k < 9; ++k) {
+    std::vector<size_t> at_tab(nt), at_off(nt);
+    for (int k = 0; k < nt; ++k) {
         at_tab[k] = total;
         total += (tabs[k]->bytes.size() + 15) & ~size_t(15);
         at_off[k] = total;
@@ -1760,7 +1668,7 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
     BCK(cudaMalloc(&G.d_dem, db * n));
     BCK(cudaMalloc(&G.d_gang, std::max<size_t>(total, 16)));
     std::vector<unsigned char> gang(std::max<size_t>(total, 16), 0);
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < nt; ++k) {
         if (!tabs[k]->bytes.empty()) std::memcpy(gang.data() + at_tab[k], tabs[k]->bytes.data(), tabs[k]->bytes.size());
         std::memcpy(gang.data() + at_off[k], tabs[k]->off.data(), sizeof(int) * tabs[k]->off.size());
     }
@@ -1786,10 +1694,20 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
         }
         launch_gang(GANG_FINALIZE, T(4), O(4), fin.count(), fin.blocks(), cs);
         launches += gl(4);
+        const int pf32 = b->storage != LBM_STORE_F64;
         if (G.n_dem > 0) {
-            launch_dem_step_batch(G.d_dem, G.n_dem, b->storage != LBM_STORE_F64, cs);
+            launch_dem_step_batch(G.d_dem, G.n_dem, pf32, cs);
             launches += 1;
         }
+        launch_dem_gang(DEM_GANG_POSITION, pf32, T(9), O(9), pos.count(), pos.blocks(), cs);
+        launches += gl(9);
+        for (int k = 0; k < (int)sub.size(); ++k) {
+            launch_dem_gang(DEM_GANG_SUBCYCLE, pf32, T(12 + k), O(12 + k), sub[k].count(), sub[k].blocks(), cs);
+            launches += gl(12 + k);
+        }
+        launch_dem_gang(DEM_GANG_COPY, pf32, T(10), O(10), copy.count(), copy.blocks(), cs);
+        launch_dem_gang(DEM_GANG_PRESCRIBED, pf32, T(11), O(11), pres.count(), pres.blocks(), cs);
+        launches += gl(10) + gl(11);
         launch_gang(GANG_ZERO, T(5), O(5), zc.count(), zc.blocks(), cs);
         launch_map_gang(GANG_SCATTER, b->storage, T(6), O(6), scat.count(), scat.blocks(), cs);
         launch_map_gang(GANG_MAP, b->storage, T(7), O(7), map.count(), map.blocks(), cs);
@@ -1835,22 +1753,9 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* cuda_stream, lbm_
     for (int i = 0; i < n; ++i)
         if (std::find(b->ctx_streams.begin(), b->ctx_streams.end(), ctxs[i]->stream) == b->ctx_streams.end())
             b->ctx_streams.push_back(ctxs[i]->stream);
-    b->inst.assign(n, nullptr);
-    b->ev_pre.assign(n, nullptr);
-    b->ev_mid.assign(n, nullptr);
-    b->ev_post.assign(n, nullptr);
     cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_dense, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_dem, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithFlags(&b->inst[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_pre[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_mid[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_post[i], cudaEventDisableTiming);
-    }
     if (e != cudaSuccess) {
         lbm_batch_destroy(b);
         cudaGetLastError();
@@ -1917,7 +1822,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
         if (it == b->graphs.end()) {
             lbm_batch::Graph G;
             const auto t0 = std::chrono::steady_clock::now();
-            lbm_status st = batch_gang_ok(b) ? batch_capture_gang(b, G) : batch_capture(b, G);
+            lbm_status st = batch_capture_gang(b, G);
             b->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             b->captures += 1;
             if (st != LBM_OK) {
@@ -1973,19 +1878,8 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_clear_graphs(b);
-    for (auto s : b->inst)
-        if (s) cudaStreamDestroy(s);
-    for (auto ev : b->ev_pre)
-        if (ev) cudaEventDestroy(ev);
-    for (auto ev : b->ev_mid)
-        if (ev) cudaEventDestroy(ev);
-    for (auto ev : b->ev_post)
-        if (ev) cudaEventDestroy(ev);
-    if (b->ev_dem) cudaEventDestroy(b->ev_dem);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_dense) cudaEventDestroy(b->ev_dense);
     if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
 }

@@ -265,6 +265,18 @@ __device__ __forceinline__ void neighbour_body(const DemParams& p, int bx) {
                 }
                 cnt += __popc(m);
             }
+    // ascending partner order (a bitonic sort over the warp), so that the
+    // subcycles' pair sums, taken in slot order, do not depend on the order
+    // in which atomics filled the bins
+    const int m = cnt < NBR_CAP ? cnt : NBR_CAP;
+    __syncwarp();
+    int v = lane < m ? p.P.nbr[i * NBR_CAP + lane] : 0x7fffffff;
+    for (int k = 2; k <= 32; k <<= 1)
+        for (int j2 = k >> 1; j2 > 0; j2 >>= 1) {
+            const int o = __shfl_xor_sync(FULL, v, j2);
+            v = (((lane & j2) == 0) == ((lane & k) == 0)) ? min(v, o) : max(v, o);
+        }
+    if (lane < m) p.P.nbr[i * NBR_CAP + lane] = v;
     if (lane == 0) {
         if (cnt > NBR_CAP) {
             atomicOr(p.status, ST_NBR_OVERFLOW);
@@ -972,6 +984,46 @@ __global__ void fp_split_kernel(const double* __restrict__ fp, double* __restric
     const long long i = k / 6;
     const int c = (int)(k - 6 * i);
     out[(c < 3 ? 0 : 3LL * n) + 3 * i + (c < 3 ? c : c - 3)] = fp[k];
+}
+
+// The multi-block DEM step and prescribed motion of many instances: one
+// launch per phase (first position update, each subcycle, the copy back after
+// an odd count, the prescribed move), each block running its block of one
+// instance's grid with that instance's entry.
+template <typename T>
+__global__ void __launch_bounds__(128) dem_gang_kernel(const DemGangEntry* __restrict__ table,
+                                                       const int* __restrict__ off, int n, int kind) {
+    __shared__ __align__(16) DemGangEntry e;
+    const int i = gang_instance(off, n, (int)blockIdx.x);
+    gang_load(table, i, e);
+    const int bx = (int)blockIdx.x - off[i];
+    const Particles& P = e.p.P;
+    if (kind == DEM_GANG_SUBCYCLE) {
+        subcycle_body<T>(e.p, e.cur, e.p.hin, e.p.hout, 0, e.last, bx);
+        return;
+    }
+    const int k = bx * blockDim.x + threadIdx.x;
+    if (kind == DEM_GANG_POSITION) {
+        if (k < P.n) position_update(e.p, k);
+    } else if (kind == DEM_GANG_COPY) {
+        if (k < 3 * P.n) {
+            P.xs[0][k] = P.xs[1][k];
+            P.us[0][k] = P.us[1][k];
+            P.oms[0][k] = P.oms[1][k];
+            P.xfs[0][k] = P.xfs[1][k];
+        }
+    } else if (k < P.n) {   // prescribed motion
+        for (int d = 0; d < 3; ++d)
+            P.x[3 * k + d] = wrap_pos(P.x[3 * k + d] + P.u[3 * k + d], e.p.g.n[d], e.p.g.per[d]);
+        write_view(P, k);
+    }
+}
+
+void launch_dem_gang(int kind, int pair_f32, const void* table, const int* off, int n, int blocks, cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return;
+    const DemGangEntry* t = static_cast<const DemGangEntry*>(table);
+    if (pair_f32) dem_gang_kernel<float><<<blocks, 128, 0, st>>>(t, off, n, kind);
+    else dem_gang_kernel<double><<<blocks, 128, 0, st>>>(t, off, n, kind);
 }
 
 // words set to zero, per instance a span (the counters a step starts from)

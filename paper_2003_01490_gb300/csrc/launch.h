@@ -182,6 +182,14 @@ struct ZeroSpan {
 };
 void launch_gang(int kind, const void* table, const int* off, int n, int blocks, cudaStream_t st);
 void launch_map_gang(int kind, int storage, const void* table, const int* off, int n, int blocks, cudaStream_t st);
+// an instance's entry of a DEM gang launch: its parameters (hin, hout for a
+// subcycle), the subcycle's state buffer and whether it is the last one
+enum { DEM_GANG_POSITION = 1, DEM_GANG_SUBCYCLE, DEM_GANG_COPY, DEM_GANG_PRESCRIBED };
+struct DemGangEntry {
+    DemParams p;
+    int cur, last, pad0, pad1;
+};
+void launch_dem_gang(int kind, int pair_f32, const void* table, const int* off, int n, int blocks, cudaStream_t st);
 size_t bc_args_bytes();
 void fill_bc_args(const LbmStepParams& p, void* out);
 void launch_boundary_gang(int storage, const void* table, const int* off, int n, int blocks, int mode,

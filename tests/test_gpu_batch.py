@@ -254,3 +254,51 @@ def test_contexts_moved_to_their_batch_streams_run_concurrently_and_equal_each_a
     for i, ctx in enumerate(ctxs):
         for g, s_ in zip(state(L, ctx), solo[i]):
             assert np.array_equal(np.nan_to_num(g, nan=7.0), np.nan_to_num(s_, nan=7.0)), i
+
+
+@pytest.mark.parametrize('kind', ['fixed', 'many', 'prescribed'])
+def test_every_kind_of_instance_in_gang_launches_equals_itself_alone(L, kind):
+    # beside a one-sphere instance (one-block DEM): 'fixed', an instance with
+    # held particles (no DEM, mapping or refill); 'many', one with 40
+    # particles (the multi-block DEM: first position update, one launch per
+    # subcycle); 'prescribed', one moved by its set velocities
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    other = suspension_case((48, 48, 96), 40 if kind == 'many' else 12, 'f32', 41)
+    if kind != 'many':
+        other['dem'] = dict(other['dem'], fixed_particles=1 if kind == 'fixed' else 2)
+    cases = [sphere_wall_case(32, 8.0, 4.0, 0.6, 'f32', 42), other]
+    steps = 20
+    solo = []
+    for c in cases:
+        ctx = build_gpu(c)
+        L.lbm_step(ctx, steps)
+        solo.append(state(L, ctx))
+        del ctx
+    ctxs = [build_gpu(c) for c in cases]
+    for ctx in ctxs:
+        L.lbm_step(ctx, 1)
+    b = L.lbm_batch_create(ctxs)
+    for i, c in enumerate(cases):
+        bx, zc = solo_launch(c['shape'], sms)
+        L.lbm_batch_set_launch(b, i, bx, zc, 4)
+    L.lbm_batch_step(b, steps - 1)
+    L.lbm_batch_sync(b)
+    for i, ctx in enumerate(ctxs):
+        got = state(L, ctx)
+        assert np.array_equal(np.nan_to_num(got[0], nan=7.0), np.nan_to_num(solo[i][0], nan=7.0)), (kind, i)
+        for g, s_ in zip(got[1:], solo[i][1:]):
+            if kind == 'many' and i == 1:
+                # the multi-block DEM runs in another compiled kernel in a gang
+                # launch than alone, whose float64 contractions may differ: its
+                # particle state agrees to rounding (the fluid, which sees the
+                # particles through float32 views, bit for bit)
+                err = np.abs(g - s_).max() / max(np.abs(s_).max(), 1e-300)
+                print('multi-block DEM in a gang launch: max relative difference %.1e' % err)
+                assert err < 1e-10, err
+            else:
+                assert np.array_equal(g, s_), (kind, i)
+    # 11 gang launches a step, plus the first position update and the 10
+    # subcycles of the multi-block DEM, or the prescribed move
+    extra = {'fixed': 0, 'many': 11, 'prescribed': 1}[kind]
+    assert L.lbm_batch_launch_count(b) == (11 + extra) * (steps - 1)
