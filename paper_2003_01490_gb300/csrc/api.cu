@@ -1580,7 +1580,9 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
         fill_step_params(c, lp);
         std::vector<unsigned char> bca(bc.elem, 0);
         fill_bc_args(lp, bca.data());
-        bc.add(bca.data(), lp.missing_links ? 4 : 1);
+        // the missing-link and refill lists grow with the particle count
+        const int list_blocks = std::min(8 * b->num_sms, 1 + np / 8);
+        bc.add(bca.data(), lp.missing_links ? list_blocks : 1);
         fill_batch_args(lp, batch_tile_bx(b, (int)i), batch_zchunk(b, (int)i), &host[ab * i]);
         DemParams dp = dem_params(c);
         if (dem) {
@@ -1648,7 +1650,7 @@ lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
             rp.cap = c->refill_cap;
             rp.s_nu = 1.0 / c->relax.tau;
             rp.accel = c->accel;
-            ref.add(&rp, 4);
+            ref.add(&rp, list_blocks);
         }
     }
     // one device buffer: the tables, then their offsets (16-byte aligned pieces)
