@@ -129,8 +129,24 @@ struct __align__(16) PartView {
     float R;
     float u[3];
     float om[3];
-    float C;               // |g|^2 - R^2 with g = 1/2 - frac (per-axis fractional offsets)
+    float C;               // |g|^2 - R^2 with g = 1/2 - frac (per-axis fractional offsets),
+    float C_lo;            // in two parts: C + C_lo holds it to float64 accuracy
 };
+
+// C and C_lo of a view whose frac is set, from the float32 g = 1/2 - frac the
+// link arithmetic uses (so |n + g|^2 - R^2 = |n|^2 + 2 n.g + C + C_lo is the
+// exact value for the sphere centred at base + frac)
+__device__ __forceinline__ void set_view_c(PartView& v, double R) {
+    double gg = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float gf = 0.5f - v.frac[d];
+        gg += (double)gf * (double)gf;
+    }
+    const double C = gg - R * R;
+    v.C = (float)C;
+    v.C_lo = (float)(C - (double)v.C);
+}
 
 struct Particles {
     int n;                 // particle count

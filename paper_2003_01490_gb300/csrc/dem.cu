@@ -83,20 +83,17 @@ __device__ __forceinline__ double mimg(double d, int n, int per) {
 
 __device__ __forceinline__ void write_view(const Particles& P, int i) {
     PartView v;
-    double gg = 0.0;
     for (int d = 0; d < 3; ++d) {
         const double x = P.x[3 * i + d];
         const double b = floor(x);
         v.base[d] = (int)b;
         v.frac[d] = (float)(x - b);
-        const double g = 0.5 - (x - b);
-        gg += g * g;
         v.u[d] = (float)P.u[3 * i + d];
         v.om[d] = (float)P.om[3 * i + d];
         P.xf[3 * i + d] = (float)x;
     }
     v.R = (float)P.R[i];
-    v.C = (float)(gg - P.R[i] * P.R[i]);
+    set_view_c(v, P.R[i]);
     P.view[i] = v;
 }
 
@@ -642,7 +639,6 @@ __device__ void integrate_particle(const DemParams& p, int ip, const T (&sum)[6]
     const double Fa[3] = {Fs.x, Fs.y, Fs.z};
     const double c = p.dt * cu;
     PartView v;
-    double gg = 0.0;
     for (int d = 0; d < 3; ++d) {
         // Eq. (37) for the next subcycle; the last subcycle keeps its positions
         double x = X[3 * ip + d];
@@ -653,15 +649,13 @@ __device__ void integrate_particle(const DemParams& p, int ip, const T (&sum)[6]
             const double b = floor(x);
             v.base[d] = (int)b;
             v.frac[d] = (float)(x - b);
-            const double g = 0.5 - (x - b);
-            gg += g * g;
             v.u[d] = (float)ua[d];
             v.om[d] = (float)(d == 0 ? om.x : d == 1 ? om.y : om.z);
         }
     }
     if (last) {
         v.R = (float)P.R[ip];
-        v.C = (float)(gg - P.R[ip] * P.R[ip]);
+        set_view_c(v, P.R[ip]);
         P.view[ip] = v;
     }
 }

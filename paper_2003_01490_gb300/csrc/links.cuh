@@ -141,7 +141,7 @@ template <> struct PartOps<float> {
     template <typename A>
     __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float& R,
                                 float (&u)[3], float (&om)[3]) {
-        float g[3], C;
+        float g[3], C[2];
         load(a, i, x, y, z, r, n, g, C, R, u, om);
     }
     // also the fractional offset g and C = |g|^2 - R^2 of the particle. The
@@ -150,7 +150,7 @@ template <> struct PartOps<float> {
     // 2 R + 4, so exactly one image has |n_d| <= floor(n / 2)
     template <typename A>
     __device__ static void load(const A& a, int i, int x, int y, int z, float (&r)[3], int (&n)[3], float (&g)[3],
-                                float& C, float& R, float (&u)[3], float (&om)[3]) {
+                                float (&C)[2], float& R, float (&u)[3], float (&om)[3]) {
         const PartView v = a.view[i];
         const int c[3] = {x, y, z};
 #pragma unroll
@@ -168,7 +168,8 @@ template <> struct PartOps<float> {
             om[d] = v.om[d];
         }
         R = v.R;
-        C = v.C;
+        C[0] = v.C;
+        C[1] = v.C_lo;
     }
 };
 
@@ -221,12 +222,14 @@ __device__ __forceinline__ T surface_cc(const T (&r)[3], T R) {
 }
 
 // the same for r = n + g with integer n and the particle's common fractional
-// offset g: |n|^2 + 2 n.g + (|g|^2 - R^2), the last term precomputed per
-// particle, so no two large float32 terms cancel
-__device__ __forceinline__ float surface_cc_split(const int (&n)[3], const float (&g)[3], float C) {
+// offset g: (|n|^2 + C) + (2 n.g + C_lo), with C + C_lo = |g|^2 - R^2
+// precomputed per particle to float64 accuracy. Near the surface |n|^2 and
+// -C agree to within a factor of two, so their sum is exact and only the
+// small terms round.
+__device__ __forceinline__ float surface_cc_split(const int (&n)[3], const float (&g)[3], const float (&C)[2]) {
     const int nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
     const float ng = fmaf((float)n[2], g[2], fmaf((float)n[1], g[1], (float)n[0] * g[0]));
-    return (float)nn + fmaf(2.0f, ng, C);
+    return ((float)nn + C[0]) + fmaf(2.0f, ng, C[1]);
 }
 
 template <typename T>

@@ -51,6 +51,7 @@ __global__ void noalloc_view_kernel(int n, const double* __restrict__ pos, const
     }
     v.R = (float)radius[i];
     v.C = 0.f;   // unused by the mapping
+    v.C_lo = 0.f;
     s->view[i] = v;
 }
 

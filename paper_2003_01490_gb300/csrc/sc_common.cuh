@@ -115,7 +115,7 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
     int n[3];
     T cc;   // |r|^2 - R^2
     if constexpr (sizeof(T) == 4) {
-        float g[3], C;
+        float g[3], C[2];
         PartOps<T>::load(a, i, x, y, z, r, n, g, C, R, u, om);
         cc = surface_cc_split(n, g, C);
     } else {
@@ -167,8 +167,9 @@ __device__ __forceinline__ T link_value(const SCArgs<S, T>& a, int x, int y, int
 //   f_q += dp + dm,  f_qbar += dp - dm,
 // the Guo source in Y and 3 w c.a; corr is the rank-2 bulk correction of the
 // shell cells. Each pair costs one chain of fused multiply-adds.
-template <typename S, typename T>
-__device__ __forceinline__ bool collide_cell_a(const SCArgs<S, T>& a, T (&f)[Q], uint8_t fl, T ax, T ay, T az) {
+template <typename T>
+__device__ __forceinline__ bool collide_core(T (&f)[Q], uint8_t fl, T ax, T ay, T az, T sp, T sm, T s_b_shell,
+                                             T s_b_bulk, int bulk_corr) {
     T sq[Q], dq[Q];   // pair sums and differences, entries q < opp(q) only
     T drho = f[0], jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
@@ -185,15 +186,14 @@ __device__ __forceinline__ bool collide_cell_a(const SCArgs<S, T>& a, T (&f)[Q],
     const T ux = jx + T(0.5) * ax, uy = jy + T(0.5) * ay, uz = jz + T(0.5) * az;
     const T usq = ux * ux + uy * uy + uz * uz;
     const T ua = ux * ax + uy * ay + uz * az;
-    const T sp = a.s_plus, sm = a.s_minus;
     const T gp = T(1) - T(0.5) * sp, gm = T(1) - T(0.5) * sm;
     // bulk moments m4 = sum (c^2 - 1) f and m5 (row 6 of M) of the streamed
     // PDFs relax with s_b in shell cells (and everywhere when Lambda_b,bulk != 1)
     const bool shell = (fl & FL_SHELL) != 0;
-    const bool bulk = shell || a.bulk_corr;
+    const bool bulk = shell || bulk_corr;
     T k4 = T(0), k5 = T(0);
     if (bulk) {
-        const T ds = (shell ? a.s_b_shell : a.s_b_bulk) - sp;
+        const T ds = (shell ? s_b_shell : s_b_bulk) - sp;
         T saxis = T(0), sdiag = T(0);
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -208,16 +208,27 @@ __device__ __forceinline__ bool collide_cell_a(const SCArgs<S, T>& a, T (&f)[Q],
     }
     const T drp = drho - T(1.5) * usq;
     const T m3ua = T(-3) * ua;
+    // Weights of the update: w2 = 2 w (even parts), w6 = 6 w (odd parts) per
+    // class (axis, diagonal) and w0. In float32 they are chosen within 6e-8
+    // of the exact fractions such that w0 + 3 w2_axis + 6 w2_diag = 1 and
+    // w6_axis + 4 w6_diag = 1 hold exactly: the relaxation towards the
+    // equilibrium then keeps the mass and momentum of every cell, where the
+    // plain roundings of 1/18, 1/36 and 1/3 would leave a steady source of
+    // relative size 3e-8 per step that builds up over a long run.
+    const T w2d = sizeof(T) == 4 ? T(0.0555555522441864) : T(1) / T(18);
+    const T w2a = T(2) * w2d;
+    const T w0 = T(1) - T(12) * w2d;
+    const T w6d = T(1) / T(6);
+    const T w6a = T(1) - T(4) * w6d;
     {
-        const T w0 = wq<T>(0);
         f[0] = f[0] + sp * (w0 * drp - f[0]) + gp * (w0 * m3ua) + w0 * (k5 - k4);
     }
     const T hsp = T(-0.5) * sp, hsm = T(-0.5) * sm;
-    // per weight class (axis 1/18, diagonal 1/36)
-    const T wa = T(1) / T(18), wd = T(1) / T(36);
-    const T spw[2] = {sp * wa, sp * wd}, gpw[2] = {gp * wa, gp * wd};
-    const T smw3[2] = {T(3) * wa * sm, T(3) * wd * sm}, gmw3[2] = {T(3) * wa * gm, T(3) * wd * gm};
-    const T corr[2] = {wa * (T(-2) * k5), wd * (k4 + k5)};
+    // per weight class (axis, diagonal); each part relaxes as rate x (value
+    // - its equilibrium)
+    const T w2[2] = {w2a, w2d}, w6[2] = {w6a, w6d};
+    const T gpw[2] = {T(0.5) * gp * w2a, T(0.5) * gp * w2d}, gmw3[2] = {T(0.5) * gm * w6a, T(0.5) * gm * w6d};
+    const T corr[2] = {-w2a * k5, T(0.5) * w2d * (k4 + k5)};
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const int qb = opp(q);
@@ -229,12 +240,17 @@ __device__ __forceinline__ bool collide_cell_a(const SCArgs<S, T>& a, T (&f)[Q],
         if (cz(q)) { cu += cz(q) > 0 ? uz : -uz; ca += cz(q) > 0 ? az : -az; }
         const T X = fma_t<T>(T(4.5) * cu, cu, drp);
         const T Y = fma_t<T>(T(9) * cu, ca, m3ua);
-        const T dp = fma_t<T>(spw[k], X, fma_t<T>(gpw[k], Y, fma_t<T>(hsp, sq[q], corr[k])));
-        const T dm = fma_t<T>(hsm, dq[q], fma_t<T>(smw3[k], cu, gmw3[k] * ca));
+        const T dp = fma_t<T>(hsp, fma_t<T>(-w2[k], X, sq[q]), fma_t<T>(gpw[k], Y, corr[k]));
+        const T dm = fma_t<T>(hsm, fma_t<T>(-w6[k], cu, dq[q]), gmw3[k] * ca);
         f[q] = f[q] + (dp + dm);
         f[qb] = f[qb] + (dp - dm);
     }
     return drho < T(0.5) && drho > T(-0.5);
+}
+
+template <typename S, typename T>
+__device__ __forceinline__ bool collide_cell_a(const SCArgs<S, T>& a, T (&f)[Q], uint8_t fl, T ax, T ay, T az) {
+    return collide_core<T>(f, fl, ax, ay, az, a.s_plus, a.s_minus, a.s_b_shell, a.s_b_bulk, a.bulk_corr);
 }
 
 template <typename S, typename T>
