@@ -169,9 +169,11 @@ def run_to_1000(L, storage):
     return ctx, errors_against(L, ctx, gold, 1000)
 
 
-# a kernel error above its storage floor: float32 arithmetic and float32
-# link geometry add rounding of the same order as the storage itself
-ARITH_FACTOR = 4.0
+# where a target lies below a floor, the error is held to this multiple of
+# the floor: the kernels' float32 arithmetic adds rounding of its own
+# (measured on GB300 at step 1000: float16 1.04 x its storage floor in u,
+# bfloat16 1.00 x)
+ARITH_FACTOR = 1.5
 
 
 def test_reduced_suspension_f32_at_1000_steps_against_the_floors(L):
@@ -180,7 +182,9 @@ def test_reduced_suspension_f32_at_1000_steps_against_the_floors(L):
     _, e = run_to_1000(L, 'f32')
     report('f32 step 1000', e, {'predictability': chaos, 'f32 storage': storage})
     # the float32 copies of rho in the predictability runs resolve no density
-    # difference below 6e-8: that floor's rho columns are not used
+    # difference below 6e-8: that floor's rho columns are not used. Measured
+    # on GB300: u 3.4e-7, rho 4.1e-10, positions 1.0e-9 (all floors lie
+    # below the targets, so the targets are asserted)
     for key, tol in (('u', 1e-6), ('rho', 1e-6), ('pos', 1e-5)):
         floor = storage[key] if key.startswith('rho') else max(storage[key], chaos[key])
         if floor < tol:
