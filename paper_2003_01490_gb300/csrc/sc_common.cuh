@@ -209,7 +209,7 @@ __device__ __forceinline__ bool collide_core(T (&f)[Q], uint8_t fl, T ax, T ay, 
     const T drp = drho - T(1.5) * usq;
     const T m3ua = T(-3) * ua;
     // Weights of the update: w2 = 2 w (even parts), w6 = 6 w (odd parts) per
-    // class (axis, diagonal) and w0. In float32 they are chosen within 6e-8
+    // class (axis, diagonal) and w0. In float32 they are chosen within 1.2e-7
     // of the exact fractions such that w0 + 3 w2_axis + 6 w2_diag = 1 and
     // w6_axis + 4 w6_diag = 1 hold exactly: the relaxation towards the
     // equilibrium then keeps the mass and momentum of every cell, where the

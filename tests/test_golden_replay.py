@@ -45,3 +45,18 @@ def test_sphere_wall_golden_is_the_oracle_as_it_stands():
         sim.step()
         got = np.concatenate([sim.X[0], sim.U[0], sim.Om[0], sim.Ffp[0], sim.Tfp[0]])
         assert np.allclose(got, gold[k], rtol=1e-13, atol=1e-16), k
+
+
+def test_storage_rounding_of_the_floor_runs_matches_torch_conversions():
+    # the storage floor rounds f - w as the GPU stores it: float32 round to
+    # nearest even, float16 and bfloat16 from the float32 value
+    import numpy as np
+    import torch
+    sys.path.insert(0, os.path.join(HERE, 'golden'))
+    import make_long_runs
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.normal(0, 1e-3, 5000), rng.normal(0, 1e-6, 5000), [0.0, -0.0, 1e-40, 65504.0]])
+    t = torch.tensor(v.astype(np.float32))
+    assert np.array_equal(make_long_runs.round_storage(v, 'f32'), t.double().numpy())
+    assert np.array_equal(make_long_runs.round_storage(v, 'f16'), t.to(torch.float16).double().numpy())
+    assert np.array_equal(make_long_runs.round_storage(v, 'bf16'), t.to(torch.bfloat16).double().numpy())
