@@ -355,6 +355,8 @@ void launch_prescribed_move(const Particles& P, const Geom& g, cudaStream_t st) 
 template <typename T>
 __device__ void lubrication_on_i(const DemConsts<T>& k, int tangential, T Ri, T Rj, T delta, Vec3<T> n,
                                  Vec3<T> uij, Vec3<T> omi, Vec3<T> omj, T dmin, Vec3<T>& F, Vec3<T>& Tq) {
+    // no term acts outside (0, largest cut-off): a far wall or partner costs nothing
+    if (!(delta > T(0) && delta < k.cut_max)) return;
     const T pi = T(3.14159265358979323846);
     const T mu = k.mu_f;
     const T dl = delta > dmin ? delta : dmin;
