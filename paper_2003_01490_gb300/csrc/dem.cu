@@ -788,7 +788,8 @@ __global__ void __launch_bounds__(128) subcycle_kernel(const DemParams p, int cu
 // the particle arrays of its (shared) parameter copy at the staged arrays, runs
 // the subcycles there -- the code of the multi-block path, reaching shared
 // memory through generic pointers -- and writes back what the step changed.
-// Neighbour lists, pair springs and the particle views stay in global memory.
+// The neighbour counts are staged too (read every subcycle); the neighbour
+// lists, pair springs and the particle views stay in global memory.
 // Latency, not arithmetic, sets the time of a few-particle DEM step, so each
 // dependent global round trip saved per subcycle counts.
 struct DemStage {
@@ -798,6 +799,7 @@ struct DemStage {
     double hm[PPB], hI[PPB], R[PPB], m[PPB];
     double whist[2][18 * PPB];
     unsigned char wact[2][6 * PPB];
+    int nbr_count[PPB];
 };
 
 // sp: the step's parameters in shared memory (n <= PPB particles); g receives
@@ -833,6 +835,7 @@ __device__ void dem_step_block(DemParams& sp, Particles& g, DemStage& st, int hc
         st.hI[k] = g.hI[k];
         st.R[k] = g.R[k];
         st.m[k] = g.m[k];
+        st.nbr_count[k] = g.nbr_count[k];
     }
     if (tid == 0) {
         Particles& P = sp.P;
@@ -858,6 +861,7 @@ __device__ void dem_step_block(DemParams& sp, Particles& g, DemStage& st, int hc
         P.hI = st.hI;
         P.R = st.R;
         P.m = st.m;
+        P.nbr_count = st.nbr_count;
     }
     __syncthreads();
     if (tid < n) position_update(sp, tid);
