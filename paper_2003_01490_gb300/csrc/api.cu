@@ -1529,8 +1529,8 @@ std::vector<int4> batch_items(const lbm_batch* b) {
     return out;
 }
 
-// The parameter tables of one kind of gang launch: one block per instance
-// that takes part, the prefix sums of their block counts.
+// The table of one kind of gang launch: a parameter block per instance that
+// takes part, and the prefix sums of the instances' launch-block counts.
 struct GangTable {
     std::vector<unsigned char> bytes;
     std::vector<int> off{0};
@@ -1547,9 +1547,11 @@ struct GangTable {
 
 // Capture one step of every active instance as gang launches (each per-step
 // kernel once for all instances; the dense kernels in one persistent launch,
-// the DEM steps in one launch), in the order of a single instance's step:
-// fluid body force and missing links, neighbour bins and lists, dense kernel,
-// force finalisation, DEM, counters, tile scatter, mapping, refill.
+// the one-block DEM steps in one launch, the multi-block DEM steps as a
+// position launch and one launch per subcycle, prescribed moves in one), in
+// the order of a single instance's step: fluid body force and missing links,
+// neighbour bins and lists, dense kernel, force finalisation, DEM, counters,
+// tile scatter, mapping, refill.
 lbm_status batch_capture_gang(lbm_batch* b, lbm_batch::Graph& G) {
     const size_t n = b->ctx.size();
     const size_t ab = batch_args_bytes(b->storage);
